@@ -1,0 +1,133 @@
+"""FP64 CPU oracle of the SAGMS / SMS / MS / BP decoder (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
+import this package.  It shares no code with the CUDA library: the arithmetic lives in
+``oracle.c`` (plain C, double precision, explicit per-edge message arrays and direct
+leave-one-out loops, following Algorithm 1 with Eqs. 1-8 of the paper), which this module
+compiles with gcc and calls through ctypes.
+
+Parity status per function:
+* ``decode`` (MS, SMS, SAGMS, BP): pinned by the tests in ``tests/test_oracle_pins.py``
+  (tree-code brute force, closed forms at the first iteration, reductions between modes,
+  the single-check ratio of Eq. 9, the zero-syndrome case).
+* ``alpha_star`` / ``alpha_star_approx``: pinned to the values the paper prints (Sec. V).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+MS, SMS, SAGMS, BP = 0, 1, 2, 3
+FLAG_L0_PER_QUBIT = 1
+FLAG_NO_EARLY_STOP = 2
+FLAG_NATURAL_UNITS = 8
+
+MSFAM_CLIP = 1.0e6
+BP_CLIP = 23.718998
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build_lib(force: bool = False) -> str:
+    """Compile oracle.c (portable flags: the same source builds on x86 and Arm hosts)."""
+    src = os.path.join(_HERE, "oracle.c")
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(src):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fno-fast-math",
+                               "-ffp-contract=off", src, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build_lib()
+        lib = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.POINTER
+        lib.oracle_decode.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_int32), P(ctypes.c_int32),
+                                      ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_int, ctypes.c_uint, ctypes.c_int64,
+                                      P(ctypes.c_uint32), P(ctypes.c_double), P(ctypes.c_uint32),
+                                      P(ctypes.c_uint8), P(ctypes.c_int32), P(ctypes.c_double)]
+        lib.oracle_decode.restype = ctypes.c_int
+        lib.oracle_alpha_star.argtypes = [ctypes.c_double, ctypes.c_int]
+        lib.oracle_alpha_star.restype = ctypes.c_double
+        lib.oracle_alpha_star_approx.argtypes = [ctypes.c_double, ctypes.c_int]
+        lib.oracle_alpha_star_approx.restype = ctypes.c_double
+        _lib = lib
+    return _lib
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct)) if a is not None else None
+
+
+def decode(m, n, row_ptr, col_idx, syn, L0, mode=SAGMS, alpha=0.75, alpha_min=0.30, alpha_max=0.50,
+           eta_unsat=1.10, max_iter=100, flags=0, trace=False, threads=1):
+    """Decode packed syndromes ``syn`` [shots][ceil(m/32)].
+
+    ``L0``: [shots] per-shot prior, or [n] with FLAG_L0_PER_QUBIT.  Returns a dict with
+    ``err`` [shots][ceil(n/32)] uint32, ``conv`` [shots] uint8, ``iters`` [shots] int32 and,
+    with ``trace=True``, ``trace`` [shots][max_iter+1][n] float64 posteriors (units the
+    decoder runs in: L0-normalised for the MS family with a per-shot prior)."""
+    lib = _load()
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+    syn = np.ascontiguousarray(syn, dtype=np.uint32).reshape(-1, (m + 31) // 32)
+    shots = syn.shape[0]
+    L0 = np.ascontiguousarray(L0, dtype=np.float64).reshape(-1)
+    per_qubit = bool(flags & FLAG_L0_PER_QUBIT)
+    if per_qubit and L0.shape[0] != n:
+        raise ValueError("per-qubit L0 must have n entries")
+    if not per_qubit and L0.shape[0] != shots:
+        raise ValueError("per-shot L0 must have one entry per shot")
+    nw = (n + 31) // 32
+    err = np.zeros((shots, nw), dtype=np.uint32)
+    conv = np.zeros(shots, dtype=np.uint8)
+    iters = np.zeros(shots, dtype=np.int32)
+    tr = np.zeros((shots, max_iter + 1, n), dtype=np.float64) if trace else None
+
+    def run(lo, hi):
+        if hi <= lo:
+            return
+        Ls = L0 if per_qubit else L0[lo:hi]
+        rc = lib.oracle_decode(m, n, _p(row_ptr, ctypes.c_int32), _p(col_idx, ctypes.c_int32), mode,
+                               alpha, alpha_min, alpha_max, eta_unsat, max_iter, flags, hi - lo,
+                               _p(syn[lo:hi], ctypes.c_uint32), _p(np.ascontiguousarray(Ls), ctypes.c_double),
+                               _p(err[lo:hi], ctypes.c_uint32), _p(conv[lo:hi], ctypes.c_uint8),
+                               _p(iters[lo:hi], ctypes.c_int32), _p(tr[lo:hi] if tr is not None else None, ctypes.c_double))
+        if rc != 0:
+            raise RuntimeError("oracle_decode: bad arguments")
+
+    threads = max(1, int(threads))
+    if threads == 1 or shots < 2 * threads:
+        run(0, shots)
+    else:
+        bounds = np.linspace(0, shots, threads + 1).astype(int)
+        with ThreadPoolExecutor(threads) as ex:
+            list(ex.map(lambda k: run(bounds[k], bounds[k + 1]), range(threads)))
+    out = {"err": err, "conv": conv, "iters": iters}
+    if tr is not None:
+        out["trace"] = tr
+    return out
+
+
+def decode_code(code, syn, L0, **kw):
+    return decode(code.m, code.n, code.row_ptr, code.col_idx, syn, L0, **kw)
+
+
+def alpha_star(L0: float, dc: int) -> float:
+    """Eq. 9, exact form."""
+    return _load().oracle_alpha_star(float(L0), int(dc))
+
+
+def alpha_star_approx(L0: float, dc: int) -> float:
+    """Eq. 9, first-order form 1 - ln(dc - 1)/L0."""
+    return _load().oracle_alpha_star_approx(float(L0), int(dc))

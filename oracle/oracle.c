@@ -1,0 +1,226 @@
+/*
+ * FP64 CPU oracle for SAGMS / SMS / MS / BP syndrome decoding.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously-correct
+ * statement of the decoder that the CUDA path is checked against.  Only the
+ * tests, the smoke check and the benchmark's CPU-baseline leg load it.  It
+ * shares no code, header, table or helper with the CUDA library.
+ *
+ * What it computes (paper: "Syndrome Adaptive Gain Control for Min-Sum
+ * Decoding of Quantum LDPC Codes"), on a binary parity-check matrix H in CSR
+ * form, for each shot:
+ *
+ *   State: one double per Tanner-graph edge e = (i, j) for the VN->CN message
+ *   q[e] = L_{j->i} and one for the CN->VN message r[e] = L_{i->j}.
+ *   Init (Sec. II, BP4 decoder): q[e] = L0_j, r[e] = 0.
+ *   For l = 1, 2, ... (Algorithm 1):
+ *     (i)   posterior P_j = L0_j + sum_{i in N(j)} r(i,j); hard decision
+ *           e_hat_j = [P_j < 0]; residual syndrome s~ = s XOR H e_hat (Eq. 1);
+ *     (ii)  s~ = 0 -> success, iters = l - 1 (rounds completed);
+ *           after max_iter rounds -> failure, iters = max_iter;
+ *     (iii) syndrome ratio gamma = |s~|_0 / m (Eq. 6) and per-check gain
+ *           g_i (Eq. 7 for SAGMS; alpha for SMS; 1 for MS);
+ *     (iv)  CN update for every edge, as the leave-one-out over M(i)\j written
+ *           out directly:
+ *             MS family (Eqs. 4, 8): r = (-1)^{s_i} prod sgn(q) * g_i * min |q|
+ *             BP (Eq. 3, tanh form): r = (-1)^{s_i} prod sgn(q) * 2 atanh(prod tanh(|q|/2))
+ *           (the tanh product is the same function as phi^{-1}(sum phi) with
+ *           phi(x) = -log tanh(x/2), evaluated in the product domain);
+ *     (v)   VN update for every edge (Eq. 2): q(j,i) = L0_j + sum_{k in N(j)\i} r(k,j),
+ *           again as a direct leave-one-out sum, using the CN messages of (iv).
+ *
+ * Readings of points the paper leaves open (each also listed in the design
+ * notes of the repository):
+ *   - binary hard decision: e_hat_j = 1 iff P_j < 0 (P_j = 0 -> 0);
+ *     sgn(0) = +1 in the sign products;
+ *   - s~_i in Eq. 7 is the residual bit; (-1)^{s_i} in Eqs. 3/4/8 uses the
+ *     input syndrome bit; |S| = m (rows of the supplied H);
+ *   - flooding schedule: (v) uses the CN messages just computed in (iv);
+ *   - max_iter message-passing rounds, each followed by the (i)/(ii) check;
+ *   - MS family with a per-shot scalar L0 runs in L0-normalised units (every
+ *     message divided by |L0|, prior sign(L0)): the MS/SMS/SAGMS updates are
+ *     positively homogeneous of degree 1, so this changes no decision and
+ *     makes MS exact-integer (ties resolve identically in any precision);
+ *   - MS-family CN outputs are clipped to |r| <= 1e6 (normalised units when
+ *     normalised), BP outputs to |r| <= 23.718998 = ln(2e10), the cap implied
+ *     by the 1e-10 guard of the paper's BP transfer-function plot (Fig. 1b);
+ *   - degree-1 checks: the leave-one-out set is empty, so min = +inf
+ *     (MS family) or prod = 1 (BP) and the output saturates at the clip.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_MODE_MS 0
+#define ORACLE_MODE_SMS 1
+#define ORACLE_MODE_SAGMS 2
+#define ORACLE_MODE_BP 3
+
+#define ORACLE_FLAG_L0_PER_QUBIT 1u
+#define ORACLE_FLAG_NO_EARLY_STOP 2u
+#define ORACLE_FLAG_NATURAL_UNITS 8u  /* oracle only: keep the MS family in LLR units */
+
+static const double MSFAM_CLIP = 1.0e6;
+static const double BP_CLIP = 23.718998;
+
+static int bit_of(const uint32_t* w, int k) { return (int)((w[k >> 5] >> (k & 31)) & 1u); }
+
+/*
+ * Decode `shots` syndromes.
+ *   row_ptr[m+1], col_idx[nnz]: H in CSR (any column order, no duplicates).
+ *   syn:   [shots][ceil(m/32)] packed input syndromes.
+ *   L0:    [shots] (per-shot scalar prior) or, with ORACLE_FLAG_L0_PER_QUBIT, [n].
+ *   err:   [shots][ceil(n/32)] packed e_hat (out).
+ *   conv:  [shots] 1 if s~ = 0 at return (out).   iters: [shots] (out).
+ *   trace: optional [shots][max_iter+1][n] posteriors P_j at each check (i),
+ *          in the units the decoder runs in; rows after the return are left as is.
+ * Returns 0, or -1 on bad arguments / allocation failure.
+ */
+int oracle_decode(int m, int n, const int32_t* row_ptr, const int32_t* col_idx,
+                  int mode, double alpha, double alpha_min, double alpha_max, double eta_unsat,
+                  int max_iter, unsigned flags, int64_t shots,
+                  const uint32_t* syn, const double* L0,
+                  uint32_t* err, uint8_t* conv, int32_t* iters, double* trace) {
+    if (m < 0 || n <= 0 || max_iter < 0 || shots < 0 || !row_ptr || !col_idx || !syn || !L0 ||
+        !err || !conv || !iters || mode < 0 || mode > 3)
+        return -1;
+    const int nnz = row_ptr[m];
+    const int mw = (m + 31) / 32, nw = (n + 31) / 32;
+
+    /* CSC edge lists: for VN j, the edge ids e (positions in col_idx) of its checks. */
+    int* vn_ptr = (int*)calloc((size_t)n + 1, sizeof(int));
+    int* vn_edges = (int*)malloc(sizeof(int) * (size_t)(nnz > 0 ? nnz : 1));
+    int* edge_row = (int*)malloc(sizeof(int) * (size_t)(nnz > 0 ? nnz : 1));
+    double* q = (double*)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+    double* r = (double*)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+    double* P = (double*)malloc(sizeof(double) * (size_t)n);
+    double* prior = (double*)malloc(sizeof(double) * (size_t)n);
+    double* gain = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+    int* ehat = (int*)malloc(sizeof(int) * (size_t)n);
+    int* sres = (int*)malloc(sizeof(int) * (size_t)(m > 0 ? m : 1));
+    int* fill = (int*)calloc((size_t)n + 1, sizeof(int));
+    int rc = 0;
+    if (!vn_ptr || !vn_edges || !edge_row || !q || !r || !P || !prior || !gain || !ehat || !sres || !fill) {
+        rc = -1;
+        goto done;
+    }
+    for (int i = 0; i < m; ++i) {
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            const int j = col_idx[e];
+            if (j < 0 || j >= n) { rc = -1; goto done; }
+            edge_row[e] = i;
+            vn_ptr[j + 1]++;
+        }
+    }
+    for (int j = 0; j < n; ++j) vn_ptr[j + 1] += vn_ptr[j];
+    for (int e = 0; e < nnz; ++e) {
+        const int j = col_idx[e];
+        vn_edges[vn_ptr[j] + fill[j]++] = e;
+    }
+
+    const int msfam = (mode != ORACLE_MODE_BP);
+    const int per_qubit = (flags & ORACLE_FLAG_L0_PER_QUBIT) != 0;
+    const int normalise = msfam && !per_qubit && !(flags & ORACLE_FLAG_NATURAL_UNITS);
+    const int early_stop = !(flags & ORACLE_FLAG_NO_EARLY_STOP);
+
+    for (int64_t s = 0; s < shots; ++s) {
+        const uint32_t* sy = syn + (size_t)s * mw;
+        uint32_t* eo = err + (size_t)s * nw;
+        double* tr = trace ? trace + (size_t)s * (size_t)(max_iter + 1) * (size_t)n : NULL;
+
+        /* prior L0_j in the units the decoder runs in */
+        for (int j = 0; j < n; ++j) {
+            double l0 = per_qubit ? L0[j] : L0[s];
+            if (normalise) l0 = (l0 > 0.0) ? 1.0 : ((l0 < 0.0) ? -1.0 : 0.0);
+            prior[j] = l0;
+        }
+        /* Init (Sec. II): L_{j->i} = L0, CN->VN messages zero. */
+        for (int e = 0; e < nnz; ++e) { q[e] = prior[col_idx[e]]; r[e] = 0.0; }
+
+        int l = 0;
+        for (;;) {
+            /* (i) posterior, hard decision, residual syndrome (Eq. 1) */
+            for (int j = 0; j < n; ++j) {
+                double acc = prior[j];
+                for (int t = vn_ptr[j]; t < vn_ptr[j + 1]; ++t) acc += r[vn_edges[t]];
+                P[j] = acc;
+                ehat[j] = (acc < 0.0) ? 1 : 0;
+            }
+            if (tr) memcpy(tr + (size_t)l * n, P, sizeof(double) * (size_t)n);
+            int unsat = 0;
+            for (int i = 0; i < m; ++i) {
+                int x = bit_of(sy, i);
+                for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) x ^= ehat[col_idx[e]];
+                sres[i] = x;
+                unsat += x;
+            }
+            /* (ii) early termination / iteration budget */
+            if (unsat == 0 && early_stop) { conv[s] = 1; iters[s] = l; break; }
+            if (l == max_iter) { conv[s] = (unsat == 0); iters[s] = max_iter; break; }
+
+            /* (iii) syndrome ratio (Eq. 6) and per-CN gain (Eq. 7) */
+            const double gamma = (m > 0) ? (double)unsat / (double)m : 0.0;
+            for (int i = 0; i < m; ++i) {
+                if (mode == ORACLE_MODE_MS) gain[i] = 1.0;
+                else if (mode == ORACLE_MODE_SMS) gain[i] = alpha;
+                else if (mode == ORACLE_MODE_SAGMS)
+                    gain[i] = (alpha_max - (alpha_max - alpha_min) * gamma) * (sres[i] ? eta_unsat : 1.0);
+                else gain[i] = 1.0;
+            }
+
+            /* (iv) CN update, leave-one-out over M(i)\j (Eqs. 3, 4, 8) */
+            for (int i = 0; i < m; ++i) {
+                for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+                    int neg = bit_of(sy, i);
+                    double mn = INFINITY, prod = 1.0;
+                    for (int f = row_ptr[i]; f < row_ptr[i + 1]; ++f) {
+                        if (f == e) continue;
+                        if (q[f] < 0.0) neg ^= 1;
+                        const double a = fabs(q[f]);
+                        if (msfam) { if (a < mn) mn = a; }
+                        else prod *= tanh(0.5 * a);
+                    }
+                    double mag;
+                    if (msfam) {
+                        mag = gain[i] * mn;
+                        if (mag > MSFAM_CLIP) mag = MSFAM_CLIP;
+                    } else {
+                        mag = (prod >= 1.0) ? INFINITY : 2.0 * atanh(prod);
+                        if (mag > BP_CLIP) mag = BP_CLIP;
+                    }
+                    r[e] = neg ? -mag : mag;
+                }
+            }
+            /* (v) VN update, leave-one-out over N(j)\i (Eq. 2) */
+            for (int j = 0; j < n; ++j) {
+                for (int t = vn_ptr[j]; t < vn_ptr[j + 1]; ++t) {
+                    const int e = vn_edges[t];
+                    double acc = prior[j];
+                    for (int u = vn_ptr[j]; u < vn_ptr[j + 1]; ++u)
+                        if (u != t) acc += r[vn_edges[u]];
+                    q[e] = acc;
+                }
+            }
+            ++l;
+        }
+        for (int k = 0; k < nw; ++k) eo[k] = 0u;
+        for (int j = 0; j < n; ++j)
+            if (ehat[j]) eo[j >> 5] |= 1u << (j & 31);
+    }
+
+done:
+    free(vn_ptr); free(vn_edges); free(edge_row); free(q); free(r); free(P); free(prior);
+    free(gain); free(ehat); free(sres); free(fill);
+    return rc;
+}
+
+/* Closed form of Eq. 9: alpha*(L0, dc) = 2 atanh(tanh(L0/2)^(dc-1)) / L0. */
+double oracle_alpha_star(double L0, int dc) {
+    return 2.0 * atanh(pow(tanh(0.5 * L0), (double)(dc - 1))) / L0;
+}
+
+/* First-order form of Eq. 9: 1 - ln(dc - 1) / L0. */
+double oracle_alpha_star_approx(double L0, int dc) {
+    return 1.0 - log((double)(dc - 1)) / L0;
+}
