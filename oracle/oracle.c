@@ -45,7 +45,9 @@
  *     normalised), BP outputs to |r| <= 23.718998 = ln(2e10), the cap implied
  *     by the 1e-10 guard of the paper's BP transfer-function plot (Fig. 1b);
  *   - degree-1 checks: the leave-one-out set is empty, so min = +inf
- *     (MS family) or prod = 1 (BP) and the output saturates at the clip.
+ *     (MS family) or prod = 1 (BP) and the output saturates at the clip;
+ *   - input validation (not part of the method): a non-finite prior marks the
+ *     shot invalid (e_hat = 0, conv = 0, iters = -1).
  */
 #include <math.h>
 #include <stdint.h>
@@ -129,6 +131,16 @@ int oracle_decode(int m, int n, const int32_t* row_ptr, const int32_t* col_idx,
         uint32_t* eo = err + (size_t)s * nw;
         double* tr = trace ? trace + (size_t)s * (size_t)(max_iter + 1) * (size_t)n : NULL;
 
+        /* A non-finite prior marks the shot invalid: e_hat = 0, conv = 0, iters = -1. */
+        int bad = 0;
+        for (int j = 0; j < (per_qubit ? n : 1); ++j)
+            if (!isfinite(per_qubit ? L0[j] : L0[s])) bad = 1;
+        if (bad) {
+            for (int k = 0; k < nw; ++k) eo[k] = 0u;
+            conv[s] = 0;
+            iters[s] = -1;
+            continue;
+        }
         /* prior L0_j in the units the decoder runs in */
         for (int j = 0; j < n; ++j) {
             double l0 = per_qubit ? L0[j] : L0[s];

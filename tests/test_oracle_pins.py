@@ -256,3 +256,12 @@ def test_ml_agreement_rate_on_tiny_loopy_code_is_reported():
         agree += int(np.array_equal(I.unpack_bits(r["err"], n)[0], best))
     print(f"SAGMS agreement with ML on a loopy n=14 code: {agree}/{trials}")
     assert agree > 0
+
+
+def test_non_finite_prior_marks_shot_invalid():
+    c = I.gb_code(63, 3)
+    _, syn = I.sample(c, 0.05, 3, seed=1)
+    r = oracle.decode_code(c, syn, np.array([np.nan, 2.0, np.inf]), mode=oracle.SAGMS, max_iter=10)
+    assert list(r["iters"][[0, 2]]) == [-1, -1] and not r["conv"][[0, 2]].any()
+    assert not r["err"][[0, 2]].any()
+    assert r["iters"][1] >= 0
