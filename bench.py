@@ -1,0 +1,336 @@
+#!/usr/bin/env python3
+"""Benchmark: batched SAGMS decoding of the n = 2046 generalized-bicycle code on GB300.
+
+One step = one pass of the whole decode path (gain, check-node, variable-node, decision,
+residual syndrome and early stop for every shot, up to 100 iterations) over one batch of
+1e7 seeded synthetic shots, already resident in HBM: GB l=1023, w=5 (n=2046, m=1023,
+d_c=10, d_v=5, 10230 edges), iid Z flips with p interleaved over {0.005, 0.01, 0.02},
+L0 = ln((1-p)/p), SAGMS alpha_min=0.30, alpha_max=0.50, eta=1.10, max_iter=100.
+
+Prints one JSON line (rank 0).  Under torchrun each rank decodes its own 1e7-shot shard on
+its own GPU (weak scaling, no data-path collective); the timed region is bracketed by a
+barrier and a device synchronize, and the slowest rank's time is reported.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this build) on the host
+cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SAGMS shots/s (n=2046 GB, 100 it) & serving p99 us vs plain launch, FER=oracle"
+UNIT = "shots/s"
+L, W = 1023, 5
+P_VALUES = [0.005, 0.01, 0.02]
+SAGMS_KW = dict(alpha_min=0.30, alpha_max=0.50, eta_unsat=1.10)
+SMS_ALPHA = 0.75
+MAX_ITER = 100
+NOISE_SEED = 20260513
+PROFILE = os.path.join(ROOT, "profiles", "decode_kernel_gb1023_sagms.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_2605_10433_gb300", "csrc", "decode_kernel.cuh")
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def workload_name(shots):
+    return (f"GB l={L} w={W} (n={2 * L}, m={L}, d_c={2 * W}, d_v={W}, {2 * W * L} edges), {shots:.0e} shots/GPU, "
+            f"iid Z flips p in {{0.005,0.01,0.02}} interleaved, L0=ln((1-p)/p), SAGMS a_min=0.30 a_max=0.50 "
+            f"eta=1.10, max_iter={MAX_ITER}")
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms during the timed region."""
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names[1:], parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def profile_traffic(shots_per_launch):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    kernel source (else None)."""
+    try:
+        txt = open(PROFILE).read()
+        sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+        m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+        m_b = re.search(r"dram_bytes_per_shot:\s*([0-9.eE+-]+)", txt)
+        if not m_sha or not m_b or m_sha.group(1) != sha:
+            return None
+        return float(m_b.group(1)) * shots_per_launch
+    except Exception:
+        return None
+
+
+def cpu_oracle_sample(code, syn, L0, shots, threads):
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.decode_code(code, syn[:shots], L0[:shots].astype(np.float64), mode=oracle.SAGMS,
+                           max_iter=MAX_ITER, threads=threads, **SAGMS_KW)
+    dt = time.perf_counter() - t0
+    return r, dt
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores, on bounded samples of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2605_10433_gb300 import inputs as I
+    import oracle
+    oracle.build_lib()
+    code = I.gb_code(L, W)
+    threads = os.cpu_count() or 1
+    sample = args.ref_sample
+    _, syn, L0, _ = I.workload(code, P_VALUES, sample * (args.steps + args.warmup), seed=NOISE_SEED)
+    times = []
+    for k in range(args.warmup + args.steps):
+        sl = slice(k * sample, (k + 1) * sample)
+        _, dt = cpu_oracle_sample(code, syn[sl], L0[sl], sample, threads)
+        if k >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = sample * args.steps / total
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(sample) + f" (bounded sample of {sample} shots per step)",
+                       "code_seed": code.seed, "a": list(code.a), "b": list(code.b), "k": code.k,
+                       "l2": "CPU run"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{sample} shots per step x {args.steps} steps of the same workload"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--shots", type=int, default=10_000_000)
+    ap.add_argument("--ref-sample", type=int, default=4000)
+    ap.add_argument("--cpu-sample", type=int, default=16000)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--mode-steps", type=int, default=3)
+    ap.add_argument("--no-extras", action="store_true", help="skip the SMS / MS lines and the CPU baseline")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2605_10433_gb300 as S
+    from paper_2605_10433_gb300 import inputs as I
+    from paper_2605_10433_gb300 import roofline
+    from paper_2605_10433_gb300.stats import wilson_interval
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    code = I.gb_code(L, W)
+    shots = args.shots
+    t0 = time.perf_counter()
+    _, syn, L0, qv = I.workload(code, P_VALUES, shots, seed=NOISE_SEED, shot0=rank * shots)
+    gen_s = time.perf_counter() - t0
+    dcode = S.DeviceCode.from_code(code)
+    d_syn = torch.from_numpy(syn.view(np.int32)).cuda()
+    d_L0 = torch.from_numpy(L0).cuda()
+    err = torch.empty((shots, code.nw), dtype=torch.int32, device="cuda")
+    conv = torch.empty((shots,), dtype=torch.uint8, device="cuda")
+    iters = torch.empty((shots,), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    sagms = S.Params(mode="sagms", max_iter=MAX_ITER, **SAGMS_KW)
+
+    def step(p):
+        S.decode(dcode, d_syn, d_L0, p, out=(err, conv, iters), stream=stream)
+
+    def timed(p, warm, steps, clocks=False):
+        for _ in range(warm):
+            step(p)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler() if clocks else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.5)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step(p)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        clk = sampler.stop() if sampler else None
+        barrier()
+        if dist is not None:
+            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, clk
+
+    ms, clk = timed(sagms, args.warmup, args.steps, clocks=True)
+    it_host = iters.cpu().numpy()
+    conv_host = conv.cpu().numpy()
+    value = shots * world * args.steps / (ms / 1e3)
+    ms_step = ms / args.steps
+
+    # roofline: algorithmic ops of this launch over the launch's average duration
+    props = torch.cuda.get_device_properties(local)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0)
+    ops_it = roofline.ops_per_iteration("sagms", code.row_ptr, code.col_idx, code.n)
+    ops_launch = float(it_host.astype(np.int64).sum()) * ops_it
+    achieved = ops_launch / (ms_step / 1e3)
+    peak = roofline.alu_peak_ops(props.multi_processor_count, sm_max)
+    traffic = profile_traffic(shots)
+    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "note": (f"ops = sum over shots of iters x {ops_it} per iteration (Eq. 15 / Table I CN cost + VN sum, "
+                     f"decision, residual XOR, popcount); peak = {props.multi_processor_count} SMs x 128 lanes x "
+                     f"{sm_max:.0f} MHz; HBM bound {roofline.hbm_bytes_per_shot(code.m, code.n)} B/shot at "
+                     f"{peaks.get('hbm_gbs', 'n/a')} GB/s is "
+                     f"{(peaks.get('hbm_gbs', 6793.1) * 1e9 / roofline.hbm_bytes_per_shot(code.m, code.n)):.3g} shots/s")}
+
+    fer = {}
+    for k, p in enumerate(P_VALUES):
+        sel = np.arange(shots) % len(P_VALUES) == k
+        f = int((conv_host[sel] == 0).sum())
+        lo, hi = wilson_interval(f, int(sel.sum()))
+        fer[str(p)] = {"fer_syn": f / sel.sum(), "wilson95": [lo, hi], "mean_iters": float(it_host[sel].mean())}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": workload_name(shots), "global_batch": shots * world, "code_seed": code.seed,
+                      "a": list(code.a), "b": list(code.b), "k": code.k,
+                      "l2": f"inputs larger than L2: {syn.nbytes / 1e9:.2f} GB syndromes per GPU",
+                      "parallelism": f"shot-sharded x{world}"},
+           "gpu_launches": args.steps, "mean_iters": float(it_host.mean()), "fer": fer, "roofline": roof,
+           "clocks": clk, "input_gen_s": gen_s}
+
+    if not args.no_extras:
+        modes = {}
+        for name, p in (("sms", S.Params(mode="sms", alpha=SMS_ALPHA, max_iter=MAX_ITER)),
+                        ("ms", S.Params(mode="ms", max_iter=MAX_ITER))):
+            m_ms, _ = timed(p, 1, args.mode_steps)
+            cv = conv.cpu().numpy()
+            modes[name] = {"shots_per_s": shots * world * args.mode_steps / (m_ms / 1e3),
+                           "mean_iters": float(iters.cpu().numpy().mean()), "fer_syn": float((cv == 0).mean())}
+        out["modes"] = modes
+        step(sagms)
+        torch.cuda.synchronize()
+
+    # e2e: the C-ABI host entry point, host<->device copies inside the timed region
+    h_syn = torch.from_numpy(syn.view(np.int32)).pin_memory()
+    h_L0 = torch.from_numpy(L0).pin_memory()
+    h_err = torch.empty((shots, code.nw), dtype=torch.int32).pin_memory()
+    h_conv = torch.empty((shots,), dtype=torch.uint8).pin_memory()
+    h_it = torch.empty((shots,), dtype=torch.int32).pin_memory()
+    S.decode_host(dcode, h_syn, h_L0, sagms, out=(h_err, h_conv, h_it))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        S.decode_host(dcode, h_syn, h_L0, sagms, out=(h_err, h_conv, h_it))
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    assert np.array_equal(h_it.numpy(), it_host), "host path disagrees with the device path"
+    out["e2e"] = {"value": shots * world * args.e2e_steps / e2e_s, "unit": UNIT,
+                  "h2d_bytes_per_step": int(syn.nbytes + L0.nbytes),
+                  "d2h_bytes_per_step": int(shots * code.nw * 4 + shots + shots * 4),
+                  "api": "sagms_decode_host (pinned host buffers, chunked copy/compute overlap)"}
+
+    if rank == 0 and world == 1 and not args.no_extras:
+        threads = os.cpu_count() or 1
+        r, dt = cpu_oracle_sample(code, syn, L0, args.cpu_sample, threads)
+        g_err = err.cpu().numpy().view(np.uint32)[:args.cpu_sample]
+        same = ((g_err == r["err"]).all(axis=1) & (it_host[:args.cpu_sample] == r["iters"])).mean()
+        out["cpu_baseline"] = {"value": args.cpu_sample / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+                               "sample": f"first {args.cpu_sample} shots of the same batch (FP64 C oracle, "
+                                         f"{threads} threads)",
+                               "oracle_fer_syn": float((r["conv"] == 0).mean()), "gpu_oracle_identical": same}
+    if rank == 0:
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

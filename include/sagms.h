@@ -1,0 +1,171 @@
+/*
+ * sagms.h -- C ABI of libsagms.so, a GB300 (sm_103a) batched syndrome decoder for
+ * quantum LDPC codes: plain Min-Sum (MS), fixed-scale Min-Sum (SMS), syndrome-adaptive
+ * gain Min-Sum (SAGMS) and the tanh-rule belief-propagation reference (BP).
+ *
+ * Method: "Syndrome Adaptive Gain Control for Min-Sum Decoding of Quantum LDPC Codes"
+ * (arXiv 2605.10433).  Each call decodes a batch of independent shots: for every shot,
+ * the flooding-schedule iteration of Algorithm 1 on the Tanner graph of a binary
+ * parity-check matrix H (m checks, n qubits), with early termination once the residual
+ * syndrome of Eq. 1 is zero.
+ *
+ * Conventions for every entry point:
+ *   - Return value: SAGMS_OK (0) or a negative SAGMS_ERR_* code; the message of the
+ *     last failure on the calling thread is sagms_last_error_string().
+ *   - Host arrays passed in are read during the call and never kept; the caller keeps
+ *     ownership.  Device pointers are caller-owned device memory (any allocator); the
+ *     library never frees them and never synchronises the caller's stream unless the
+ *     entry point says so.
+ *   - Packed bit layout: bit k of a pattern is bit (k % 32) of uint32 word k / 32.
+ *     A syndrome occupies ceil(m/32) words per shot, an error estimate ceil(n/32).
+ *   - A code handle is immutable after sagms_load_code and may be used from several
+ *     host threads and streams at once.
+ */
+#ifndef SAGMS_H
+#define SAGMS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Decoder forms (Sec. II and III). */
+enum {
+    SAGMS_MS = 0,    /* Eq. 4: CN output = (-1)^{s_i} prod sgn * min |.| */
+    SAGMS_SMS = 1,   /* Eq. 4 times a fixed alpha in (0, 1] */
+    SAGMS_SAGMS = 2, /* Eq. 8 with the per-shot, per-check gain of Eq. 7 */
+    SAGMS_BP = 3     /* Eq. 3, the phi-domain (tanh) rule */
+};
+
+/* Flags of sagms_params.flags. */
+enum {
+    /* d_L0 holds n per-qubit priors shared by all shots (LLR units) instead of one
+     * prior per shot.  Without it the MS family runs in L0-normalised units. */
+    SAGMS_FLAG_L0_PER_QUBIT = 1u,
+    /* Run exactly max_iter rounds even after the residual syndrome reaches zero. */
+    SAGMS_FLAG_NO_EARLY_STOP = 2u
+};
+
+/* Status codes. */
+enum {
+    SAGMS_OK = 0,
+    SAGMS_ERR_ARG = -1,     /* null pointer, negative size, unknown flag */
+    SAGMS_ERR_CSR = -2,     /* malformed CSR (row_ptr not monotone, column out of range, duplicate) */
+    SAGMS_ERR_DEGREE = -3,  /* check degree > SAGMS_MAX_DC or qubit degree > SAGMS_MAX_DV */
+    SAGMS_ERR_PARAM = -4,   /* parameters outside the ranges of Eq. 7 and Sec. II */
+    SAGMS_ERR_OOM = -5,     /* device allocation failed */
+    SAGMS_ERR_CUDA = -6,    /* a CUDA runtime call failed (no device, launch failure, ...) */
+    SAGMS_ERR_TIMEOUT = -7, /* a bounded wait ran out */
+    SAGMS_ERR_BUSY = -8,    /* resource temporarily unavailable */
+    SAGMS_ERR_SIZE = -9     /* code too large for one CTA's shared memory / thread block */
+};
+
+#define SAGMS_MAX_DC 32     /* largest check degree |M(i)| */
+#define SAGMS_MAX_DV 16     /* largest qubit degree |N(j)| */
+#define SAGMS_MAX_M 1024    /* one thread per check within a CTA */
+
+typedef struct sagms_code sagms_code; /* opaque, library-owned, immutable after load */
+
+/*
+ * Decoder parameters.
+ *   mode:       SAGMS_MS / SAGMS_SMS / SAGMS_SAGMS / SAGMS_BP.
+ *   alpha:      SMS scale, 0 < alpha <= 1 (Eq. 4 and the SMS rule of Sec. II).
+ *   alpha_min, alpha_max, eta_unsat: SAGMS gain of Eq. 7, with
+ *               0 < alpha_min <= alpha_max <= 1, eta_unsat >= 1 and
+ *               alpha_max * eta_unsat <= 1 (the stability constraint of Sec. III-A).
+ *               eta_unsat = 0 selects the default 1.10 used in the paper's experiments.
+ *   max_iter:   message-passing rounds, 0 <= max_iter <= 100000 (l_max of Algorithm 1).
+ *   flags:      SAGMS_FLAG_* bits.
+ * Fields a mode does not use are ignored.
+ */
+typedef struct {
+    int32_t mode;
+    float alpha;
+    float alpha_min;
+    float alpha_max;
+    float eta_unsat;
+    int32_t max_iter;
+    uint32_t flags;
+} sagms_params;
+
+/*
+ * Load a parity-check matrix (Tanner graph sets M(i), N(j) of Sec. II) onto the current
+ * CUDA device.  row_ptr[m+1] and col_idx[nnz] are host arrays in CSR form; the order of
+ * columns inside a row is kept as the edge order of that check (no sorting needed).
+ * Requires 1 <= m <= SAGMS_MAX_M, n >= 1, check degrees <= SAGMS_MAX_DC and qubit
+ * degrees <= SAGMS_MAX_DV.  On success *out owns device memory until sagms_free_code.
+ * Errors: ERR_ARG, ERR_CSR, ERR_DEGREE, ERR_SIZE, ERR_OOM, ERR_CUDA.
+ */
+int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr,
+                    const int32_t* col_idx, sagms_code** out);
+
+/* Release a code handle (device memory freed synchronously).  NULL is ignored. */
+void sagms_free_code(sagms_code* code);
+
+/* Shape of a loaded code: any output pointer may be NULL. */
+int sagms_code_info(const sagms_code* code, int32_t* m, int32_t* n, int32_t* dc_max, int32_t* dv_max);
+
+/* Validate a parameter block without decoding.  Returns SAGMS_OK or SAGMS_ERR_PARAM /
+ * SAGMS_ERR_ARG.  Runs on the host only (no CUDA call). */
+int sagms_check_params(const sagms_params* params);
+
+/*
+ * Decode `shots` syndromes (Algorithm 1, flooding schedule, per-shot early stop).
+ *   d_syn   [shots][ceil(m/32)] device, packed input syndromes s.
+ *   d_L0    device: [shots] per-shot channel prior L0 = ln((1-q)/q), or [n] per-qubit
+ *           priors with SAGMS_FLAG_L0_PER_QUBIT.  A non-finite per-shot prior marks that
+ *           shot invalid (err = 0, conv = 0, iters = -1).
+ *   d_err   [shots][ceil(n/32)] device, out: packed hard decision e_hat (bit j = 1 iff the
+ *           posterior L0_j + sum_{i in N(j)} L_{i->j} is negative).
+ *   d_conv  [shots] device, out: 1 if the residual syndrome s XOR H e_hat is zero on return.
+ *   d_iters [shots] device, out: message-passing rounds completed when the residual first
+ *           became zero (0 for a zero syndrome); max_iter when it never did.
+ *   stream  cudaStream_t to launch on (NULL = legacy default stream).
+ * Asynchronous: results are valid once `stream` has reached this point.  shots == 0 is
+ * a no-op.  Errors: ERR_ARG, ERR_PARAM, ERR_SIZE, ERR_OOM, ERR_CUDA.
+ */
+int sagms_decode(const sagms_code* code, const sagms_params* params, int64_t shots,
+                 const uint32_t* d_syn, const float* d_L0, uint32_t* d_err, uint8_t* d_conv,
+                 int32_t* d_iters, void* stream);
+
+/*
+ * sagms_decode plus a posterior trace for parity checking: d_trace is device memory of
+ * [shots][max_iter+1][n] floats; row l receives the posteriors P_j evaluated at the l-th
+ * check of Algorithm 1 (l = 0: the prior), in the units the decoder runs in (L0-normalised
+ * for the MS family with per-shot priors, LLR units otherwise).  Rows after the shot's
+ * last check are left unwritten.
+ */
+int sagms_decode_trace(const sagms_code* code, const sagms_params* params, int64_t shots,
+                       const uint32_t* d_syn, const float* d_L0, uint32_t* d_err, uint8_t* d_conv,
+                       int32_t* d_iters, float* d_trace, void* stream);
+
+/*
+ * End-to-end decode from HOST buffers: copies syndromes and priors to the device in
+ * chunks, decodes, and copies the results back, overlapping the copies of one chunk with
+ * the decoding of another on library-owned streams.  Host arrays have the layouts of
+ * sagms_decode (h_L0: [shots], or [n] with SAGMS_FLAG_L0_PER_QUBIT); page-locked host
+ * memory gives the fastest copies.  Synchronous: returns after all results are in host
+ * memory.  Device buffers are allocated from the stream-ordered pool and released before
+ * returning.  Errors: as sagms_decode.
+ */
+int sagms_decode_host(const sagms_code* code, const sagms_params* params, int64_t shots,
+                      const uint32_t* h_syn, const float* h_L0, uint32_t* h_err, uint8_t* h_conv,
+                      int32_t* h_iters);
+
+/* Eq. 9: alpha*(L0, d_c) = 2 atanh(tanh(L0/2)^(d_c - 1)) / L0, the SMS scale matching one
+ * BP CN update under uniform inputs (Remark 1).  Returns NaN for L0 <= 0 or d_c < 2. */
+double sagms_alpha_star(double L0, int32_t dc);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* sagms_last_error_string(void);
+
+/* Library version and build constants (clip levels, limits), human-readable. */
+const char* sagms_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SAGMS_H */

@@ -1,0 +1,131 @@
+"""GB300-native batched SAGMS / SMS / MS / BP syndrome decoding of quantum LDPC codes.
+
+The decoder runs in ``libsagms.so`` (hand-written CUDA for sm_103a, C ABI in
+``include/sagms.h``).  This package adds the thin Python layer: ``_native`` binds the C
+entry points by name, and :class:`DeviceCode` / :func:`decode` pass PyTorch tensors (device
+memory and streams only) to them.  ``inputs`` builds seeded codes and syndromes.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+MODES = {"ms": 0, "sms": 1, "sagms": 2, "bp": 3}
+FLAG_L0_PER_QUBIT = 1
+FLAG_NO_EARLY_STOP = 2
+
+
+@dataclass
+class Params:
+    """Decoder parameters (defaults: the SAGMS values of the paper's experiments, Sec. V-B)."""
+    mode: str = "sagms"
+    alpha: float = 0.75
+    alpha_min: float = 0.30
+    alpha_max: float = 0.50
+    eta_unsat: float = 1.10
+    max_iter: int = 100
+    flags: int = 0
+
+    def to_c(self):
+        from . import _native
+        return _native.sagms_params(MODES[self.mode] if isinstance(self.mode, str) else int(self.mode),
+                                    self.alpha, self.alpha_min, self.alpha_max, self.eta_unsat,
+                                    self.max_iter, self.flags)
+
+
+class DeviceCode:
+    """A parity-check matrix loaded on the current CUDA device (owns the C handle)."""
+
+    def __init__(self, m, n, row_ptr, col_idx):
+        from . import _native
+        self._native = _native
+        self.m, self.n = int(m), int(n)
+        self.handle = _native.sagms_load_code(m, n, row_ptr, col_idx)
+        _, _, self.dc_max, self.dv_max = _native.sagms_code_info(self.handle)
+
+    @classmethod
+    def from_code(cls, code):
+        return cls(code.m, code.n, code.row_ptr, code.col_idx)
+
+    @property
+    def mw(self):
+        return (self.m + 31) // 32
+
+    @property
+    def nw(self):
+        return (self.n + 31) // 32
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._native.sagms_free_code(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes_void(stream.cuda_stream)
+
+
+def ctypes_void(x):
+    import ctypes
+    return ctypes.c_void_p(int(x))
+
+
+def decode(code: DeviceCode, syn, L0, params: Params | None = None, out=None, stream=None, trace=False):
+    """Decode packed syndromes on the GPU.
+
+    syn: int32 CUDA tensor [shots, ceil(m/32)] (uint32 bit patterns); L0: float32 CUDA tensor
+    [shots] (or [n] with FLAG_L0_PER_QUBIT).  Returns (err [shots, ceil(n/32)] int32,
+    conv [shots] uint8, iters [shots] int32[, trace [shots, max_iter+1, n] float32]).
+    Asynchronous on ``stream`` (default: torch's current stream)."""
+    import torch
+    from . import _native
+    params = params or Params()
+    shots = syn.shape[0]
+    dev = syn.device
+    assert syn.dtype == torch.int32 and syn.is_cuda and syn.is_contiguous()
+    assert L0.dtype == torch.float32 and L0.is_cuda and L0.is_contiguous()
+    if out is None:
+        err = torch.empty((shots, code.nw), dtype=torch.int32, device=dev)
+        conv = torch.empty((shots,), dtype=torch.uint8, device=dev)
+        iters = torch.empty((shots,), dtype=torch.int32, device=dev)
+    else:
+        err, conv, iters = out
+    p = params.to_c()
+    sp = _stream_ptr(stream)
+    if trace:
+        tr = torch.full((shots, params.max_iter + 1, code.n), float("nan"), dtype=torch.float32, device=dev)
+        _native.sagms_decode_trace(code.handle, p, shots, syn.data_ptr(), L0.data_ptr(), err.data_ptr(),
+                                   conv.data_ptr(), iters.data_ptr(), tr.data_ptr(), sp)
+        return err, conv, iters, tr
+    _native.sagms_decode(code.handle, p, shots, syn.data_ptr(), L0.data_ptr(), err.data_ptr(), conv.data_ptr(),
+                         iters.data_ptr(), sp)
+    return err, conv, iters
+
+
+def decode_host(code: DeviceCode, syn, L0, params: Params | None = None, out=None):
+    """End-to-end decode from host memory (numpy or CPU torch tensors, ideally pinned):
+    the library copies in, decodes and copies back with overlapped chunks.  Synchronous."""
+    import numpy as np
+    from . import _native
+    params = params or Params()
+    shots = syn.shape[0]
+
+    def ptr(a):
+        return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+
+    if out is None:
+        err = np.empty((shots, code.nw), dtype=np.uint32)
+        conv = np.empty((shots,), dtype=np.uint8)
+        iters = np.empty((shots,), dtype=np.int32)
+    else:
+        err, conv, iters = out
+    _native.sagms_decode_host(code.handle, params.to_c(), shots, ptr(syn), ptr(L0), ptr(err), ptr(conv), ptr(iters))
+    return err, conv, iters

@@ -1,0 +1,126 @@
+"""ctypes binding of libsagms.so (include/sagms.h): argument marshalling only.
+
+Every function named ``sagms_*`` here is the C entry point of the same name; the helpers
+below them take PyTorch tensors for device memory and streams and pass raw pointers.
+If the library has not been built, importing the binding raises instead of falling
+back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsagms.so")
+
+SAGMS_MS, SAGMS_SMS, SAGMS_SAGMS, SAGMS_BP = 0, 1, 2, 3
+SAGMS_FLAG_L0_PER_QUBIT = 1
+SAGMS_FLAG_NO_EARLY_STOP = 2
+SAGMS_OK = 0
+ERRORS = {-1: "ERR_ARG", -2: "ERR_CSR", -3: "ERR_DEGREE", -4: "ERR_PARAM", -5: "ERR_OOM", -6: "ERR_CUDA",
+          -7: "ERR_TIMEOUT", -8: "ERR_BUSY", -9: "ERR_SIZE"}
+MODES = {"ms": SAGMS_MS, "sms": SAGMS_SMS, "sagms": SAGMS_SAGMS, "bp": SAGMS_BP}
+
+
+class SagmsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class sagms_params(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("alpha", ctypes.c_float), ("alpha_min", ctypes.c_float),
+                ("alpha_max", ctypes.c_float), ("eta_unsat", ctypes.c_float), ("max_iter", ctypes.c_int32),
+                ("flags", ctypes.c_uint32)]
+
+
+def _load_library():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libsagms.so is not built ({LIB_PATH}); run __graft_entry__.build() "
+                          "or python -m paper_2605_10433_gb300.build")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    P = ctypes.POINTER
+    sig = {
+        "sagms_load_code": (ctypes.c_int, [i32, i32, i64, P(i32), P(i32), P(vp)]),
+        "sagms_free_code": (None, [vp]),
+        "sagms_code_info": (ctypes.c_int, [vp, P(i32), P(i32), P(i32), P(i32)]),
+        "sagms_check_params": (ctypes.c_int, [P(sagms_params)]),
+        "sagms_decode": (ctypes.c_int, [vp, P(sagms_params), i64, vp, vp, vp, vp, vp, vp]),
+        "sagms_decode_trace": (ctypes.c_int, [vp, P(sagms_params), i64, vp, vp, vp, vp, vp, vp, vp]),
+        "sagms_decode_host": (ctypes.c_int, [vp, P(sagms_params), i64, vp, vp, vp, vp, vp]),
+        "sagms_alpha_star": (ctypes.c_double, [ctypes.c_double, i32]),
+        "sagms_last_error_string": (ctypes.c_char_p, []),
+        "sagms_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load_library()
+
+
+def lib():
+    return _lib
+
+
+def _check(rc: int):
+    if rc != SAGMS_OK:
+        raise SagmsError(rc, _lib.sagms_last_error_string().decode())
+
+
+# ----------------------------------------------------------------------- C entry points
+def sagms_load_code(m, n, row_ptr, col_idx):
+    """Returns an opaque handle (int).  row_ptr / col_idx: int32 numpy arrays (host)."""
+    import numpy as np
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(_lib.sagms_load_code(int(m), int(n), int(rp[-1]) if len(rp) else 0,
+                                rp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                ci.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(h)))
+    return h.value
+
+
+def sagms_free_code(handle):
+    _lib.sagms_free_code(handle)
+
+
+def sagms_code_info(handle):
+    v = [ctypes.c_int32() for _ in range(4)]
+    _check(_lib.sagms_code_info(handle, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def sagms_check_params(params: sagms_params) -> int:
+    return _lib.sagms_check_params(ctypes.byref(params))
+
+
+def sagms_decode(handle, params, shots, syn_ptr, L0_ptr, err_ptr, conv_ptr, iters_ptr, stream_ptr):
+    _check(_lib.sagms_decode(handle, ctypes.byref(params), int(shots), syn_ptr, L0_ptr, err_ptr, conv_ptr,
+                             iters_ptr, stream_ptr))
+
+
+def sagms_decode_trace(handle, params, shots, syn_ptr, L0_ptr, err_ptr, conv_ptr, iters_ptr, trace_ptr, stream_ptr):
+    _check(_lib.sagms_decode_trace(handle, ctypes.byref(params), int(shots), syn_ptr, L0_ptr, err_ptr, conv_ptr,
+                                   iters_ptr, trace_ptr, stream_ptr))
+
+
+def sagms_decode_host(handle, params, shots, syn_ptr, L0_ptr, err_ptr, conv_ptr, iters_ptr):
+    _check(_lib.sagms_decode_host(handle, ctypes.byref(params), int(shots), syn_ptr, L0_ptr, err_ptr, conv_ptr,
+                                  iters_ptr))
+
+
+def sagms_alpha_star(L0: float, dc: int) -> float:
+    return _lib.sagms_alpha_star(float(L0), int(dc))
+
+
+def sagms_version() -> str:
+    return _lib.sagms_version().decode()
+
+
+def sagms_last_error_string() -> str:
+    return _lib.sagms_last_error_string().decode()

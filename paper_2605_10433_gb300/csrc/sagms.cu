@@ -1,0 +1,355 @@
+// libsagms.so: C ABI (include/sagms.h) around the batched decoder kernels.
+//
+// Host responsibilities: validate the CSR matrix and the parameters, lay the Tanner graph
+// out for the kernel (slot-major u16 index arrays, padded to the variant's degrees), pick
+// the kernel variant and grid, and launch on the caller's stream.  Every step of the
+// decode itself runs in decode_kernel.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/sagms.h"
+#include "decode_kernel.cuh"
+
+using namespace sagms;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    cudaGetLastError();  // clear a sticky launch error so later calls are not poisoned
+    return fail(e == cudaErrorMemoryAllocation ? SAGMS_ERR_OOM : SAGMS_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+// Kernel variants: (padded check degree, padded qubit degree).  A code uses the first
+// variant whose degrees cover its largest check and qubit degree.
+struct Variant { int dc, dv; };
+constexpr Variant kVariants[] = {{4, 2}, {6, 3}, {8, 4}, {10, 5}, {12, 6}, {16, 8}, {32, 16}};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+using KernelFn = void (*)(const DecodeArgs);
+
+template <int DC, int DV>
+KernelFn pick(bool bp) { return bp ? decode_kernel<DC, DV, true> : decode_kernel<DC, DV, false>; }
+
+KernelFn kernel_for(int variant, bool bp) {
+    switch (variant) {
+        case 0: return pick<4, 2>(bp);
+        case 1: return pick<6, 3>(bp);
+        case 2: return pick<8, 4>(bp);
+        case 3: return pick<10, 5>(bp);
+        case 4: return pick<12, 6>(bp);
+        case 5: return pick<16, 8>(bp);
+        default: return pick<32, 16>(bp);
+    }
+}
+
+int round_up(int x, int k) { return (x + k - 1) / k * k; }
+
+}  // namespace
+
+struct sagms_code {
+    int m, n, nnz;
+    int dc_max, dv_max;
+    int variant, DC, DV;
+    int Mp, Np;
+    int device;
+    uint16_t* d_colT;
+    uint16_t* d_vneT;
+};
+
+extern "C" {
+
+const char* sagms_last_error_string(void) { return g_last_error.c_str(); }
+
+const char* sagms_version(void) {
+    static char buf[256];
+    static std::once_flag once;
+    std::call_once(once, [] {
+        snprintf(buf, sizeof(buf),
+                 "libsagms 0.1 sm_103a; msfam_clip=%g bp_clip=%g max_dc=%d max_dv=%d max_m=%d",
+                 (double)kMsFamClip, (double)kBpClip, SAGMS_MAX_DC, SAGMS_MAX_DV, SAGMS_MAX_M);
+    });
+    return buf;
+}
+
+double sagms_alpha_star(double L0, int32_t dc) {
+    if (!(L0 > 0.0) || dc < 2) return NAN;
+    return 2.0 * std::atanh(std::pow(std::tanh(0.5 * L0), (double)(dc - 1))) / L0;
+}
+
+int sagms_check_params(const sagms_params* p) {
+    if (!p) return fail(SAGMS_ERR_ARG, "params is NULL");
+    if (p->flags & ~(uint32_t)(SAGMS_FLAG_L0_PER_QUBIT | SAGMS_FLAG_NO_EARLY_STOP))
+        return fail(SAGMS_ERR_ARG, "unknown flag bits 0x%x", p->flags);
+    if (p->max_iter < 0 || p->max_iter > 100000)
+        return fail(SAGMS_ERR_PARAM, "max_iter %d outside [0, 100000]", p->max_iter);
+    switch (p->mode) {
+        case SAGMS_MS:
+        case SAGMS_BP:
+            return SAGMS_OK;
+        case SAGMS_SMS:
+            if (!(p->alpha > 0.0f && p->alpha <= 1.0f))
+                return fail(SAGMS_ERR_PARAM, "SMS alpha %g outside (0, 1]", (double)p->alpha);
+            return SAGMS_OK;
+        case SAGMS_SAGMS: {
+            const float eta = (p->eta_unsat == 0.0f) ? 1.10f : p->eta_unsat;
+            if (!(p->alpha_min > 0.0f && p->alpha_min <= p->alpha_max && p->alpha_max <= 1.0f))
+                return fail(SAGMS_ERR_PARAM, "need 0 < alpha_min <= alpha_max <= 1 (got %g, %g)",
+                            (double)p->alpha_min, (double)p->alpha_max);
+            if (!(eta >= 1.0f) || !std::isfinite(eta))
+                return fail(SAGMS_ERR_PARAM, "eta_unsat %g must be >= 1", (double)eta);
+            if ((double)p->alpha_max * (double)eta > 1.0 + 1e-6)
+                return fail(SAGMS_ERR_PARAM, "stability constraint alpha_max * eta_unsat <= 1 violated (%g)",
+                            (double)p->alpha_max * (double)eta);
+            return SAGMS_OK;
+        }
+        default:
+            return fail(SAGMS_ERR_PARAM, "unknown mode %d", p->mode);
+    }
+}
+
+int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+                    sagms_code** out) {
+    if (!out) return fail(SAGMS_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!row_ptr || (nnz > 0 && !col_idx)) return fail(SAGMS_ERR_ARG, "row_ptr/col_idx is NULL");
+    if (m < 1 || n < 1 || nnz < 0) return fail(SAGMS_ERR_ARG, "need m >= 1, n >= 1, nnz >= 0");
+    if (m > SAGMS_MAX_M) return fail(SAGMS_ERR_SIZE, "m = %d exceeds %d checks", m, SAGMS_MAX_M);
+    if (n > 60000) return fail(SAGMS_ERR_SIZE, "n = %d too large", n);
+    if (row_ptr[0] != 0 || row_ptr[m] != nnz) return fail(SAGMS_ERR_CSR, "row_ptr[0] must be 0 and row_ptr[m] == nnz");
+    int dc_max = 0;
+    std::vector<int> deg_v(n, 0);
+    std::vector<int> seen(n, -1);
+    for (int i = 0; i < m; ++i) {
+        if (row_ptr[i + 1] < row_ptr[i]) return fail(SAGMS_ERR_CSR, "row_ptr not monotone at row %d", i);
+        const int d = row_ptr[i + 1] - row_ptr[i];
+        dc_max = std::max(dc_max, d);
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            const int j = col_idx[e];
+            if (j < 0 || j >= n) return fail(SAGMS_ERR_CSR, "column %d out of range in row %d", j, i);
+            if (seen[j] == i) return fail(SAGMS_ERR_CSR, "duplicate column %d in row %d", j, i);
+            seen[j] = i;
+            deg_v[j]++;
+        }
+    }
+    const int dv_max = *std::max_element(deg_v.begin(), deg_v.end());
+    if (dc_max > SAGMS_MAX_DC || dv_max > SAGMS_MAX_DV)
+        return fail(SAGMS_ERR_DEGREE, "degrees dc=%d dv=%d exceed limits %d/%d", dc_max, dv_max, SAGMS_MAX_DC,
+                    SAGMS_MAX_DV);
+    int variant = kNumVariants - 1;
+    for (int v = 0; v < kNumVariants; ++v)
+        if (kVariants[v].dc >= dc_max && kVariants[v].dv >= dv_max) { variant = v; break; }
+    const int DC = kVariants[variant].dc, DV = kVariants[variant].dv;
+    const int Mp = round_up(m, 32);
+    const int Np = round_up(n + 1, 32);
+    if ((long long)DC * Mp + 1 > 65535) return fail(SAGMS_ERR_SIZE, "edge slots exceed 16-bit indexing");
+
+    // Slot-major layouts.  colT[j*Mp + i] = column of the j-th edge of check i (n = padding).
+    std::vector<uint16_t> colT((size_t)DC * Mp, (uint16_t)n);
+    for (int i = 0; i < m; ++i)
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+            colT[(size_t)(e - row_ptr[i]) * Mp + i] = (uint16_t)col_idx[e];
+    // vneT[q*Np + c] = slot position of the q-th edge of qubit c, edges ordered by slot index j
+    // (for circulant codes consecutive qubits then touch consecutive positions).
+    std::vector<std::vector<std::pair<int, int>>> vedges(n);
+    for (int i = 0; i < m; ++i)
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) vedges[col_idx[e]].push_back({e - row_ptr[i], i});
+    std::vector<uint16_t> vneT((size_t)DV * Np, (uint16_t)(DC * Mp));
+    for (int c = 0; c < n; ++c) {
+        auto& ve = vedges[c];
+        std::sort(ve.begin(), ve.end());
+        for (size_t q = 0; q < ve.size(); ++q) vneT[q * Np + c] = (uint16_t)(ve[q].first * Mp + ve[q].second);
+    }
+
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
+    sagms_code* code = new sagms_code();
+    code->m = m; code->n = n; code->nnz = (int)nnz;
+    code->dc_max = dc_max; code->dv_max = dv_max;
+    code->variant = variant; code->DC = DC; code->DV = DV;
+    code->Mp = Mp; code->Np = Np; code->device = dev;
+    code->d_colT = nullptr; code->d_vneT = nullptr;
+    ce = cudaMalloc(&code->d_colT, colT.size() * sizeof(uint16_t));
+    if (ce == cudaSuccess) ce = cudaMalloc(&code->d_vneT, vneT.size() * sizeof(uint16_t));
+    if (ce == cudaSuccess) ce = cudaMemcpy(code->d_colT, colT.data(), colT.size() * 2, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(code->d_vneT, vneT.data(), vneT.size() * 2, cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) {
+        cudaFree(code->d_colT);
+        cudaFree(code->d_vneT);
+        delete code;
+        return cuda_fail(ce, "sagms_load_code upload");
+    }
+    *out = code;
+    return SAGMS_OK;
+}
+
+void sagms_free_code(sagms_code* code) {
+    if (!code) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != code->device) cudaSetDevice(code->device);
+    cudaFree(code->d_colT);
+    cudaFree(code->d_vneT);
+    if (prev >= 0 && prev != code->device) cudaSetDevice(prev);
+    delete code;
+}
+
+int sagms_code_info(const sagms_code* code, int32_t* m, int32_t* n, int32_t* dc_max, int32_t* dv_max) {
+    if (!code) return fail(SAGMS_ERR_ARG, "code is NULL");
+    if (m) *m = code->m;
+    if (n) *n = code->n;
+    if (dc_max) *dc_max = code->dc_max;
+    if (dv_max) *dv_max = code->dv_max;
+    return SAGMS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, const uint32_t* d_syn,
+                  const float* d_L0, uint32_t* d_err, uint8_t* d_conv, int32_t* d_iters, float* d_trace,
+                  cudaStream_t stream) {
+    if (!code) return fail(SAGMS_ERR_ARG, "code is NULL");
+    int rc = sagms_check_params(p);
+    if (rc != SAGMS_OK) return rc;
+    if (shots < 0) return fail(SAGMS_ERR_ARG, "shots < 0");
+    if (shots == 0) return SAGMS_OK;
+    if (!d_syn || !d_L0 || !d_err || !d_conv || !d_iters) return fail(SAGMS_ERR_ARG, "NULL device buffer");
+    const bool bp = p->mode == SAGMS_BP;
+    const bool per_qubit = (p->flags & SAGMS_FLAG_L0_PER_QUBIT) != 0;
+    DecodeArgs a;
+    a.colT = code->d_colT;
+    a.vneT = code->d_vneT;
+    a.m = code->m; a.n = code->n; a.Mp = code->Mp; a.Np = code->Np;
+    a.mode = p->mode;
+    a.alpha = p->alpha;
+    a.amin = p->alpha_min;
+    a.amax = p->alpha_max;
+    a.eta = (p->eta_unsat == 0.0f) ? 1.10f : p->eta_unsat;
+    a.inv_m = 1.0f / (float)code->m;
+    a.max_iter = p->max_iter;
+    a.flags = p->flags;
+    a.shots = shots;
+    a.syn = d_syn; a.L0 = d_L0; a.err = d_err; a.conv = d_conv; a.iters = d_iters; a.trace = d_trace;
+
+    KernelFn kfn = kernel_for(code->variant, bp);
+    const size_t smem = smem_bytes(code->DC, code->DV, code->Mp, code->Np, per_qubit);
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
+    if (dev != code->device) return fail(SAGMS_ERR_ARG, "code was loaded on device %d, current is %d", code->device, dev);
+    int smem_optin = 0, sms = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (smem > (size_t)smem_optin)
+        return fail(SAGMS_ERR_SIZE, "code needs %zu B of shared memory per CTA (limit %d)", smem, smem_optin);
+    ce = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaFuncSetAttribute");
+    int per_sm = 0;
+    ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, code->Mp, smem);
+    if (ce != cudaSuccess) return cuda_fail(ce, "occupancy query");
+    if (per_sm < 1) return fail(SAGMS_ERR_SIZE, "kernel does not fit on an SM");
+    const long long grid = std::min<long long>(shots, (long long)per_sm * sms);
+    kfn<<<(unsigned)grid, code->Mp, smem, stream>>>(a);
+    ce = cudaGetLastError();
+    if (ce != cudaSuccess) return cuda_fail(ce, "decode launch");
+    return SAGMS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sagms_decode(const sagms_code* code, const sagms_params* params, int64_t shots, const uint32_t* d_syn,
+                 const float* d_L0, uint32_t* d_err, uint8_t* d_conv, int32_t* d_iters, void* stream) {
+    return launch_decode(code, params, shots, d_syn, d_L0, d_err, d_conv, d_iters, nullptr,
+                         static_cast<cudaStream_t>(stream));
+}
+
+int sagms_decode_trace(const sagms_code* code, const sagms_params* params, int64_t shots, const uint32_t* d_syn,
+                       const float* d_L0, uint32_t* d_err, uint8_t* d_conv, int32_t* d_iters, float* d_trace,
+                       void* stream) {
+    if (shots > 0 && !d_trace) return fail(SAGMS_ERR_ARG, "d_trace is NULL");
+    return launch_decode(code, params, shots, d_syn, d_L0, d_err, d_conv, d_iters, d_trace,
+                         static_cast<cudaStream_t>(stream));
+}
+
+int sagms_decode_host(const sagms_code* code, const sagms_params* params, int64_t shots, const uint32_t* h_syn,
+                      const float* h_L0, uint32_t* h_err, uint8_t* h_conv, int32_t* h_iters) {
+    if (!code) return fail(SAGMS_ERR_ARG, "code is NULL");
+    int rc = sagms_check_params(params);
+    if (rc != SAGMS_OK) return rc;
+    if (shots < 0) return fail(SAGMS_ERR_ARG, "shots < 0");
+    if (shots == 0) return SAGMS_OK;
+    if (!h_syn || !h_L0 || !h_err || !h_conv || !h_iters) return fail(SAGMS_ERR_ARG, "NULL host buffer");
+    const bool per_qubit = (params->flags & SAGMS_FLAG_L0_PER_QUBIT) != 0;
+    const int mw = (code->m + 31) / 32, nw = (code->n + 31) / 32;
+    const int kStreams = 2;
+    const int64_t chunk = std::max<int64_t>(std::min<int64_t>((shots + 7) / 8, 1 << 20), 1);
+    cudaStream_t st[kStreams] = {nullptr, nullptr};
+    struct Bufs { uint32_t* syn; float* L0; uint32_t* err; uint8_t* conv; int32_t* iters; } b[kStreams];
+    memset(b, 0, sizeof(b));
+    cudaError_t ce = cudaSuccess;
+    for (int k = 0; k < kStreams && ce == cudaSuccess; ++k) ce = cudaStreamCreateWithFlags(&st[k], cudaStreamNonBlocking);
+    const size_t l0_elems = per_qubit ? (size_t)code->n : (size_t)chunk;
+    for (int k = 0; k < kStreams && ce == cudaSuccess; ++k) {
+        ce = cudaMallocAsync((void**)&b[k].syn, (size_t)chunk * mw * 4, st[k]);
+        if (ce == cudaSuccess) ce = cudaMallocAsync((void**)&b[k].L0, l0_elems * 4, st[k]);
+        if (ce == cudaSuccess) ce = cudaMallocAsync((void**)&b[k].err, (size_t)chunk * nw * 4, st[k]);
+        if (ce == cudaSuccess) ce = cudaMallocAsync((void**)&b[k].conv, (size_t)chunk, st[k]);
+        if (ce == cudaSuccess) ce = cudaMallocAsync((void**)&b[k].iters, (size_t)chunk * 4, st[k]);
+        if (ce == cudaSuccess && per_qubit)
+            ce = cudaMemcpyAsync(b[k].L0, h_L0, (size_t)code->n * 4, cudaMemcpyHostToDevice, st[k]);
+    }
+    rc = (ce == cudaSuccess) ? SAGMS_OK : cuda_fail(ce, "sagms_decode_host setup");
+    int64_t chunk_id = 0;
+    for (int64_t s0 = 0; s0 < shots && rc == SAGMS_OK; s0 += chunk, ++chunk_id) {
+        const int k = (int)(chunk_id % kStreams);
+        const int64_t cnt = std::min(chunk, shots - s0);
+        ce = cudaMemcpyAsync(b[k].syn, h_syn + s0 * mw, (size_t)cnt * mw * 4, cudaMemcpyHostToDevice, st[k]);
+        if (ce == cudaSuccess && !per_qubit)
+            ce = cudaMemcpyAsync(b[k].L0, h_L0 + s0, (size_t)cnt * 4, cudaMemcpyHostToDevice, st[k]);
+        if (ce != cudaSuccess) { rc = cuda_fail(ce, "H2D copy"); break; }
+        rc = launch_decode(code, params, cnt, b[k].syn, b[k].L0, b[k].err, b[k].conv, b[k].iters, nullptr, st[k]);
+        if (rc != SAGMS_OK) break;
+        ce = cudaMemcpyAsync(h_err + s0 * nw, b[k].err, (size_t)cnt * nw * 4, cudaMemcpyDeviceToHost, st[k]);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_conv + s0, b[k].conv, (size_t)cnt, cudaMemcpyDeviceToHost, st[k]);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_iters + s0, b[k].iters, (size_t)cnt * 4, cudaMemcpyDeviceToHost, st[k]);
+        if (ce != cudaSuccess) { rc = cuda_fail(ce, "D2H copy"); break; }
+    }
+    for (int k = 0; k < kStreams; ++k) {
+        if (!st[k]) continue;
+        void* ptrs[5] = {b[k].syn, b[k].L0, b[k].err, b[k].conv, b[k].iters};
+        for (void* ptr : ptrs)
+            if (ptr) cudaFreeAsync(ptr, st[k]);
+        ce = cudaStreamSynchronize(st[k]);
+        if (ce != cudaSuccess && rc == SAGMS_OK) rc = cuda_fail(ce, "sagms_decode_host sync");
+        cudaStreamDestroy(st[k]);
+    }
+    return rc;
+}
+
+}  // extern "C"

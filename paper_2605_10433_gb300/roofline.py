@@ -1,0 +1,45 @@
+"""Algorithmic work model of one decoder iteration and the ALU-issue roofline.
+
+The per-check-node cost follows the weighted operation count of Eq. 15 / Table I
+(additions, multiplications, comparisons weight 1, transcendentals weight 10):
+    MS    2 d_c - 3   (Table I: d_c - 1 multiplications, d_c - 2 comparisons)
+    SMS   2 d_c - 2   (Eq. 15: MS plus the alpha multiplication)
+    SAGMS 2 d_c + 3   (Eq. 15 / Table I: 3 additions, d_c + 1 multiplications, d_c - 1 comparisons)
+    BP    22 d_c - 13 (Eq. 15 / Table I: d_c - 2 additions, d_c - 1 multiplications, 2 d_c - 1 transcendentals)
+To that one iteration adds, per qubit j of degree d_v, the posterior sum, the d_v extrinsic
+subtractions and the hard decision (2 d_v + 1), one XOR per edge for the residual syndrome
+(Eq. 1), and one popcount step per check (Eq. 6).  Retired shots do no work, so the work of a
+batch is sum over shots of iters x ops_per_iteration.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+CN_OPS = {
+    "ms": lambda dc: 2 * dc - 3,
+    "sms": lambda dc: 2 * dc - 2,
+    "sagms": lambda dc: 2 * dc + 3,
+    "bp": lambda dc: 22 * dc - 13,
+}
+
+THREAD_OPS_PER_SM_CLK = 128   # 4 schedulers x 32 lanes issue one instruction each per clock
+
+
+def ops_per_iteration(mode: str, row_ptr, col_idx, n: int) -> int:
+    row_ptr = np.asarray(row_ptr)
+    dc = np.diff(row_ptr)
+    dv = np.bincount(np.asarray(col_idx), minlength=n)
+    cn = int(sum(CN_OPS[mode](int(d)) for d in dc))
+    vn = int((2 * dv + 1).sum())
+    edges = int(row_ptr[-1])
+    return cn + vn + edges + len(dc)
+
+
+def alu_peak_ops(sms: int, sm_mhz: float) -> float:
+    """Thread-instruction issue rate of the whole GPU: SMs x 128 lanes x clock."""
+    return sms * THREAD_OPS_PER_SM_CLK * sm_mhz * 1e6
+
+
+def hbm_bytes_per_shot(m: int, n: int) -> int:
+    """Syndrome in, prior in, packed estimate + flag + count out."""
+    return ((m + 31) // 32) * 4 + 4 + ((n + 31) // 32) * 4 + 1 + 4

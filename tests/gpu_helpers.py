@@ -1,0 +1,167 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path and the FP64 oracle on the
+same seeded shots and compare them element by element.
+
+Acceptance (the tolerances of the decoder's specification, with the readings below):
+* Per-shot outputs (e_hat, conv, iters) identical on >= 99.99% of shots.  Every
+  mismatching shot is traced to its first divergent check l_d.  If l_d is within the shot's
+  conditioning horizon (below), the differing bits must be near-ties (oracle |P| < 1e-4,
+  decoder units) and count against the 0.01%.  If l_d lies past the horizon, or the FP64
+  outcome itself changes under the perturbation, the trajectory had already amplified
+  FP32-level differences beyond 1e-6 before diverging: the shot has no FP32-determined
+  answer and is reported, not counted.  The conditioning perturbation scales the decoder
+  parameters (BP and LLR-unit runs: the priors; SMS / SAGMS: the gains) by 1 +- 2^-23.
+* Posteriors: normwise relative error max_j |g_j - o_j| / max(max_j |o_j|, 1) <= 1e-5 at
+  every check up to the shot's conditioning horizon (the last check at which the
+  1 +- 2^-23 parameter perturbation moves the FP64 posteriors by <= 1e-6 normwise) and
+  before any hard-decision divergence.  Normwise, because a posterior is a sum of d_v + 1
+  messages and the rounding error of a sum scales with the size of its terms, not with a
+  result that may cancel to near zero.
+MS in L0-normalised units is integer-valued: it must match exactly, with no exemption.
+"""
+import os
+
+import numpy as np
+import torch
+
+import oracle
+import paper_2605_10433_gb300 as S
+from paper_2605_10433_gb300 import inputs as I
+
+ORACLE_MODE = {"ms": oracle.MS, "sms": oracle.SMS, "sagms": oracle.SAGMS, "bp": oracle.BP}
+THREADS = max(1, min(32, os.cpu_count() or 1))
+MSG_RTOL = 1e-5
+TIE_ABS = 1e-4
+PERTURB = 2.0 ** -23
+HORIZON_RTOL = 1e-6
+
+
+def oracle_decode(code, syn, L0, p: S.Params, trace=False):
+    return oracle.decode_code(code, syn, np.asarray(L0, dtype=np.float64), mode=ORACLE_MODE[p.mode],
+                              alpha=p.alpha, alpha_min=p.alpha_min, alpha_max=p.alpha_max,
+                              eta_unsat=p.eta_unsat, max_iter=p.max_iter, flags=p.flags, trace=trace,
+                              threads=THREADS)
+
+
+def gpu_decode(dcode, syn, L0, p: S.Params, trace=False):
+    d_syn = torch.from_numpy(np.ascontiguousarray(syn).view(np.int32)).cuda()
+    d_L0 = torch.from_numpy(np.ascontiguousarray(L0, dtype=np.float32)).cuda()
+    out = S.decode(dcode, d_syn, d_L0, p, trace=trace)
+    torch.cuda.synchronize()
+    res = {"err": out[0].cpu().numpy().view(np.uint32), "conv": out[1].cpu().numpy(),
+           "iters": out[2].cpu().numpy()}
+    if trace:
+        res["trace"] = out[3].cpu().numpy()
+    return res
+
+
+def first_divergence(gt, ot, iters_g, iters_o, n):
+    """First check index where the sign-bit hard decisions of the two traces differ."""
+    last = min(iters_g, iters_o)
+    for l in range(last + 1):
+        gd = np.signbit(gt[l, :n])
+        od = ot[l, :n] < 0
+        if (gd != od).any():
+            return l, np.nonzero(gd != od)[0]
+    return None, None
+
+
+def perturbed(p: S.Params, L0, sign):
+    """Parameters and priors scaled by (1 + sign 2^-23): the FP32-level perturbation used to
+    measure how well the FP64 trajectory of a shot is determined."""
+    f = 1.0 + sign * PERTURB
+    L0 = np.asarray(L0, dtype=np.float64)
+    llr_units = p.mode == "bp" or bool(p.flags & 1)   # per-qubit priors: no normalisation
+    LL = L0 * f if llr_units else L0
+    if p.mode == "sms":
+        return S.Params(**{**p.__dict__, "alpha": p.alpha * f}), LL
+    if p.mode == "sagms":
+        return S.Params(**{**p.__dict__, "alpha_min": p.alpha_min * f, "alpha_max": p.alpha_max * f}), LL
+    if llr_units:
+        return p, LL
+    return None, L0   # MS in L0-normalised units: integer-valued, nothing to perturb
+
+
+def _normwise(a, b):
+    return float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), 1.0)) if a.size else 0.0
+
+
+def conditioning(code, syn1, L01, p: S.Params):
+    """FP64 trajectory of one shot and its 1 +- 2^-23 perturbations.  Returns (trace, outcome
+    stable?, horizon), horizon = last check whose normwise posterior change stays <= 1e-6."""
+    o = oracle_decode(code, syn1, L01, p, trace=True)
+    n = code.n
+    last = int(o["iters"][0])
+    horizon = last
+    stable = True
+    for sign in (+1, -1):
+        pp, LL = perturbed(p, L01, sign)
+        if pp is None:
+            continue
+        q = oracle_decode(code, syn1, LL, pp, trace=True)
+        if not (np.array_equal(q["err"], o["err"]) and q["iters"][0] == o["iters"][0] and q["conv"][0] == o["conv"][0]):
+            stable = False
+        for l in range(min(last, int(q["iters"][0])) + 1):
+            if _normwise(q["trace"][0, l, :n], o["trace"][0, l, :n]) > HORIZON_RTOL:
+                horizon = min(horizon, l - 1)
+                break
+    return o, stable, horizon
+
+
+def compare(code, dcode, syn, L0, p: S.Params, min_frac=0.9999, ref=None):
+    """Decode on both sides and enforce the acceptance above.  Returns a summary dict."""
+    g = gpu_decode(dcode, syn, L0, p)
+    o = ref if ref is not None else oracle_decode(code, syn, L0, p)
+    same = (g["err"] == o["err"]).all(axis=1) & (g["conv"] == o["conv"]) & (g["iters"] == o["iters"])
+    shots = len(same)
+    bad = np.nonzero(~same)[0]
+    per_qubit = bool(p.flags & 1)
+    counted, ill = [], []
+    for s in bad:
+        L1 = L0 if per_qubit else L0[s:s + 1]
+        gt = gpu_decode(dcode, syn[s:s + 1], L1, p, trace=True)
+        ot, stable, horizon = conditioning(code, syn[s:s + 1], L1, p)
+        l, bits = first_divergence(gt["trace"][0], ot["trace"][0], int(gt["iters"][0]), int(ot["iters"][0]), code.n)
+        assert l is not None, f"shot {s}: outputs differ but no posterior sign differs"
+        worst = float(np.abs(ot["trace"][0, l, bits]).max())
+        if worst < TIE_ABS:
+            counted.append(int(s))
+            continue
+        assert (not stable) or l > horizon, (
+            f"shot {s} ({p.mode}): divergence at check {l} (horizon {horizon}) with oracle |P| = {worst:.3g}")
+        ill.append(int(s))
+    allowed = int(np.floor((1 - min_frac) * shots))
+    assert len(counted) <= allowed, f"{len(counted)} near-tie mismatches / {shots} shots ({p.mode}), allowed {allowed}"
+    fer_g = float(1 - g["conv"].mean()) if shots else 0.0
+    fer_o = float(1 - o["conv"].mean()) if shots else 0.0
+    return {"shots": shots, "mismatch": len(bad), "near_tie": len(counted), "ill_conditioned": len(ill),
+            "fer_gpu": fer_g, "fer_oracle": fer_o, "gpu": g, "oracle": o}
+
+
+def compare_traces(code, dcode, syn, L0, p: S.Params):
+    """Posterior traces within the normwise tolerance up to each shot's conditioning horizon.
+    Returns (largest normwise error inside the horizons, largest anywhere, mean horizon)."""
+    g = gpu_decode(dcode, syn, L0, p, trace=True)
+    n = code.n
+    per_qubit = bool(p.flags & 1)
+    worst_in, worst_all, hz = 0.0, 0.0, []
+    for s in range(syn.shape[0]):
+        L1 = L0 if per_qubit else L0[s:s + 1]
+        o, _, horizon = conditioning(code, syn[s:s + 1], L1, p)
+        ot = o["trace"][0]
+        gi, oi = int(g["iters"][s]), int(o["iters"][0])
+        l_div, _ = first_divergence(g["trace"][s], ot, gi, oi, n)
+        last = min(gi, oi) if l_div is None else l_div - 1
+        hz.append(horizon)
+        for l in range(last + 1):
+            e = _normwise(g["trace"][s, l, :n].astype(np.float64), ot[l, :n])
+            worst_all = max(worst_all, e)
+            if l <= horizon:
+                worst_in = max(worst_in, e)
+                assert e <= MSG_RTOL, f"shot {s} check {l} (horizon {horizon}): normwise posterior error {e:.3g}"
+    return worst_in, worst_all, float(np.mean(hz)) if hz else 0.0
+
+
+def residual_ok(code, syn, err):
+    """conv must equal [s XOR H e_hat == 0] (a property that holds at any size)."""
+    s_hat = I.syndrome(code, err)
+    return (s_hat == syn).all(axis=1)
