@@ -40,8 +40,8 @@ SAGMS_KW = dict(alpha_min=0.30, alpha_max=0.50, eta_unsat=1.10)
 SMS_ALPHA = 0.75
 MAX_ITER = 100
 NOISE_SEED = 20260513
-PROFILE = os.path.join(ROOT, "profiles", "decode_kernel_gb1023_sagms.md")
-KERNEL_SRC = os.path.join(ROOT, "paper_2605_10433_gb300", "csrc", "decode_kernel.cuh")
+PROFILE = os.path.join(ROOT, "profiles", "slot_kernel_gb1023_sagms.md")
+KERNEL_SRC = [os.path.join(ROOT, "paper_2605_10433_gb300", "csrc", f) for f in ("decode_slots.cuh", "decode_kernel.cuh")]
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -106,12 +106,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
+def kernel_sha():
+    h = hashlib.sha256()
+    for f in KERNEL_SRC:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def profile_traffic(shots_per_launch):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
     kernel source (else None)."""
     try:
         txt = open(PROFILE).read()
-        sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+        sha = kernel_sha()
         m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
         m_b = re.search(r"dram_bytes_per_shot:\s*([0-9.eE+-]+)", txt)
         if not m_sha or not m_b or m_sha.group(1) != sha:

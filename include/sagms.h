@@ -45,7 +45,10 @@ enum {
      * prior per shot.  Without it the MS family runs in L0-normalised units. */
     SAGMS_FLAG_L0_PER_QUBIT = 1u,
     /* Run exactly max_iter rounds even after the residual syndrome reaches zero. */
-    SAGMS_FLAG_NO_EARLY_STOP = 2u
+    SAGMS_FLAG_NO_EARLY_STOP = 2u,
+    /* Use the one-shot-per-CTA kernel even where a two-slot kernel exists (cross-checks:
+     * both kernels give bitwise identical results). */
+    SAGMS_FLAG_GENERIC_KERNEL = 4u
 };
 
 /* Status codes. */

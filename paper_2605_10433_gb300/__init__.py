@@ -12,6 +12,7 @@ from dataclasses import dataclass
 MODES = {"ms": 0, "sms": 1, "sagms": 2, "bp": 3}
 FLAG_L0_PER_QUBIT = 1
 FLAG_NO_EARLY_STOP = 2
+FLAG_GENERIC_KERNEL = 4
 
 
 @dataclass

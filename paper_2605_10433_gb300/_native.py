@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libsagms.so")
 SAGMS_MS, SAGMS_SMS, SAGMS_SAGMS, SAGMS_BP = 0, 1, 2, 3
 SAGMS_FLAG_L0_PER_QUBIT = 1
 SAGMS_FLAG_NO_EARLY_STOP = 2
+SAGMS_FLAG_GENERIC_KERNEL = 4
 SAGMS_OK = 0
 ERRORS = {-1: "ERR_ARG", -2: "ERR_CSR", -3: "ERR_DEGREE", -4: "ERR_PARAM", -5: "ERR_OOM", -6: "ERR_CUDA",
           -7: "ERR_TIMEOUT", -8: "ERR_BUSY", -9: "ERR_SIZE"}

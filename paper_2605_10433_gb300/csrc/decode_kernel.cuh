@@ -50,6 +50,7 @@ struct DecodeArgs {
     uint8_t* conv;
     int32_t* iters;
     float* trace;
+    int* work;   // two-slot kernel: zero-initialised shot counter (dynamic scheduling), or null
 };
 
 enum { kModeMS = 0, kModeSMS = 1, kModeSAGMS = 2, kModeBP = 3 };

@@ -1,0 +1,353 @@
+// Two-slot continuous-batching decoder kernel for the MS family (MS / SMS / SAGMS).
+//
+// A CTA owns two shot slots that advance independently through Algorithm 1.  When a slot's
+// residual syndrome reaches zero (or its iteration budget runs out) the CTA writes that
+// shot's result and loads the next shot into the slot in the same iteration: the slot's
+// check-node outputs are forced to zero for one round, so the variable-node update leaves
+// P = L0 of the new shot, and its first check happens at the next iteration.  No slot waits
+// for the other, and the code graph, the barriers and the index loads are shared by two
+// shots.
+//
+// Layout (shared memory, sizes fixed at compile time for the thread count MP = padded check
+// count and NP = padded qubit count, so every per-thread address is a register plus an
+// immediate):
+//   P2[NP]         float2: posterior of qubit c for slot 0 (.x) and slot 1 (.y); +inf past n
+//   C2[DC*MP + 2]  float2: CN->VN message of edge (i, j) at [j*MP + i]; C2[DC*MP] = 0
+//   colB[DC*MP]    u16: byte offset of P2[col(i, j)]
+//   vneB[DV*NP]    u32: byte offset (from C2) of the q-th edge of qubit c; padding -> zero slot
+// Packed FP32 pairs (add/sub.rn.f32x2) update both slots' edges in one instruction; min /
+// compare work stays per slot.  The arithmetic of each slot is, operation for operation and
+// in the same order, the one of decode_kernel.cuh, so both kernels give bitwise identical
+// results.
+#pragma once
+
+#include "decode_kernel.cuh"
+
+namespace sagms {
+
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(*reinterpret_cast<unsigned long long*>(&a)),
+        "l"(*reinterpret_cast<unsigned long long*>(&b)));
+    return *reinterpret_cast<float2*>(&r);
+}
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(*reinterpret_cast<unsigned long long*>(&a)),
+        "l"(*reinterpret_cast<unsigned long long*>(&b)));
+    return *reinterpret_cast<float2*>(&r);
+}
+
+struct SlotLayout {
+    const uint16_t* colB;  // [DC][MP]
+    const uint32_t* vneB;  // [DV][NP]
+};
+
+__host__ __device__ inline size_t slot_smem_bytes(int DC, int DV, int MP, int NP, bool per_qubit) {
+    return (size_t)NP * 8 + ((size_t)DC * MP + 2) * 8 + (per_qubit ? (size_t)NP * 4 : 0) + (size_t)DC * MP * 2 +
+           (size_t)DV * NP * 4 + 16 + 32 * 4 + 64 * 4 + 16;
+}
+
+// Resident CTAs per SM the register allocation must allow: 1024 threads per SM, except the
+// widest checks at 256 threads, which trade a fourth CTA for spill-free registers.
+template <int DC, int MP>
+struct SlotBounds {
+    static constexpr int kMinBlocks = (DC >= 12 && MP == 256) ? 3 : ((1024 / MP) > 0 ? (1024 / MP) : 1);
+};
+
+template <int DC, int DV, int MP, int NP>
+__global__ void __launch_bounds__(MP, SlotBounds<DC, MP>::kMinBlocks)
+slot_kernel(const DecodeArgs a, const SlotLayout lay) {
+    static_assert(NP % MP == 0, "qubit padding must be a multiple of the thread count");
+    static_assert(MP <= 1024, "one thread per check");
+    constexpr int VPT = NP / MP;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const bool per_qubit = (a.flags & kFlagPerQubit) != 0;
+    const bool early = (a.flags & kFlagNoEarlyStop) == 0;
+    float2* P2 = reinterpret_cast<float2*>(smem);
+    float2* C2 = P2 + NP;
+    float* PQ = reinterpret_cast<float*>(C2 + DC * MP + 2);
+    uint16_t* colB = reinterpret_cast<uint16_t*>(PQ + (per_qubit ? NP : 0));
+    uint32_t* vneB = reinterpret_cast<uint32_t*>(colB + DC * MP);
+    int* cnt = reinterpret_cast<int*>(vneB + DV * NP);        // [4]
+    uint32_t* flipw = reinterpret_cast<uint32_t*>(cnt + 4);  // [32] first-check flip bits per check
+    uint32_t* negw = flipw + 32;                              // [64] per-qubit [L0_j < 0] bits
+    int* claim = reinterpret_cast<int*>(negw + 64);           // [2 slots][2] claimed shot indices
+    const unsigned char* c2base = reinterpret_cast<const unsigned char*>(C2);
+
+    const int t = threadIdx.x;
+    const int lane = t & 31;
+    const int n = a.n, m = a.m;
+    const int mw = (m + 31) >> 5, nw = (n + 31) >> 5;
+    const float inf = __uint_as_float(0x7f800000u);
+    const uint16_t pad = (uint16_t)(n * 8);
+
+    {
+        const int4* s1 = reinterpret_cast<const int4*>(lay.colB);
+        int4* d1 = reinterpret_cast<int4*>(colB);
+        for (int k = t; k < DC * MP * 2 / 16; k += MP) d1[k] = __ldg(s1 + k);
+        const int4* s2 = reinterpret_cast<const int4*>(lay.vneB);
+        int4* d2 = reinterpret_cast<int4*>(vneB);
+        for (int k = t; k < DV * NP * 4 / 16; k += MP) d2[k] = __ldg(s2 + k);
+    }
+    for (int c = t; c < NP; c += MP) {
+        P2[c] = (c < n) ? make_float2(0.0f, 0.0f) : make_float2(inf, inf);
+        if (per_qubit) PQ[c] = (c < n) ? __ldg(a.L0 + c) : inf;
+    }
+    if (t < 2) C2[DC * MP + t] = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int j = 0; j < DC; ++j) C2[j * MP + t] = make_float2(0.0f, 0.0f);
+    if (t < 4) cnt[t] = 0;
+    __syncthreads();
+    // First check of a shot: every hard decision is [prior_j < 0], so the residual bit of a
+    // check (Eq. 1) is s_i XOR flip_i with flip_i = parity of its negative priors:
+    // per-qubit priors -> from PQ; a negative per-shot prior -> the check's degree parity.
+    int pq_ok = 1;
+    {
+        uint32_t f = 0u;
+        if (t < m) {
+            int d = 0;
+#pragma unroll
+            for (int j = 0; j < DC; ++j) {
+                const uint16_t off = colB[j * MP + t];
+                if (off != pad) {
+                    ++d;
+                    if (per_qubit) f ^= __float_as_uint(PQ[off >> 3]) >> 31;
+                }
+            }
+            if (!per_qubit) f = (uint32_t)d & 1u;
+        }
+        const uint32_t w = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) flipw[t >> 5] = w;
+        if (per_qubit) {
+            for (int c = t; c < n; c += MP) pq_ok &= isfinite(PQ[c]) ? 1 : 0;
+#pragma unroll
+            for (int vv = 0; vv < VPT; ++vv) {
+                const int c = vv * MP + t;
+                const uint32_t nb = __ballot_sync(0xffffffffu, (c < n) && (__float_as_uint(PQ[c]) >> 31));
+                if (lane == 0 && c < n) negw[c >> 5] = nb;
+            }
+        }
+    }
+    pq_ok = __syncthreads_and(pq_ok);
+
+    // Slot states: decoding, waiting for its next shot, no shots left.
+    enum { kActive = 0, kPending = 1, kDone = 2 };
+    // Round kinds per slot: regular, first round of a freshly loaded shot, zero (idle slot).
+    enum { kRegular = 0, kFresh = 1, kZero = 2 };
+    // Shot indices fit in 32 bits: the host splits larger batches into several launches.
+    // With a work counter, slots claim shots dynamically (thread 0, one atomic per shot, each
+    // claim made one refill ahead of its use and published through the shared ring `claim`);
+    // without one, slot k of CTA b takes shots 2b + k, 2b + k + 2G, ...
+    const int nshots = (int)a.shots;
+    const int stride = 2 * (int)gridDim.x;
+    const bool dynamic = a.work != nullptr;
+    int shot[2] = {-1, -1};
+    int nxt[2] = {2 * (int)blockIdx.x, 2 * (int)blockIdx.x + 1};
+    int cpar = 0;   // bit k: which ring entry slot k reads at its next refill
+    if (dynamic) {
+        if (t == 0) {
+            claim[0] = atomicAdd(a.work, 1);
+            claim[2] = atomicAdd(a.work, 1);
+            claim[1] = atomicAdd(a.work, 1);
+            claim[3] = atomicAdd(a.work, 1);
+        }
+        __syncthreads();
+        nxt[0] = claim[0];
+        nxt[1] = claim[2];
+        cpar = 0x3;
+    }
+    int state[2] = {kPending, kPending};
+    int itk[2] = {0, 0};
+    float prior[2] = {0.0f, 0.0f};
+    uint32_t sbits = 0;    // bit k: this thread's check syndrome bit of slot k
+    // Inputs of shot nxt[k], loaded one shot ahead: the prior and this thread's syndrome
+    // bit.  Together the CTA's bit loads pull the shot's whole syndrome into L1, so the
+    // per-lane word loads of the first-check popcount at refill time hit L1.
+    float pf_l0[2] = {0.0f, 0.0f};
+    uint32_t pf_bits = 0;
+    auto prefetch = [&](int k, int s) {
+        if (s < nshots) {
+            pf_l0[k] = per_qubit ? 0.0f : __ldg(a.L0 + s);
+            const uint32_t b = (t < m) ? ((__ldg(a.syn + (size_t)s * mw + (t >> 5)) >> (t & 31)) & 1u) : 0u;
+            pf_bits = (pf_bits & ~(1u << k)) | (b << k);
+        }
+    };
+    auto write_trace_row = [&](int k, int row) {
+        float* tr = a.trace + ((size_t)shot[k] * (size_t)(a.max_iter + 1) + (size_t)row) * (size_t)n;
+        for (int c = t; c < n; c += MP) tr[c] = k ? P2[c].y : P2[c].x;
+    };
+    prefetch(0, nxt[0]);
+    prefetch(1, nxt[1]);
+
+    int ph = 0;
+    while (state[0] != kDone || state[1] != kDone) {
+        // A5: gather, residual bits, unsatisfied counts of both slots
+        float2 v[DC];
+        uint32_t x0 = (sbits & 1u) << 31, x1 = (sbits >> 1) << 31;
+#pragma unroll
+        for (int j = 0; j < DC; ++j) {
+            v[j] = *reinterpret_cast<const float2*>(smem + colB[j * MP + t]);
+            x0 ^= __float_as_uint(v[j].x);
+            x1 ^= __float_as_uint(v[j].y);
+        }
+        const uint32_t b0 = __ballot_sync(0xffffffffu, x0 >> 31);
+        const uint32_t b1 = __ballot_sync(0xffffffffu, x1 >> 31);
+        if (lane == 0) {
+            if (b0) atomicAdd(&cnt[ph * 2 + 0], __popc(b0));
+            if (b1) atomicAdd(&cnt[ph * 2 + 1], __popc(b1));
+        }
+        __syncthreads();
+        int gcnt[2] = {cnt[ph * 2 + 0], cnt[ph * 2 + 1]};
+        uint32_t gst[2] = {x0 >> 31, x1 >> 31};
+        if (t == 0) { cnt[(ph ^ 1) * 2 + 0] = 0; cnt[(ph ^ 1) * 2 + 1] = 0; }
+
+        // A6 per slot: finish, refill, or count the round about to run.
+        int kind[2] = {kZero, kZero};
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (state[k] == kActive) {
+                if (a.trace) write_trace_row(k, itk[k]);
+                if ((gcnt[k] == 0 && early) || itk[k] == a.max_iter) {
+                    const size_t s = (size_t)shot[k];
+#pragma unroll
+                    for (int vv = 0; vv < VPT; ++vv) {
+                        const int c = vv * MP + t;
+                        const float pc = k ? P2[c].y : P2[c].x;
+                        const uint32_t word = __ballot_sync(0xffffffffu, (c < n) && (__float_as_uint(pc) >> 31));
+                        if (lane == 0 && c < n) a.err[s * nw + (c >> 5)] = word;
+                    }
+                    if (t == 0) { a.conv[s] = (gcnt[k] == 0) ? 1 : 0; a.iters[s] = itk[k]; }
+                    state[k] = kPending;
+                } else {
+                    itk[k]++;
+                    kind[k] = kRegular;
+                }
+            }
+            if (state[k] != kPending) continue;
+            // Take the prefetched shot (at most one per round: a shot finished at its first
+            // check leaves the slot pending for the next round).
+            const int s = nxt[k];
+            shot[k] = s;
+            if (s >= nshots) { state[k] = kDone; continue; }
+            const float l0 = pf_l0[k];
+            const uint32_t bit = (pf_bits >> k) & 1u;
+            const uint32_t word = (lane < mw) ? __ldg(a.syn + (size_t)s * mw + lane) : 0u;
+            if (dynamic) {
+                const int r = (cpar >> k) & 1;
+                nxt[k] = claim[2 * k + r];
+                if (t == 0) claim[2 * k + (r ^ 1)] = (nxt[k] < nshots) ? atomicAdd(a.work, 1) : nshots;
+                cpar ^= 1 << k;
+            } else {
+                nxt[k] = s + stride;
+            }
+            prefetch(k, nxt[k]);
+            if (!(per_qubit ? (pq_ok != 0) : isfinite(l0))) {
+                for (int w = t; w < nw; w += MP) a.err[(size_t)s * nw + w] = 0u;
+                if (t == 0) { a.conv[s] = 0; a.iters[s] = -1; }
+                continue;
+            }
+            const float pi = per_qubit ? 0.0f : ((l0 > 0.0f) ? 1.0f : ((l0 < 0.0f) ? -1.0f : 0.0f));
+            prior[k] = pi;
+            sbits = (sbits & ~(1u << k)) | (bit << k);
+            const bool flipped = per_qubit || pi < 0.0f;
+            // First check (l = 0) of the new shot, Eqs. 1 and 6: popcount of s XOR flip.
+            const uint32_t flip_lane = (flipped && lane < mw) ? flipw[lane] : 0u;
+            const int c0 = __reduce_add_sync(0xffffffffu, (int)__popc(word ^ flip_lane));
+            if (a.trace) {
+                float* tr = a.trace + (size_t)s * (size_t)(a.max_iter + 1) * (size_t)n;
+                for (int c = t; c < n; c += MP) tr[c] = per_qubit ? PQ[c] : pi;
+            }
+            if ((c0 == 0 && early) || a.max_iter == 0) {
+                for (int w = t; w < nw; w += MP) {
+                    uint32_t e0;
+                    if (per_qubit) e0 = negw[w];
+                    else e0 = (pi < 0.0f) ? ((w == nw - 1 && (n & 31)) ? ((1u << (n & 31)) - 1u) : 0xffffffffu) : 0u;
+                    a.err[(size_t)s * nw + w] = e0;
+                }
+                if (t == 0) { a.conv[s] = (c0 == 0) ? 1 : 0; a.iters[s] = 0; }
+                continue;
+            }
+            // Round 1 runs now: its inputs are the priors themselves (C = 0), Eq. 2 at l = 1.
+            state[k] = kActive;
+            itk[k] = 1;
+            kind[k] = kFresh;
+            gcnt[k] = c0;
+            gst[k] = bit ^ ((flipped && t < m) ? ((flipw[t >> 5] >> (t & 31)) & 1u) : 0u);
+#pragma unroll
+            for (int j = 0; j < DC; ++j) {
+                const uint16_t off = colB[j * MP + t];
+                const float pv = (off == pad) ? inf : (per_qubit ? PQ[off >> 3] : pi);
+                if (k) { v[j].y = pv; C2[j * MP + t].y = 0.0f; }
+                else { v[j].x = pv; C2[j * MP + t].x = 0.0f; }
+            }
+        }
+        if (state[0] == kDone && state[1] == kDone) break;
+
+        // A2 gains (Eq. 7 with this round's count and residual bit)
+        float g0 = 1.0f, g1 = 1.0f;
+        if (a.mode == kModeSAGMS) {
+            g0 = (a.amax - (a.amax - a.amin) * ((float)gcnt[0] * a.inv_m)) * (gst[0] ? a.eta : 1.0f);
+            g1 = (a.amax - (a.amax - a.amin) * ((float)gcnt[1] * a.inv_m)) * (gst[1] ? a.eta : 1.0f);
+        } else if (a.mode == kModeSMS) {
+            g0 = a.alpha;
+            g1 = a.alpha;
+        }
+        // A3 check-node update for both slots
+        uint32_t par0 = (sbits & 1u) << 31, par1 = (sbits >> 1) << 31;
+#pragma unroll
+        for (int j = 0; j < DC; ++j) {
+            v[j] = sub2(v[j], C2[j * MP + t]);
+            par0 ^= __float_as_uint(v[j].x);
+            par1 ^= __float_as_uint(v[j].y);
+        }
+        par0 &= kSign;
+        par1 &= kSign;
+        float m1a = inf, m2a = inf, m1b = inf, m2b = inf;
+#pragma unroll
+        for (int j = 0; j < DC; ++j) {
+            const float aa = fabsf(v[j].x), ab = fabsf(v[j].y);
+            m2a = fminf(m2a, fmaxf(m1a, aa));
+            m1a = fminf(m1a, aa);
+            m2b = fminf(m2b, fmaxf(m1b, ab));
+            m1b = fminf(m1b, ab);
+        }
+        const bool za = kind[0] == kZero, zb = kind[1] == kZero;
+        const float o1a = za ? 0.0f : __uint_as_float(__float_as_uint(fminf(g0 * m1a, kMsFamClip)) | par0);
+        const float o2a = za ? 0.0f : __uint_as_float(__float_as_uint(fminf(g0 * m2a, kMsFamClip)) | par0);
+        const float o1b = zb ? 0.0f : __uint_as_float(__float_as_uint(fminf(g1 * m1b, kMsFamClip)) | par1);
+        const float o2b = zb ? 0.0f : __uint_as_float(__float_as_uint(fminf(g1 * m2b, kMsFamClip)) | par1);
+#pragma unroll
+        for (int j = 0; j < DC; ++j) {
+            const float ma = (fabsf(v[j].x) == m1a) ? o2a : o1a;
+            const float mb = (fabsf(v[j].y) == m1b) ? o2b : o1b;
+            C2[j * MP + t] = make_float2(__uint_as_float(__float_as_uint(ma) ^ (__float_as_uint(v[j].x) & kSign)),
+                                         __uint_as_float(__float_as_uint(mb) ^ (__float_as_uint(v[j].y) & kSign)));
+        }
+        __syncthreads();
+
+        // A4 variable-node update for both slots
+#pragma unroll
+        for (int vv = 0; vv < VPT; ++vv) {
+            const int c = vv * MP + t;
+            if (c < n) {
+                float2 acc;
+                if (per_qubit) {
+                    const float p = PQ[c];
+                    acc = make_float2(p, p);
+                } else {
+                    acc = make_float2(prior[0], prior[1]);
+                }
+#pragma unroll
+                for (int q = 0; q < DV; ++q)
+                    acc = add2(acc, *reinterpret_cast<const float2*>(c2base + vneB[q * NP + c]));
+                P2[c] = acc;
+            }
+        }
+        __syncthreads();
+        ph ^= 1;
+    }
+}
+
+}  // namespace sagms

@@ -18,6 +18,7 @@
 
 #include "../../include/sagms.h"
 #include "decode_kernel.cuh"
+#include "decode_slots.cuh"
 
 using namespace sagms;
 
@@ -66,6 +67,29 @@ KernelFn kernel_for(int variant, bool bp) {
 
 int round_up(int x, int k) { return (x + k - 1) / k * k; }
 
+// Two-slot MS-family kernels with compile-time layout: (DC, DV, MP threads, NP qubit slots).
+struct SlotVariant { int dc, dv, mp, np; };
+constexpr SlotVariant kSlotVariants[] = {
+    {6, 3, 64, 128},   {8, 4, 128, 256},  {6, 3, 256, 512},   {8, 4, 256, 512},  {10, 5, 256, 512},
+    {12, 6, 256, 512}, {16, 8, 256, 512}, {10, 5, 512, 1024}, {10, 5, 1024, 2048}};
+constexpr int kNumSlotVariants = sizeof(kSlotVariants) / sizeof(kSlotVariants[0]);
+
+using SlotFn = void (*)(const DecodeArgs, const SlotLayout);
+
+SlotFn slot_kernel_for(int v) {
+    switch (v) {
+        case 0: return slot_kernel<6, 3, 64, 128>;
+        case 1: return slot_kernel<8, 4, 128, 256>;
+        case 2: return slot_kernel<6, 3, 256, 512>;
+        case 3: return slot_kernel<8, 4, 256, 512>;
+        case 4: return slot_kernel<10, 5, 256, 512>;
+        case 5: return slot_kernel<12, 6, 256, 512>;
+        case 6: return slot_kernel<16, 8, 256, 512>;
+        case 7: return slot_kernel<10, 5, 512, 1024>;
+        default: return slot_kernel<10, 5, 1024, 2048>;
+    }
+}
+
 }  // namespace
 
 struct sagms_code {
@@ -76,6 +100,9 @@ struct sagms_code {
     int device;
     uint16_t* d_colT;
     uint16_t* d_vneT;
+    int slot_variant;      // -1: no two-slot kernel for this shape
+    uint16_t* d_colB;      // [DC][MP] byte offsets into P2
+    uint32_t* d_vneB;      // [DV][NP] byte offsets into C2
 };
 
 extern "C" {
@@ -100,7 +127,7 @@ double sagms_alpha_star(double L0, int32_t dc) {
 
 int sagms_check_params(const sagms_params* p) {
     if (!p) return fail(SAGMS_ERR_ARG, "params is NULL");
-    if (p->flags & ~(uint32_t)(SAGMS_FLAG_L0_PER_QUBIT | SAGMS_FLAG_NO_EARLY_STOP))
+    if (p->flags & ~(uint32_t)(SAGMS_FLAG_L0_PER_QUBIT | SAGMS_FLAG_NO_EARLY_STOP | SAGMS_FLAG_GENERIC_KERNEL))
         return fail(SAGMS_ERR_ARG, "unknown flag bits 0x%x", p->flags);
     if (p->max_iter < 0 || p->max_iter > 100000)
         return fail(SAGMS_ERR_PARAM, "max_iter %d outside [0, 100000]", p->max_iter);
@@ -182,10 +209,36 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
         for (size_t q = 0; q < ve.size(); ++q) vneT[q * Np + c] = (uint16_t)(ve[q].first * Mp + ve[q].second);
     }
 
+    // Two-slot layout, when a compiled shape covers the code.
+    int sv = -1;
+    for (int v = 0; v < kNumSlotVariants; ++v) {
+        const SlotVariant& S = kSlotVariants[v];
+        if (dc_max <= S.dc && dv_max <= S.dv && m <= S.mp && S.mp <= 2 * round_up(m, 32) &&
+            n + 1 <= S.np && n * 8 < 65536) { sv = v; break; }
+    }
+    std::vector<uint16_t> colB;
+    std::vector<uint32_t> vneB;
+    if (sv >= 0) {
+        const SlotVariant& S = kSlotVariants[sv];
+        colB.assign((size_t)S.dc * S.mp, (uint16_t)(n * 8));
+        for (int i = 0; i < m; ++i)
+            for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+                colB[(size_t)(e - row_ptr[i]) * S.mp + i] = (uint16_t)(col_idx[e] * 8);
+        vneB.assign((size_t)S.dv * S.np, (uint32_t)(S.dc * S.mp * 8));
+        for (int c = 0; c < n; ++c) {
+            const auto& ve = vedges[c];
+            for (size_t q = 0; q < ve.size(); ++q)
+                vneB[q * S.np + c] = (uint32_t)((ve[q].first * S.mp + ve[q].second) * 8);
+        }
+    }
+
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
     sagms_code* code = new sagms_code();
+    code->slot_variant = sv;
+    code->d_colB = nullptr;
+    code->d_vneB = nullptr;
     code->m = m; code->n = n; code->nnz = (int)nnz;
     code->dc_max = dc_max; code->dv_max = dv_max;
     code->variant = variant; code->DC = DC; code->DV = DV;
@@ -195,9 +248,17 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
     if (ce == cudaSuccess) ce = cudaMalloc(&code->d_vneT, vneT.size() * sizeof(uint16_t));
     if (ce == cudaSuccess) ce = cudaMemcpy(code->d_colT, colT.data(), colT.size() * 2, cudaMemcpyHostToDevice);
     if (ce == cudaSuccess) ce = cudaMemcpy(code->d_vneT, vneT.data(), vneT.size() * 2, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess && sv >= 0) {
+        ce = cudaMalloc(&code->d_colB, colB.size() * sizeof(uint16_t));
+        if (ce == cudaSuccess) ce = cudaMalloc(&code->d_vneB, vneB.size() * sizeof(uint32_t));
+        if (ce == cudaSuccess) ce = cudaMemcpy(code->d_colB, colB.data(), colB.size() * 2, cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess) ce = cudaMemcpy(code->d_vneB, vneB.data(), vneB.size() * 4, cudaMemcpyHostToDevice);
+    }
     if (ce != cudaSuccess) {
         cudaFree(code->d_colT);
         cudaFree(code->d_vneT);
+        cudaFree(code->d_colB);
+        cudaFree(code->d_vneB);
         delete code;
         return cuda_fail(ce, "sagms_load_code upload");
     }
@@ -212,6 +273,8 @@ void sagms_free_code(sagms_code* code) {
     if (prev != code->device) cudaSetDevice(code->device);
     cudaFree(code->d_colT);
     cudaFree(code->d_vneT);
+    cudaFree(code->d_colB);
+    cudaFree(code->d_vneB);
     if (prev >= 0 && prev != code->device) cudaSetDevice(prev);
     delete code;
 }
@@ -254,9 +317,9 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     a.flags = p->flags;
     a.shots = shots;
     a.syn = d_syn; a.L0 = d_L0; a.err = d_err; a.conv = d_conv; a.iters = d_iters; a.trace = d_trace;
+    a.work = nullptr;
 
-    KernelFn kfn = kernel_for(code->variant, bp);
-    const size_t smem = smem_bytes(code->DC, code->DV, code->Mp, code->Np, per_qubit);
+    const bool use_slots = !bp && code->slot_variant >= 0 && !(p->flags & SAGMS_FLAG_GENERIC_KERNEL);
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
@@ -264,16 +327,68 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     int smem_optin = 0, sms = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const void* fn;
+    size_t smem;
+    int threads;
+    long long units;
+    if (use_slots) {
+        const SlotVariant& S = kSlotVariants[code->slot_variant];
+        fn = reinterpret_cast<const void*>(slot_kernel_for(code->slot_variant));
+        smem = slot_smem_bytes(S.dc, S.dv, S.mp, S.np, per_qubit);
+        threads = S.mp;
+        units = (shots + 1) / 2;   // two shots in flight per CTA
+    } else {
+        fn = reinterpret_cast<const void*>(kernel_for(code->variant, bp));
+        smem = smem_bytes(code->DC, code->DV, code->Mp, code->Np, per_qubit);
+        threads = code->Mp;
+        units = shots;
+    }
     if (smem > (size_t)smem_optin)
         return fail(SAGMS_ERR_SIZE, "code needs %zu B of shared memory per CTA (limit %d)", smem, smem_optin);
-    ce = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    ce = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaFuncSetAttribute");
     int per_sm = 0;
-    ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, code->Mp, smem);
+    ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
     if (ce != cudaSuccess) return cuda_fail(ce, "occupancy query");
     if (per_sm < 1) return fail(SAGMS_ERR_SIZE, "kernel does not fit on an SM");
-    const long long grid = std::min<long long>(shots, (long long)per_sm * sms);
-    kfn<<<(unsigned)grid, code->Mp, smem, stream>>>(a);
+    const long long grid = std::min<long long>(units, (long long)per_sm * sms);
+    if (use_slots) {
+        // 32-bit shot indices inside the kernel: split batches beyond 2^31 - 1 shots.  Each
+        // launch gets a zeroed shot counter (scratch from the stream-ordered pool) that its
+        // CTAs claim shots from.
+        SlotLayout lay{code->d_colB, code->d_vneB};
+        const long long kMaxChunk = 0x7fffffffLL;
+        const long long nchunks = (shots + kMaxChunk - 1) / kMaxChunk;
+        int* d_work = nullptr;
+        ce = cudaMallocAsync(reinterpret_cast<void**>(&d_work), (size_t)nchunks * sizeof(int), stream);
+        if (ce != cudaSuccess) return cuda_fail(ce, "work counter allocation");
+        ce = cudaMemsetAsync(d_work, 0, (size_t)nchunks * sizeof(int), stream);
+        if (ce != cudaSuccess) {
+            cudaFreeAsync(d_work, stream);
+            return cuda_fail(ce, "work counter reset");
+        }
+        for (long long s0 = 0, ci = 0; s0 < shots; s0 += kMaxChunk, ++ci) {
+            DecodeArgs c = a;
+            const long long cnt = std::min(kMaxChunk, shots - s0);
+            const int mw = (code->m + 31) / 32, nw = (code->n + 31) / 32;
+            c.shots = cnt;
+            c.syn = a.syn + s0 * mw;
+            c.L0 = per_qubit ? a.L0 : a.L0 + s0;
+            c.err = a.err + s0 * nw;
+            c.conv = a.conv + s0;
+            c.iters = a.iters + s0;
+            c.trace = a.trace ? a.trace + s0 * (long long)(a.max_iter + 1) * code->n : nullptr;
+            c.work = d_work + ci;
+            const long long g = std::min(grid, (cnt + 1) / 2);
+            slot_kernel_for(code->slot_variant)<<<(unsigned)g, threads, smem, stream>>>(c, lay);
+        }
+        ce = cudaGetLastError();
+        cudaFreeAsync(d_work, stream);
+        if (ce != cudaSuccess) return cuda_fail(ce, "decode launch");
+        return SAGMS_OK;
+    } else {
+        kernel_for(code->variant, bp)<<<(unsigned)grid, threads, smem, stream>>>(a);
+    }
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return cuda_fail(ce, "decode launch");
     return SAGMS_OK;

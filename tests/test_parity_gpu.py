@@ -66,7 +66,7 @@ def test_config2_n254_fer_parity(codes, mode, p_dep):
     """GB l=127 (n=254), depolarising p marginalised to 2p/3, max_iter=100."""
     c, dc = codes[(127, 4)]
     q = float(I.depolarizing_to_z(p_dep))
-    _, syn, L0, _ = I.workload(c, [q], 6000, seed=int(2000 + 1000 * p_dep))
+    _, syn, L0, _ = I.workload(c, [q], 30000, seed=int(2000 + 1000 * p_dep))
     r = G.compare(c, dc, syn, L0, _p(mode, max_iter=100))
     fails_o = int(round(r["fer_oracle"] * r["shots"]))
     lo, hi = wilson_interval(fails_o, r["shots"])
@@ -238,3 +238,21 @@ def test_concurrent_streams_share_a_code(codes):
     for o in outs:
         assert np.array_equal(o[0].cpu().numpy().view(np.uint32), ref["err"])
         assert np.array_equal(o[2].cpu().numpy(), ref["iters"])
+
+
+@pytest.mark.parametrize("mode", ["ms", "sms", "sagms"])
+@pytest.mark.parametrize("lw", [(63, 3), (127, 4), (255, 8), (1023, 5)])
+def test_two_slot_kernel_is_bitwise_identical_to_generic(codes, mode, lw):
+    """The two-slot continuous-batching kernel and the one-shot-per-CTA kernel run the same
+    arithmetic in the same order: outputs and posterior traces agree bit for bit."""
+    c, dc = codes[lw]
+    _, syn, L0, _ = I.workload(c, [0.01, 0.03, 0.06], 3001, seed=31 + lw[0])
+    p = _p(mode, max_iter=60)
+    pg = _p(mode, max_iter=60, flags=S.FLAG_GENERIC_KERNEL)
+    a = G.gpu_decode(dc, syn, L0, p)
+    b = G.gpu_decode(dc, syn, L0, pg)
+    for k in ("err", "conv", "iters"):
+        assert np.array_equal(a[k], b[k])
+    ta = G.gpu_decode(dc, syn[:40], L0[:40], p, trace=True)["trace"]
+    tb = G.gpu_decode(dc, syn[:40], L0[:40], pg, trace=True)["trace"]
+    assert np.array_equal(np.nan_to_num(ta, nan=7.0), np.nan_to_num(tb, nan=7.0))
