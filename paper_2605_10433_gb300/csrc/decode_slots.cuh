@@ -25,28 +25,24 @@
 
 namespace sagms {
 
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
-    unsigned long long r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(*reinterpret_cast<unsigned long long*>(&a)),
-        "l"(*reinterpret_cast<unsigned long long*>(&b)));
-    return *reinterpret_cast<float2*>(&r);
-}
-
-__device__ __forceinline__ float2 add2(float2 a, float2 b) {
-    unsigned long long r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(*reinterpret_cast<unsigned long long*>(&a)),
-        "l"(*reinterpret_cast<unsigned long long*>(&b)));
-    return *reinterpret_cast<float2*>(&r);
-}
+// Paired FP32 add / subtract (round to nearest); a - b is a + (-b) exactly.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 
 struct SlotLayout {
     const uint16_t* colB;  // [DC][MP]
     const uint32_t* vneB;  // [DV][NP]
 };
 
+// Shared memory of one CTA (bytes), in the order the kernel carves it up.
 __host__ __device__ inline size_t slot_smem_bytes(int DC, int DV, int MP, int NP, bool per_qubit) {
-    return (size_t)NP * 8 + ((size_t)DC * MP + 2) * 8 + (per_qubit ? (size_t)NP * 4 : 0) + (size_t)DC * MP * 2 +
-           (size_t)DV * NP * 4 + 16 + 32 * 4 + 64 * 4 + 16;
+    return (size_t)(NP + 2) * 8                      // P2 (+ sentinel)
+           + ((size_t)DC * MP + 2) * 8               // C2 (+ zero slot)
+           + (per_qubit ? (size_t)(NP + 4) * 4 : 0)  // PQ
+           + (size_t)DC * MP * 2                     // colB
+           + (size_t)DV * NP * 4                     // vneB
+           + 16 + 32 * 4 + 64 * 4 + 16 + 16 + 16     // cnt, flipw, negw, claim, pfidx, shotsm
+           + 2 * 2 * 32 * 4 + 2 * 2 * 4;             // prefetch buffers (syndrome rows, priors)
 }
 
 // Resident CTAs per SM the register allocation must allow: 1024 threads per SM, except the
@@ -55,6 +51,13 @@ template <int DC, int MP>
 struct SlotBounds {
     static constexpr int kMinBlocks = (DC >= 12 && MP == 256) ? 3 : ((1024 / MP) > 0 ? (1024 / MP) : 1);
 };
+
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 template <int DC, int DV, int MP, int NP>
 __global__ void __launch_bounds__(MP, SlotBounds<DC, MP>::kMinBlocks)
@@ -66,14 +69,18 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
     const bool per_qubit = (a.flags & kFlagPerQubit) != 0;
     const bool early = (a.flags & kFlagNoEarlyStop) == 0;
     float2* P2 = reinterpret_cast<float2*>(smem);
-    float2* C2 = P2 + NP;
+    float2* C2 = P2 + NP + 2;
     float* PQ = reinterpret_cast<float*>(C2 + DC * MP + 2);
-    uint16_t* colB = reinterpret_cast<uint16_t*>(PQ + (per_qubit ? NP : 0));
+    uint16_t* colB = reinterpret_cast<uint16_t*>(PQ + (per_qubit ? NP + 4 : 0));
     uint32_t* vneB = reinterpret_cast<uint32_t*>(colB + DC * MP);
-    int* cnt = reinterpret_cast<int*>(vneB + DV * NP);        // [4]
-    uint32_t* flipw = reinterpret_cast<uint32_t*>(cnt + 4);  // [32] first-check flip bits per check
+    int* cnt = reinterpret_cast<int*>(vneB + DV * NP);       // [2 parity][2 slots]
+    uint32_t* flipw = reinterpret_cast<uint32_t*>(cnt + 4);  // [32] first-check flip bit per check
     uint32_t* negw = flipw + 32;                              // [64] per-qubit [L0_j < 0] bits
     int* claim = reinterpret_cast<int*>(negw + 64);           // [2 slots][2] claimed shot indices
+    uint32_t* pfsyn = reinterpret_cast<uint32_t*>(claim + 4); // [2 slots][2 buffers][32] syndrome rows
+    float* pfl0 = reinterpret_cast<float*>(pfsyn + 128);      // [2 slots][2 buffers] priors
+    int* pfidx = reinterpret_cast<int*>(pfl0 + 4);            // [2 slots][2 buffers] shot in each buffer
+    int* shotsm = pfidx + 4;                                  // [2 slots][2] shot being decoded
     const unsigned char* c2base = reinterpret_cast<const unsigned char*>(C2);
 
     const int t = threadIdx.x;
@@ -81,7 +88,7 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
     const int n = a.n, m = a.m;
     const int mw = (m + 31) >> 5, nw = (n + 31) >> 5;
     const float inf = __uint_as_float(0x7f800000u);
-    const uint16_t pad = (uint16_t)(n * 8);
+    const uint16_t pad = (uint16_t)(NP * 8);   // padding slots read the sentinel P2[NP] = +inf
 
     {
         const int4* s1 = reinterpret_cast<const int4*>(lay.colB);
@@ -91,10 +98,9 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
         int4* d2 = reinterpret_cast<int4*>(vneB);
         for (int k = t; k < DV * NP * 4 / 16; k += MP) d2[k] = __ldg(s2 + k);
     }
-    for (int c = t; c < NP; c += MP) {
-        P2[c] = (c < n) ? make_float2(0.0f, 0.0f) : make_float2(inf, inf);
-        if (per_qubit) PQ[c] = (c < n) ? __ldg(a.L0 + c) : inf;
-    }
+    for (int c = t; c < NP + 2; c += MP) P2[c] = (c < n) ? make_float2(0.0f, 0.0f) : make_float2(inf, inf);
+    if (per_qubit)
+        for (int c = t; c < NP + 4; c += MP) PQ[c] = (c < n) ? __ldg(a.L0 + c) : inf;
     if (t < 2) C2[DC * MP + t] = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int j = 0; j < DC; ++j) C2[j * MP + t] = make_float2(0.0f, 0.0f);
@@ -130,12 +136,7 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
             }
         }
     }
-    pq_ok = __syncthreads_and(pq_ok);
 
-    // Slot states: decoding, waiting for its next shot, no shots left.
-    enum { kActive = 0, kPending = 1, kDone = 2 };
-    // Round kinds per slot: regular, first round of a freshly loaded shot, zero (idle slot).
-    enum { kRegular = 0, kFresh = 1, kZero = 2 };
     // Shot indices fit in 32 bits: the host splits larger batches into several launches.
     // With a work counter, slots claim shots dynamically (thread 0, one atomic per shot, each
     // claim made one refill ahead of its use and published through the shared ring `claim`);
@@ -143,43 +144,36 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
     const int nshots = (int)a.shots;
     const int stride = 2 * (int)gridDim.x;
     const bool dynamic = a.work != nullptr;
-    int shot[2] = {-1, -1};
-    int nxt[2] = {2 * (int)blockIdx.x, 2 * (int)blockIdx.x + 1};
-    int cpar = 0;   // bit k: which ring entry slot k reads at its next refill
-    if (dynamic) {
-        if (t == 0) {
-            claim[0] = atomicAdd(a.work, 1);
-            claim[2] = atomicAdd(a.work, 1);
-            claim[1] = atomicAdd(a.work, 1);
-            claim[3] = atomicAdd(a.work, 1);
-        }
-        __syncthreads();
-        nxt[0] = claim[0];
-        nxt[1] = claim[2];
-        cpar = 0x3;
+    if (dynamic && t == 0) {
+        claim[0] = atomicAdd(a.work, 1);
+        claim[2] = atomicAdd(a.work, 1);
+        claim[1] = atomicAdd(a.work, 1);
+        claim[3] = atomicAdd(a.work, 1);
     }
+    pq_ok = __syncthreads_and(pq_ok);
+    const int first0 = dynamic ? claim[0] : 2 * (int)blockIdx.x;
+    const int first1 = dynamic ? claim[2] : 2 * (int)blockIdx.x + 1;
+    if (t == 0) { pfidx[0] = first0; pfidx[2] = first1; }
+    // Inputs of the shot a slot starts next (its syndrome row and prior) are copied into
+    // shared memory by warp 0 with cp.async one refill ahead, double-buffered per slot;
+    // warp 0 waits for its copies before each CTA barrier that precedes their use.
+    auto prefetch = [&](int k, int b, int s) {
+        if (t < 32 && s < nshots) {
+            if (lane < mw) cp_async4(pfsyn + (k * 2 + b) * 32 + lane, a.syn + (size_t)s * mw + lane);
+            if (lane == 0 && !per_qubit) cp_async4(pfl0 + k * 2 + b, a.L0 + s);
+            cp_async_commit();
+        }
+    };
+    prefetch(0, 0, first0);
+    prefetch(1, 0, first1);
+
+    // Slot states: decoding, waiting for its next shot, no shots left.
+    enum { kActive = 0, kPending = 1, kDone = 2 };
     int state[2] = {kPending, kPending};
     int itk[2] = {0, 0};
     float prior[2] = {0.0f, 0.0f};
-    uint32_t sbits = 0;    // bit k: this thread's check syndrome bit of slot k
-    // Inputs of shot nxt[k], loaded one shot ahead: the prior and this thread's syndrome
-    // bit.  Together the CTA's bit loads pull the shot's whole syndrome into L1, so the
-    // per-lane word loads of the first-check popcount at refill time hit L1.
-    float pf_l0[2] = {0.0f, 0.0f};
-    uint32_t pf_bits = 0;
-    auto prefetch = [&](int k, int s) {
-        if (s < nshots) {
-            pf_l0[k] = per_qubit ? 0.0f : __ldg(a.L0 + s);
-            const uint32_t b = (t < m) ? ((__ldg(a.syn + (size_t)s * mw + (t >> 5)) >> (t & 31)) & 1u) : 0u;
-            pf_bits = (pf_bits & ~(1u << k)) | (b << k);
-        }
-    };
-    auto write_trace_row = [&](int k, int row) {
-        float* tr = a.trace + ((size_t)shot[k] * (size_t)(a.max_iter + 1) + (size_t)row) * (size_t)n;
-        for (int c = t; c < n; c += MP) tr[c] = k ? P2[c].y : P2[c].x;
-    };
-    prefetch(0, nxt[0]);
-    prefetch(1, nxt[1]);
+    uint32_t sbits = 0;  // bit k: this thread's check syndrome bit of slot k
+    uint32_t pbits = 0;  // bit k: prefetch buffer / claim-ring entry slot k reads next
 
     int ph = 0;
     while (state[0] != kDone || state[1] != kDone) {
@@ -195,22 +189,37 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
         const uint32_t b0 = __ballot_sync(0xffffffffu, x0 >> 31);
         const uint32_t b1 = __ballot_sync(0xffffffffu, x1 >> 31);
         if (lane == 0) {
-            if (b0) atomicAdd(&cnt[ph * 2 + 0], __popc(b0));
-            if (b1) atomicAdd(&cnt[ph * 2 + 1], __popc(b1));
+            atomicAdd(&cnt[ph * 2 + 0], __popc(b0));
+            atomicAdd(&cnt[ph * 2 + 1], __popc(b1));
         }
+        if (t < 32) cp_async_wait_all();
         __syncthreads();
         int gcnt[2] = {cnt[ph * 2 + 0], cnt[ph * 2 + 1]};
         uint32_t gst[2] = {x0 >> 31, x1 >> 31};
         if (t == 0) { cnt[(ph ^ 1) * 2 + 0] = 0; cnt[(ph ^ 1) * 2 + 1] = 0; }
-
-        // A6 per slot: finish, refill, or count the round about to run.
-        int kind[2] = {kZero, kZero};
+        if (a.trace) {
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            if (state[k] == kActive) {
-                if (a.trace) write_trace_row(k, itk[k]);
-                if ((gcnt[k] == 0 && early) || itk[k] == a.max_iter) {
-                    const size_t s = (size_t)shot[k];
+            for (int k = 0; k < 2; ++k) {
+                if (state[k] != kActive) continue;
+                const int sk = shotsm[2 * k + (((pbits >> k) & 1) ^ 1)];
+                float* tr = a.trace + ((size_t)sk * (size_t)(a.max_iter + 1) + (size_t)itk[k]) * (size_t)n;
+                for (int c = t; c < n; c += MP) tr[c] = k ? P2[c].y : P2[c].x;
+            }
+        }
+
+        // A6 per slot: the common case (both slots decoding, neither finished) is one test.
+        bool zero[2] = {false, false};
+        const bool fin0 = state[0] == kActive && ((gcnt[0] == 0 && early) || itk[0] == a.max_iter);
+        const bool fin1 = state[1] == kActive && ((gcnt[1] == 0 && early) || itk[1] == a.max_iter);
+        if (!(fin0 || fin1 || state[0] != kActive || state[1] != kActive)) {
+            itk[0]++;
+            itk[1]++;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const bool fin = k ? fin1 : fin0;
+                if (fin) {
+                    const size_t s = (size_t)shotsm[2 * k + (((pbits >> k) & 1) ^ 1)];
 #pragma unroll
                     for (int vv = 0; vv < VPT; ++vv) {
                         const int c = vv * MP + t;
@@ -220,70 +229,71 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
                     }
                     if (t == 0) { a.conv[s] = (gcnt[k] == 0) ? 1 : 0; a.iters[s] = itk[k]; }
                     state[k] = kPending;
-                } else {
+                } else if (state[k] == kActive) {
                     itk[k]++;
-                    kind[k] = kRegular;
+                    continue;
                 }
-            }
-            if (state[k] != kPending) continue;
-            // Take the prefetched shot (at most one per round: a shot finished at its first
-            // check leaves the slot pending for the next round).
-            const int s = nxt[k];
-            shot[k] = s;
-            if (s >= nshots) { state[k] = kDone; continue; }
-            const float l0 = pf_l0[k];
-            const uint32_t bit = (pf_bits >> k) & 1u;
-            const uint32_t word = (lane < mw) ? __ldg(a.syn + (size_t)s * mw + lane) : 0u;
-            if (dynamic) {
-                const int r = (cpar >> k) & 1;
-                nxt[k] = claim[2 * k + r];
-                if (t == 0) claim[2 * k + (r ^ 1)] = (nxt[k] < nshots) ? atomicAdd(a.work, 1) : nshots;
-                cpar ^= 1 << k;
-            } else {
-                nxt[k] = s + stride;
-            }
-            prefetch(k, nxt[k]);
-            if (!(per_qubit ? (pq_ok != 0) : isfinite(l0))) {
-                for (int w = t; w < nw; w += MP) a.err[(size_t)s * nw + w] = 0u;
-                if (t == 0) { a.conv[s] = 0; a.iters[s] = -1; }
-                continue;
-            }
-            const float pi = per_qubit ? 0.0f : ((l0 > 0.0f) ? 1.0f : ((l0 < 0.0f) ? -1.0f : 0.0f));
-            prior[k] = pi;
-            sbits = (sbits & ~(1u << k)) | (bit << k);
-            const bool flipped = per_qubit || pi < 0.0f;
-            // First check (l = 0) of the new shot, Eqs. 1 and 6: popcount of s XOR flip.
-            const uint32_t flip_lane = (flipped && lane < mw) ? flipw[lane] : 0u;
-            const int c0 = __reduce_add_sync(0xffffffffu, (int)__popc(word ^ flip_lane));
-            if (a.trace) {
-                float* tr = a.trace + (size_t)s * (size_t)(a.max_iter + 1) * (size_t)n;
-                for (int c = t; c < n; c += MP) tr[c] = per_qubit ? PQ[c] : pi;
-            }
-            if ((c0 == 0 && early) || a.max_iter == 0) {
-                for (int w = t; w < nw; w += MP) {
-                    uint32_t e0;
-                    if (per_qubit) e0 = negw[w];
-                    else e0 = (pi < 0.0f) ? ((w == nw - 1 && (n & 31)) ? ((1u << (n & 31)) - 1u) : 0xffffffffu) : 0u;
-                    a.err[(size_t)s * nw + w] = e0;
+                zero[k] = true;
+                if (state[k] != kPending) continue;
+                // Start the prefetched shot (at most one per round: a shot finished at its
+                // first check leaves the slot pending for the next round).
+                const int b = (pbits >> k) & 1;
+                const int s = pfidx[2 * k + b];
+                if (s >= nshots) { state[k] = kDone; continue; }
+                const int nx = dynamic ? claim[2 * k + (b ^ 1)] : s + stride;
+                if (t == 0) {
+                    if (dynamic) claim[2 * k + b] = (nx < nshots) ? atomicAdd(a.work, 1) : nshots;
+                    pfidx[2 * k + (b ^ 1)] = nx;
+                    shotsm[2 * k + b] = s;
                 }
-                if (t == 0) { a.conv[s] = (c0 == 0) ? 1 : 0; a.iters[s] = 0; }
-                continue;
-            }
-            // Round 1 runs now: its inputs are the priors themselves (C = 0), Eq. 2 at l = 1.
-            state[k] = kActive;
-            itk[k] = 1;
-            kind[k] = kFresh;
-            gcnt[k] = c0;
-            gst[k] = bit ^ ((flipped && t < m) ? ((flipw[t >> 5] >> (t & 31)) & 1u) : 0u);
+                pbits ^= 1u << k;
+                const uint32_t* row = pfsyn + (k * 2 + b) * 32;
+                const float l0 = per_qubit ? 0.0f : pfl0[k * 2 + b];
+                const uint32_t bit = (t < m) ? ((row[t >> 5] >> (t & 31)) & 1u) : 0u;
+                const uint32_t word = (lane < mw) ? row[lane] : 0u;
+                prefetch(k, b ^ 1, nx);
+                if (!(per_qubit ? (pq_ok != 0) : isfinite(l0))) {
+                    for (int w = t; w < nw; w += MP) a.err[(size_t)s * nw + w] = 0u;
+                    if (t == 0) { a.conv[s] = 0; a.iters[s] = -1; }
+                    continue;
+                }
+                const float pi = per_qubit ? 0.0f : ((l0 > 0.0f) ? 1.0f : ((l0 < 0.0f) ? -1.0f : 0.0f));
+                prior[k] = pi;
+                sbits = (sbits & ~(1u << k)) | (bit << k);
+                const bool flipped = per_qubit || pi < 0.0f;
+                // First check (l = 0) of the new shot, Eqs. 1 and 6: popcount of s XOR flip.
+                const uint32_t flip_lane = (flipped && lane < mw) ? flipw[lane] : 0u;
+                const int c0 = __reduce_add_sync(0xffffffffu, (int)__popc(word ^ flip_lane));
+                if (a.trace) {
+                    float* tr = a.trace + (size_t)s * (size_t)(a.max_iter + 1) * (size_t)n;
+                    for (int c = t; c < n; c += MP) tr[c] = per_qubit ? PQ[c] : pi;
+                }
+                if ((c0 == 0 && early) || a.max_iter == 0) {
+                    for (int w = t; w < nw; w += MP) {
+                        uint32_t e0;
+                        if (per_qubit) e0 = negw[w];
+                        else e0 = (pi < 0.0f) ? ((w == nw - 1 && (n & 31)) ? ((1u << (n & 31)) - 1u) : 0xffffffffu) : 0u;
+                        a.err[(size_t)s * nw + w] = e0;
+                    }
+                    if (t == 0) { a.conv[s] = (c0 == 0) ? 1 : 0; a.iters[s] = 0; }
+                    continue;
+                }
+                // Round 1 runs now: its inputs are the priors themselves (C = 0), Eq. 2 at l = 1.
+                state[k] = kActive;
+                itk[k] = 1;
+                zero[k] = false;
+                gcnt[k] = c0;
+                gst[k] = bit ^ ((flipped && t < m) ? ((flipw[t >> 5] >> (t & 31)) & 1u) : 0u);
 #pragma unroll
-            for (int j = 0; j < DC; ++j) {
-                const uint16_t off = colB[j * MP + t];
-                const float pv = (off == pad) ? inf : (per_qubit ? PQ[off >> 3] : pi);
-                if (k) { v[j].y = pv; C2[j * MP + t].y = 0.0f; }
-                else { v[j].x = pv; C2[j * MP + t].x = 0.0f; }
+                for (int j = 0; j < DC; ++j) {
+                    const uint16_t off = colB[j * MP + t];
+                    const float pv = (off == pad) ? inf : (per_qubit ? PQ[off >> 3] : pi);
+                    if (k) { v[j].y = pv; C2[j * MP + t].y = 0.0f; }
+                    else { v[j].x = pv; C2[j * MP + t].x = 0.0f; }
+                }
             }
+            if (state[0] == kDone && state[1] == kDone) break;
         }
-        if (state[0] == kDone && state[1] == kDone) break;
 
         // A2 gains (Eq. 7 with this round's count and residual bit)
         float g0 = 1.0f, g1 = 1.0f;
@@ -313,11 +323,10 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
             m2b = fminf(m2b, fmaxf(m1b, ab));
             m1b = fminf(m1b, ab);
         }
-        const bool za = kind[0] == kZero, zb = kind[1] == kZero;
-        const float o1a = za ? 0.0f : __uint_as_float(__float_as_uint(fminf(g0 * m1a, kMsFamClip)) | par0);
-        const float o2a = za ? 0.0f : __uint_as_float(__float_as_uint(fminf(g0 * m2a, kMsFamClip)) | par0);
-        const float o1b = zb ? 0.0f : __uint_as_float(__float_as_uint(fminf(g1 * m1b, kMsFamClip)) | par1);
-        const float o2b = zb ? 0.0f : __uint_as_float(__float_as_uint(fminf(g1 * m2b, kMsFamClip)) | par1);
+        const float o1a = zero[0] ? 0.0f : __uint_as_float(__float_as_uint(fminf(g0 * m1a, kMsFamClip)) | par0);
+        const float o2a = zero[0] ? 0.0f : __uint_as_float(__float_as_uint(fminf(g0 * m2a, kMsFamClip)) | par0);
+        const float o1b = zero[1] ? 0.0f : __uint_as_float(__float_as_uint(fminf(g1 * m1b, kMsFamClip)) | par1);
+        const float o2b = zero[1] ? 0.0f : __uint_as_float(__float_as_uint(fminf(g1 * m2b, kMsFamClip)) | par1);
 #pragma unroll
         for (int j = 0; j < DC; ++j) {
             const float ma = (fabsf(v[j].x) == m1a) ? o2a : o1a;
@@ -327,23 +336,21 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
         }
         __syncthreads();
 
-        // A4 variable-node update for both slots
+        // A4 variable-node update for both slots (qubits past n compute on the zero slot and
+        // are never read: no bounds test in the loop)
+        const float2 pr = make_float2(prior[0], prior[1]);
 #pragma unroll
         for (int vv = 0; vv < VPT; ++vv) {
             const int c = vv * MP + t;
-            if (c < n) {
-                float2 acc;
-                if (per_qubit) {
-                    const float p = PQ[c];
-                    acc = make_float2(p, p);
-                } else {
-                    acc = make_float2(prior[0], prior[1]);
-                }
-#pragma unroll
-                for (int q = 0; q < DV; ++q)
-                    acc = add2(acc, *reinterpret_cast<const float2*>(c2base + vneB[q * NP + c]));
-                P2[c] = acc;
+            float2 acc = pr;
+            if (per_qubit) {
+                const float p = PQ[c];
+                acc = make_float2(p, p);
             }
+#pragma unroll
+            for (int q = 0; q < DV; ++q)
+                acc = add2(acc, *reinterpret_cast<const float2*>(c2base + vneB[q * NP + c]));
+            P2[c] = acc;
         }
         __syncthreads();
         ph ^= 1;

@@ -214,13 +214,13 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
     for (int v = 0; v < kNumSlotVariants; ++v) {
         const SlotVariant& S = kSlotVariants[v];
         if (dc_max <= S.dc && dv_max <= S.dv && m <= S.mp && S.mp <= 2 * round_up(m, 32) &&
-            n + 1 <= S.np && n * 8 < 65536) { sv = v; break; }
+            n <= S.np && S.np * 8 < 65536) { sv = v; break; }
     }
     std::vector<uint16_t> colB;
     std::vector<uint32_t> vneB;
     if (sv >= 0) {
         const SlotVariant& S = kSlotVariants[sv];
-        colB.assign((size_t)S.dc * S.mp, (uint16_t)(n * 8));
+        colB.assign((size_t)S.dc * S.mp, (uint16_t)(S.np * 8));   // padding -> sentinel qubit NP
         for (int i = 0; i < m; ++i)
             for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
                 colB[(size_t)(e - row_ptr[i]) * S.mp + i] = (uint16_t)(col_idx[e] * 8);
