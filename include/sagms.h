@@ -157,6 +157,32 @@ int sagms_decode_host(const sagms_code* code, const sagms_params* params, int64_
                       const uint32_t* h_syn, const float* h_L0, uint32_t* h_err, uint8_t* h_conv,
                       int32_t* h_iters);
 
+/*
+ * sagms_decode without any device allocation.  (The paper has no counterpart: this is a
+ * deployment variant of sagms_decode.)
+ *
+ * For callers that cannot allocate device memory while decoding: latency-critical serving
+ * threads (cudaMalloc, and cudaMallocAsync when its pool grows, can synchronise or stall
+ * the device), processes confined to a device-memory budget fixed at start-up, and host
+ * frameworks that own every allocation.  Arguments, layouts and results are those of
+ * sagms_decode; results are identical.  The only scratch -- the shot counters the
+ * two-slot kernel claims shots from -- is a fixed array of SAGMS_NOALLOC_COUNTERS ints in
+ * the library's device memory, one counter per launch of up to 2^31 - 1 shots, so at most
+ * SAGMS_NOALLOC_COUNTERS * (2^31 - 1) shots per call; larger batches get SAGMS_ERR_SIZE.
+ * Every GPU that loads the library keeps the array until the process exits.
+ *   - The first call on a device looks the array's device address up (with that device
+ *     current); make that first call before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents.  Each call zeroes the
+ *     counters it uses on `stream` before launching, so calls that overlap on the GPU (other
+ *     streams, other host threads) race: serialise them.
+ *   - The call itself allocates nothing: no cudaMalloc / cudaMallocAsync / cudaFree.
+ * Errors: as sagms_decode, plus SAGMS_ERR_SIZE for batches beyond the fixed scratch.
+ */
+#define SAGMS_NOALLOC_COUNTERS 64
+int sagms_decode_noalloc(const sagms_code* code, const sagms_params* params, int64_t shots,
+                         const uint32_t* d_syn, const float* d_L0, uint32_t* d_err, uint8_t* d_conv,
+                         int32_t* d_iters, void* stream);
+
 /* Eq. 9: alpha*(L0, d_c) = 2 atanh(tanh(L0/2)^(d_c - 1)) / L0, the SMS scale matching one
  * BP CN update under uniform inputs (Remark 1).  Returns NaN for L0 <= 0 or d_c < 2. */
 double sagms_alpha_star(double L0, int32_t dc);

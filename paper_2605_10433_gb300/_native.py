@@ -50,6 +50,7 @@ def _load_library():
         "sagms_decode": (ctypes.c_int, [vp, P(sagms_params), i64, vp, vp, vp, vp, vp, vp]),
         "sagms_decode_trace": (ctypes.c_int, [vp, P(sagms_params), i64, vp, vp, vp, vp, vp, vp, vp]),
         "sagms_decode_host": (ctypes.c_int, [vp, P(sagms_params), i64, vp, vp, vp, vp, vp]),
+        "sagms_decode_noalloc": (ctypes.c_int, [vp, P(sagms_params), i64, vp, vp, vp, vp, vp, vp]),
         "sagms_alpha_star": (ctypes.c_double, [ctypes.c_double, i32]),
         "sagms_last_error_string": (ctypes.c_char_p, []),
         "sagms_version": (ctypes.c_char_p, []),
@@ -113,6 +114,12 @@ def sagms_decode_trace(handle, params, shots, syn_ptr, L0_ptr, err_ptr, conv_ptr
 def sagms_decode_host(handle, params, shots, syn_ptr, L0_ptr, err_ptr, conv_ptr, iters_ptr):
     _check(_lib.sagms_decode_host(handle, ctypes.byref(params), int(shots), syn_ptr, L0_ptr, err_ptr, conv_ptr,
                                   iters_ptr))
+
+
+def sagms_decode_noalloc(handle, params, shots, syn_ptr, L0_ptr, err_ptr, conv_ptr, iters_ptr, stream_ptr):
+    """sagms_decode for callers that cannot allocate device memory (fixed library scratch)."""
+    _check(_lib.sagms_decode_noalloc(handle, ctypes.byref(params), int(shots), syn_ptr, L0_ptr, err_ptr, conv_ptr,
+                                     iters_ptr, stream_ptr))
 
 
 def sagms_alpha_star(L0: float, dc: int) -> float:

@@ -467,4 +467,121 @@ int sagms_decode_host(const sagms_code* code, const sagms_params* params, int64_
     return rc;
 }
 
+// ---------------------------------------------------------------------------------------
+// Allocation-free decoding.
+//
+// Some callers cannot allocate device memory while they decode: latency-critical serving
+// threads (cudaMalloc and pool growth of cudaMallocAsync can synchronise or stall the
+// device), processes that run under a fixed device-memory budget reserved at start-up, and
+// host frameworks that own every allocation themselves.  sagms_decode_noalloc takes its
+// only scratch -- the per-launch shot counters the two-slot kernel claims shots from -- from
+// this file-scope array instead of allocating it.  Every GPU that loads the library holds
+// the array until the process exits.  All calls share it and it keeps the last call's
+// contents; each call zeroes the counters it uses on its stream before launching, so calls
+// that overlap on the GPU (different streams, or different host threads) race on it.
+constexpr int kNoAllocCounters = SAGMS_NOALLOC_COUNTERS;
+static __device__ __align__(256) int g_noalloc_scratch[kNoAllocCounters];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+int* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of g_noalloc_scratch on the current device `dev`.  In host code the array's
+// name is only a host-side stand-in, so its device address must come from the runtime; that
+// lookup happens once per device, with that device current, at the device's first call.
+int noalloc_scratch(int dev, int** out) {
+    if (dev < 0 || dev >= kMaxDevices) return fail(SAGMS_ERR_ARG, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        int* ptr = nullptr;
+        const cudaError_t ce = cudaGetSymbolAddress(reinterpret_cast<void**>(&ptr), g_noalloc_scratch);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetSymbolAddress(no-alloc scratch)");
+        g_noalloc_ptr[dev] = ptr;
+    }
+    *out = g_noalloc_ptr[dev];
+    return SAGMS_OK;
+}
+
+}  // namespace
+
+int sagms_decode_noalloc(const sagms_code* code, const sagms_params* p, int64_t shots, const uint32_t* d_syn,
+                         const float* d_L0, uint32_t* d_err, uint8_t* d_conv, int32_t* d_iters, void* stream_v) {
+    if (!code) return fail(SAGMS_ERR_ARG, "code is NULL");
+    int rc = sagms_check_params(p);
+    if (rc != SAGMS_OK) return rc;
+    if (shots < 0) return fail(SAGMS_ERR_ARG, "shots < 0");
+    if (shots == 0) return SAGMS_OK;
+    if (!d_syn || !d_L0 || !d_err || !d_conv || !d_iters) return fail(SAGMS_ERR_ARG, "NULL device buffer");
+    const long long kMaxChunk = 0x7fffffffLL;
+    if (shots > kMaxChunk * kNoAllocCounters)
+        return fail(SAGMS_ERR_SIZE, "sagms_decode_noalloc: %lld shots exceed the fixed scratch (%d counters of %lld shots)",
+                    (long long)shots, kNoAllocCounters, kMaxChunk);
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    const bool bp = p->mode == SAGMS_BP;
+    const bool use_slots = !bp && code->slot_variant >= 0 && !(p->flags & SAGMS_FLAG_GENERIC_KERNEL);
+    if (!use_slots)   // the one-shot-per-CTA kernel uses no scratch and allocates nothing
+        return launch_decode(code, p, shots, d_syn, d_L0, d_err, d_conv, d_iters, nullptr, stream);
+
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
+    if (dev != code->device) return fail(SAGMS_ERR_ARG, "code was loaded on device %d, current is %d", code->device, dev);
+    int* scratch = nullptr;
+    rc = noalloc_scratch(dev, &scratch);
+    if (rc != SAGMS_OK) return rc;
+
+    const bool per_qubit = (p->flags & SAGMS_FLAG_L0_PER_QUBIT) != 0;
+    const SlotVariant& S = kSlotVariants[code->slot_variant];
+    SlotFn fn = slot_kernel_for(code->slot_variant);
+    const size_t smem = slot_smem_bytes(S.dc, S.dv, S.mp, S.np, per_qubit);
+    int smem_optin = 0, sms = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (smem > (size_t)smem_optin)
+        return fail(SAGMS_ERR_SIZE, "code needs %zu B of shared memory per CTA (limit %d)", smem, smem_optin);
+    ce = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaFuncSetAttribute");
+    int per_sm = 0;
+    ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void*>(fn), S.mp, smem);
+    if (ce != cudaSuccess) return cuda_fail(ce, "occupancy query");
+    if (per_sm < 1) return fail(SAGMS_ERR_SIZE, "kernel does not fit on an SM");
+
+    const long long nchunks = (shots + kMaxChunk - 1) / kMaxChunk;
+    ce = cudaMemsetAsync(scratch, 0, (size_t)nchunks * sizeof(int), stream);   // counters start at zero
+    if (ce != cudaSuccess) return cuda_fail(ce, "no-alloc scratch reset");
+    DecodeArgs a;
+    a.colT = code->d_colT;
+    a.vneT = code->d_vneT;
+    a.m = code->m; a.n = code->n; a.Mp = code->Mp; a.Np = code->Np;
+    a.mode = p->mode;
+    a.alpha = p->alpha;
+    a.amin = p->alpha_min;
+    a.amax = p->alpha_max;
+    a.eta = (p->eta_unsat == 0.0f) ? 1.10f : p->eta_unsat;
+    a.inv_m = 1.0f / (float)code->m;
+    a.max_iter = p->max_iter;
+    a.flags = p->flags;
+    a.trace = nullptr;
+    const SlotLayout lay{code->d_colB, code->d_vneB};
+    const int mw = (code->m + 31) / 32, nw = (code->n + 31) / 32;
+    const long long grid = (long long)per_sm * sms;
+    for (long long s0 = 0, ci = 0; s0 < shots; s0 += kMaxChunk, ++ci) {
+        const long long cnt = std::min(kMaxChunk, shots - s0);
+        a.shots = cnt;
+        a.syn = d_syn + s0 * mw;
+        a.L0 = per_qubit ? d_L0 : d_L0 + s0;
+        a.err = d_err + s0 * nw;
+        a.conv = d_conv + s0;
+        a.iters = d_iters + s0;
+        a.work = scratch + ci;
+        const long long g = std::min(grid, (cnt + 1) / 2);
+        fn<<<(unsigned)g, S.mp, smem, stream>>>(a, lay);
+    }
+    ce = cudaGetLastError();
+    if (ce != cudaSuccess) return cuda_fail(ce, "decode launch");
+    return SAGMS_OK;
+}
+
 }  // extern "C"
