@@ -167,8 +167,9 @@ int sagms_decode_host(const sagms_code* code, const sagms_params* params, int64_
  * frameworks that own every allocation.  Arguments, layouts and results are those of
  * sagms_decode; results are identical.  The only scratch -- the shot counters the
  * two-slot kernel claims shots from -- is a fixed array of SAGMS_NOALLOC_COUNTERS ints in
- * the library's device memory, one counter per launch of up to 2^31 - 1 shots, so at most
- * SAGMS_NOALLOC_COUNTERS * (2^31 - 1) shots per call; larger batches get SAGMS_ERR_SIZE.
+ * the library's device memory, one counter per launch of up to (2^31 - 1) / W shots
+ * (W = max(ceil(m/32), ceil(n/32)) words per pattern; 33.5 million shots at n = 2046), so
+ * at most SAGMS_NOALLOC_COUNTERS times that per call; larger batches get SAGMS_ERR_SIZE.
  * Every GPU that loads the library keeps the array until the process exits.
  *   - The first call on a device looks the array's device address up (with that device
  *     current); make that first call before any stream capture.

@@ -25,9 +25,8 @@
 
 namespace sagms {
 
-// Paired FP32 add / subtract (round to nearest); a - b is a + (-b) exactly.
+// Paired FP32 add (round to nearest).
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 
 struct SlotLayout {
     const uint16_t* colB;  // [DC][MP]
@@ -89,6 +88,10 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
     const int mw = (m + 31) >> 5, nw = (n + 31) >> 5;
     const float inf = __uint_as_float(0x7f800000u);
     const uint16_t pad = (uint16_t)(NP * 8);   // padding slots read the sentinel P2[NP] = +inf
+    // C2 holds NEGATED messages D = -L_{i->j}: the check node then forms P_j - L_{i->j} as the
+    // plain sum P_j + D, and the variable node sums Q = -L0 + sum D and stores P = -Q + 0.
+    // Round-to-nearest is symmetric under negation, so every value is bitwise the one of
+    // the unnegated formulation (decode_kernel.cuh), including +0 for an exact cancellation.
 
     {
         const int4* s1 = reinterpret_cast<const int4*>(lay.colB);
@@ -110,10 +113,12 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
     // check (Eq. 1) is s_i XOR flip_i with flip_i = parity of its negative priors:
     // per-qubit priors -> from PQ; a negative per-shot prior -> the check's degree parity.
     int pq_ok = 1;
+    int haspad_local = 0;
     {
         uint32_t f = 0u;
+        int d = DC;
         if (t < m) {
-            int d = 0;
+            d = 0;
 #pragma unroll
             for (int j = 0; j < DC; ++j) {
                 const uint16_t off = colB[j * MP + t];
@@ -126,6 +131,7 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
         }
         const uint32_t w = __ballot_sync(0xffffffffu, f);
         if (lane == 0) flipw[t >> 5] = w;
+        if (t < m && d < DC) haspad_local = 1;
         if (per_qubit) {
             for (int c = t; c < n; c += MP) pq_ok &= isfinite(PQ[c]) ? 1 : 0;
 #pragma unroll
@@ -138,28 +144,41 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
     }
 
     // Shot indices fit in 32 bits: the host splits larger batches into several launches.
-    // With a work counter, slots claim shots dynamically (thread 0, one atomic per shot, each
-    // claim made one refill ahead of its use and published through the shared ring `claim`);
-    // without one, slot k of CTA b takes shots 2b + k, 2b + k + 2G, ...
+    // A CTA takes its shots as chunks of 2^chunk_lg consecutive shots, assigned to its two
+    // slots in order.  With a work counter the chunks are claimed dynamically (thread 0,
+    // one atomic per chunk, a chunk ahead of its use, through the two-entry ring `claim`);
+    // without one, CTA b takes chunks b, b + G, b + 2G, ...
     const int nshots = (int)a.shots;
-    const int stride = 2 * (int)gridDim.x;
+    const int clg = a.chunk_lg;
+    const int cmask = (1 << clg) - 1;
     const bool dynamic = a.work != nullptr;
-    if (dynamic && t == 0) {
-        claim[0] = atomicAdd(a.work, 1);
-        claim[2] = atomicAdd(a.work, 1);
-        claim[1] = atomicAdd(a.work, 1);
-        claim[3] = atomicAdd(a.work, 1);
+    if (t == 0) {
+        claim[0] = dynamic ? atomicAdd(a.work, 1) : (int)blockIdx.x;
+        claim[1] = dynamic ? atomicAdd(a.work, 1) : (int)blockIdx.x + (int)gridDim.x;
     }
+    int seqp = 0;   // shots this CTA has assigned to its slots so far
     pq_ok = __syncthreads_and(pq_ok);
-    const int first0 = dynamic ? claim[0] : 2 * (int)blockIdx.x;
-    const int first1 = dynamic ? claim[2] : 2 * (int)blockIdx.x + 1;
+    const bool haspad = __syncthreads_or(haspad_local) != 0;   // some check has fewer than DC edges
+    // Next shot of this CTA's sequence.  Entering chunk c (c > 0) claims chunk c + 1 into the
+    // ring entry that held chunk c - 1, which is fully assigned; the claim has a whole chunk
+    // of refills to land before it is read.
+    auto assign = [&]() -> int {
+        const int p = seqp++;
+        const int c = p >> clg;
+        const long long idx = ((long long)claim[c & 1] << clg) + (p & cmask);
+        if ((p & cmask) == 0 && c > 0 && t == 0)
+            claim[(c + 1) & 1] = dynamic ? atomicAdd(a.work, 1) : (int)blockIdx.x + (c + 1) * (int)gridDim.x;
+        return idx < (long long)nshots ? (int)idx : nshots;
+    };
+    const int first0 = assign();
+    const int first1 = assign();
     if (t == 0) { pfidx[0] = first0; pfidx[2] = first1; }
     // Inputs of the shot a slot starts next (its syndrome row and prior) are copied into
     // shared memory by warp 0 with cp.async one refill ahead, double-buffered per slot;
     // warp 0 waits for its copies before each CTA barrier that precedes their use.
     auto prefetch = [&](int k, int b, int s) {
         if (t < 32 && s < nshots) {
-            if (lane < mw) cp_async4(pfsyn + (k * 2 + b) * 32 + lane, a.syn + (size_t)s * mw + lane);
+            if (lane < mw) cp_async4(pfsyn + (k * 2 + b) * 32 + lane, a.syn + s * mw + lane);
             if (lane == 0 && !per_qubit) cp_async4(pfl0 + k * 2 + b, a.L0 + s);
             cp_async_commit();
         }
@@ -173,7 +192,7 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
     int itk[2] = {0, 0};
     float prior[2] = {0.0f, 0.0f};
     uint32_t sbits = 0;  // bit k: this thread's check syndrome bit of slot k
-    uint32_t pbits = 0;  // bit k: prefetch buffer / claim-ring entry slot k reads next
+    uint32_t pbits = 0;  // bit k: prefetch buffer slot k reads at its next refill
 
     int ph = 0;
     while (state[0] != kDone || state[1] != kDone) {
@@ -209,6 +228,7 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
 
         // A6 per slot: the common case (both slots decoding, neither finished) is one test.
         bool zero[2] = {false, false};
+        uint32_t fresh = 0u;   // bit k: slot k runs the first round of a newly loaded shot
         const bool fin0 = state[0] == kActive && ((gcnt[0] == 0 && early) || itk[0] == a.max_iter);
         const bool fin1 = state[1] == kActive && ((gcnt[1] == 0 && early) || itk[1] == a.max_iter);
         if (!(fin0 || fin1 || state[0] != kActive || state[1] != kActive)) {
@@ -219,7 +239,7 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
             for (int k = 0; k < 2; ++k) {
                 const bool fin = k ? fin1 : fin0;
                 if (fin) {
-                    const size_t s = (size_t)shotsm[2 * k + (((pbits >> k) & 1) ^ 1)];
+                    const int s = shotsm[2 * k + (((pbits >> k) & 1) ^ 1)];
 #pragma unroll
                     for (int vv = 0; vv < VPT; ++vv) {
                         const int c = vv * MP + t;
@@ -240,9 +260,8 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
                 const int b = (pbits >> k) & 1;
                 const int s = pfidx[2 * k + b];
                 if (s >= nshots) { state[k] = kDone; continue; }
-                const int nx = dynamic ? claim[2 * k + (b ^ 1)] : s + stride;
+                const int nx = assign();
                 if (t == 0) {
-                    if (dynamic) claim[2 * k + b] = (nx < nshots) ? atomicAdd(a.work, 1) : nshots;
                     pfidx[2 * k + (b ^ 1)] = nx;
                     shotsm[2 * k + b] = s;
                 }
@@ -253,7 +272,7 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
                 const uint32_t word = (lane < mw) ? row[lane] : 0u;
                 prefetch(k, b ^ 1, nx);
                 if (!(per_qubit ? (pq_ok != 0) : isfinite(l0))) {
-                    for (int w = t; w < nw; w += MP) a.err[(size_t)s * nw + w] = 0u;
+                    for (int w = t; w < nw; w += MP) a.err[s * nw + w] = 0u;
                     if (t == 0) { a.conv[s] = 0; a.iters[s] = -1; }
                     continue;
                 }
@@ -273,24 +292,19 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
                         uint32_t e0;
                         if (per_qubit) e0 = negw[w];
                         else e0 = (pi < 0.0f) ? ((w == nw - 1 && (n & 31)) ? ((1u << (n & 31)) - 1u) : 0xffffffffu) : 0u;
-                        a.err[(size_t)s * nw + w] = e0;
+                        a.err[s * nw + w] = e0;
                     }
                     if (t == 0) { a.conv[s] = (c0 == 0) ? 1 : 0; a.iters[s] = 0; }
                     continue;
                 }
-                // Round 1 runs now: its inputs are the priors themselves (C = 0), Eq. 2 at l = 1.
+                // Round 1 runs now: its inputs are the priors themselves (C = 0), Eq. 2 at l = 1;
+                // the check-node phase substitutes them for this slot.
                 state[k] = kActive;
                 itk[k] = 1;
                 zero[k] = false;
+                fresh |= 1u << k;
                 gcnt[k] = c0;
                 gst[k] = bit ^ ((flipped && t < m) ? ((flipw[t >> 5] >> (t & 31)) & 1u) : 0u);
-#pragma unroll
-                for (int j = 0; j < DC; ++j) {
-                    const uint16_t off = colB[j * MP + t];
-                    const float pv = (off == pad) ? inf : (per_qubit ? PQ[off >> 3] : pi);
-                    if (k) { v[j].y = pv; C2[j * MP + t].y = 0.0f; }
-                    else { v[j].x = pv; C2[j * MP + t].x = 0.0f; }
-                }
             }
             if (state[0] == kDone && state[1] == kDone) break;
         }
@@ -305,12 +319,28 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
             g1 = a.alpha;
         }
         // A3 check-node update for both slots
+#pragma unroll
+        for (int j = 0; j < DC; ++j) v[j] = add2(v[j], C2[j * MP + t]);   // P - L_old (C2 is negated)
+        if (fresh) {
+            // A freshly loaded slot's round-1 inputs are its priors (+inf on padding slots).
+#pragma unroll
+            for (int j = 0; j < DC; ++j) {
+                float p0 = prior[0], p1 = prior[1];
+                if (per_qubit || haspad) {
+                    const uint16_t off = colB[j * MP + t];
+                    const float pq = per_qubit ? PQ[off >> 3] : ((off == pad) ? inf : 0.0f);
+                    p0 = per_qubit ? pq : ((off == pad) ? inf : p0);
+                    p1 = per_qubit ? pq : ((off == pad) ? inf : p1);
+                }
+                if (fresh & 1u) v[j].x = p0;
+                if (fresh & 2u) v[j].y = p1;
+            }
+        }
         uint32_t par0 = (sbits & 1u) << 31, par1 = (sbits >> 1) << 31;
 #pragma unroll
-        for (int j = 0; j < DC; ++j) {
-            v[j] = sub2(v[j], C2[j * MP + t]);
-            par0 ^= __float_as_uint(v[j].x);
-            par1 ^= __float_as_uint(v[j].y);
+        for (int j = 0; j < DC; j += 2) {
+            par0 ^= __float_as_uint(v[j].x) ^ __float_as_uint(v[j + 1].x);
+            par1 ^= __float_as_uint(v[j].y) ^ __float_as_uint(v[j + 1].y);
         }
         par0 &= kSign;
         par1 &= kSign;
@@ -331,26 +361,29 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
         for (int j = 0; j < DC; ++j) {
             const float ma = (fabsf(v[j].x) == m1a) ? o2a : o1a;
             const float mb = (fabsf(v[j].y) == m1b) ? o2b : o1b;
-            C2[j * MP + t] = make_float2(__uint_as_float(__float_as_uint(ma) ^ (__float_as_uint(v[j].x) & kSign)),
-                                         __uint_as_float(__float_as_uint(mb) ^ (__float_as_uint(v[j].y) & kSign)));
+            // store D = -L_{i->j}: the sign of the output flipped once more
+            C2[j * MP + t] = make_float2(__uint_as_float(__float_as_uint(ma) ^ (~__float_as_uint(v[j].x) & kSign)),
+                                         __uint_as_float(__float_as_uint(mb) ^ (~__float_as_uint(v[j].y) & kSign)));
         }
         __syncthreads();
 
         // A4 variable-node update for both slots (qubits past n compute on the zero slot and
         // are never read: no bounds test in the loop)
-        const float2 pr = make_float2(prior[0], prior[1]);
+        const float2 npr = make_float2(-prior[0], -prior[1]);
 #pragma unroll
         for (int vv = 0; vv < VPT; ++vv) {
             const int c = vv * MP + t;
-            float2 acc = pr;
+            float2 acc = npr;
             if (per_qubit) {
-                const float p = PQ[c];
+                const float p = -PQ[c];
                 acc = make_float2(p, p);
             }
 #pragma unroll
             for (int q = 0; q < DV; ++q)
                 acc = add2(acc, *reinterpret_cast<const float2*>(c2base + vneB[q * NP + c]));
-            P2[c] = acc;
+            // P = -Q exactly, with either zero mapped to +0 (a posterior of -0.0 would read as a
+            // negative sign bit): -Q + 0 by one fused multiply-add per pair.
+            P2[c] = __ffma2_rn(acc, make_float2(-1.0f, -1.0f), make_float2(0.0f, 0.0f));
         }
         __syncthreads();
         ph ^= 1;

@@ -67,6 +67,21 @@ KernelFn kernel_for(int variant, bool bp) {
 
 int round_up(int x, int k) { return (x + k - 1) / k * k; }
 
+// Largest launch of the two-slot kernel: its per-shot indexing (shot * words per pattern)
+// stays within 32-bit integers.
+long long max_slot_chunk(int m, int n) {
+    const long long words = std::max((m + 31) / 32, (n + 31) / 32);
+    return 0x7fffffffLL / std::max(1LL, words);
+}
+
+// Shots per claimed chunk of the two-slot kernel (log2): about eight chunks per CTA, at
+// least 2 shots (the claim ring needs a chunk of slack per refill round) and at most 16.
+int chunk_lg_for(long long shots, long long grid) {
+    int lg = 1;
+    while (lg < 4 && (shots >> (lg + 1)) >= grid * 8) ++lg;
+    return lg;
+}
+
 // Two-slot MS-family kernels with compile-time layout: (DC, DV, MP threads, NP qubit slots).
 struct SlotVariant { int dc, dv, mp, np; };
 constexpr SlotVariant kSlotVariants[] = {
@@ -318,6 +333,7 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     a.shots = shots;
     a.syn = d_syn; a.L0 = d_L0; a.err = d_err; a.conv = d_conv; a.iters = d_iters; a.trace = d_trace;
     a.work = nullptr;
+    a.chunk_lg = 1;
 
     const bool use_slots = !bp && code->slot_variant >= 0 && !(p->flags & SAGMS_FLAG_GENERIC_KERNEL);
     int dev = 0;
@@ -353,11 +369,12 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     if (per_sm < 1) return fail(SAGMS_ERR_SIZE, "kernel does not fit on an SM");
     const long long grid = std::min<long long>(units, (long long)per_sm * sms);
     if (use_slots) {
-        // 32-bit shot indices inside the kernel: split batches beyond 2^31 - 1 shots.  Each
+        // 32-bit shot indexing inside the kernel: split batches into launches of at most
+        // max_slot_chunk shots.  Each
         // launch gets a zeroed shot counter (scratch from the stream-ordered pool) that its
         // CTAs claim shots from.
         SlotLayout lay{code->d_colB, code->d_vneB};
-        const long long kMaxChunk = 0x7fffffffLL;
+        const long long kMaxChunk = max_slot_chunk(code->m, code->n);
         const long long nchunks = (shots + kMaxChunk - 1) / kMaxChunk;
         int* d_work = nullptr;
         ce = cudaMallocAsync(reinterpret_cast<void**>(&d_work), (size_t)nchunks * sizeof(int), stream);
@@ -380,6 +397,7 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
             c.trace = a.trace ? a.trace + s0 * (long long)(a.max_iter + 1) * code->n : nullptr;
             c.work = d_work + ci;
             const long long g = std::min(grid, (cnt + 1) / 2);
+            c.chunk_lg = chunk_lg_for(cnt, g);
             slot_kernel_for(code->slot_variant)<<<(unsigned)g, threads, smem, stream>>>(c, lay);
         }
         ce = cudaGetLastError();
@@ -474,7 +492,7 @@ int sagms_decode_host(const sagms_code* code, const sagms_params* params, int64_
 // threads (cudaMalloc and pool growth of cudaMallocAsync can synchronise or stall the
 // device), processes that run under a fixed device-memory budget reserved at start-up, and
 // host frameworks that own every allocation themselves.  sagms_decode_noalloc takes its
-// only scratch -- the per-launch shot counters the two-slot kernel claims shots from -- from
+// only scratch -- the per-launch chunk counters the two-slot kernel claims shots from -- from
 // this file-scope array instead of allocating it.  Every GPU that loads the library holds
 // the array until the process exits.  All calls share it and it keeps the last call's
 // contents; each call zeroes the counters it uses on its stream before launching, so calls
@@ -514,7 +532,7 @@ int sagms_decode_noalloc(const sagms_code* code, const sagms_params* p, int64_t 
     if (shots < 0) return fail(SAGMS_ERR_ARG, "shots < 0");
     if (shots == 0) return SAGMS_OK;
     if (!d_syn || !d_L0 || !d_err || !d_conv || !d_iters) return fail(SAGMS_ERR_ARG, "NULL device buffer");
-    const long long kMaxChunk = 0x7fffffffLL;
+    const long long kMaxChunk = max_slot_chunk(code->m, code->n);
     if (shots > kMaxChunk * kNoAllocCounters)
         return fail(SAGMS_ERR_SIZE, "sagms_decode_noalloc: %lld shots exceed the fixed scratch (%d counters of %lld shots)",
                     (long long)shots, kNoAllocCounters, kMaxChunk);
@@ -577,6 +595,7 @@ int sagms_decode_noalloc(const sagms_code* code, const sagms_params* p, int64_t 
         a.iters = d_iters + s0;
         a.work = scratch + ci;
         const long long g = std::min(grid, (cnt + 1) / 2);
+        a.chunk_lg = chunk_lg_for(cnt, g);
         fn<<<(unsigned)g, S.mp, smem, stream>>>(a, lay);
     }
     ce = cudaGetLastError();
