@@ -128,6 +128,45 @@ def profile_traffic(shots_per_launch):
         return None
 
 
+def bench_mixed_degree(S, I, steps, shots_per_code=1_000_000):
+    """Mixed-degree batching: GB l=255 (n=510) with w in {3,4,5,6,8} (check degree 6..16),
+    p=0.02, SAGMS max_iter=100, 1e6 shots per code in one CUDA-graph launch of a multi-code
+    decode; each code's launch plan autotuned on a 1e5-shot sample first."""
+    import torch
+    p = S.Params(mode="sagms", max_iter=MAX_ITER, **SAGMS_KW)
+    jobs, plans = [], {}
+    for w in (3, 4, 5, 6, 8):
+        c = I.gb_code(255, w)
+        _, syn, L0, _ = I.workload(c, [0.02], shots_per_code, seed=NOISE_SEED + w)
+        dc = S.DeviceCode.from_code(c)
+        d_syn = torch.from_numpy(syn.view(np.int32)).cuda()
+        d_L0 = torch.from_numpy(L0).cuda()
+        plan, rate = S.autotune(dc, d_syn[:100000], d_L0[:100000], p)
+        plans[f"w={w}"] = {**S.decode_plan(plan), "sample_shots_per_s": rate}
+        jobs.append(S.Job(dc, d_syn, d_L0, p))
+    g = S.Graph(jobs)
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        g.launch(stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        g.launch(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    total = shots_per_code * len(jobs) * steps
+    fer = {f"w={w}": float((j.conv == 0).float().mean().item()) for w, j in zip((3, 4, 5, 6, 8), jobs)}
+    iters = {f"w={w}": float(j.iters.float().mean().item()) for w, j in zip((3, 4, 5, 6, 8), jobs)}
+    g.close()
+    return {"workload": "GB l=255 (n=510) w in {3,4,5,6,8}, 1e6 shots per code, p=0.02, SAGMS max_iter=100, "
+                        "one CUDA-graph launch of sagms_decode_multi per step",
+            "shots_per_s": total / (ms / 1e3), "ms_per_launch": ms / steps, "launches": steps,
+            "plans": plans, "fer_syn": fer, "mean_iters": iters}
+
+
 def cpu_oracle_sample(code, syn, L0, shots, threads):
     import oracle
     t0 = time.perf_counter()
@@ -300,6 +339,8 @@ def main():
         out["modes"] = modes
         step(sagms)
         torch.cuda.synchronize()
+        if world == 1:
+            out["config3_mixed_degree"] = bench_mixed_degree(S, I, args.mode_steps)
 
     # e2e: the C-ABI host entry point, host<->device copies inside the timed region
     h_syn = torch.from_numpy(syn.view(np.int32)).pin_memory()

@@ -184,6 +184,52 @@ int sagms_decode_noalloc(const sagms_code* code, const sagms_params* params, int
                          const uint32_t* d_syn, const float* d_L0, uint32_t* d_err, uint8_t* d_conv,
                          int32_t* d_iters, void* stream);
 
+/*
+ * One decode of a batched, mixed-code launch: a code, its parameters and caller-owned
+ * device buffers with the layouts of sagms_decode.
+ */
+typedef struct {
+    const sagms_code* code;
+    sagms_params params;
+    int64_t shots;
+    const uint32_t* d_syn;
+    const float* d_L0;
+    uint32_t* d_err;
+    uint8_t* d_conv;
+    int32_t* d_iters;
+} sagms_job;
+
+/*
+ * Decode several batches of possibly different codes (different n and check degrees) in
+ * one call: each job runs the decoder of Algorithm 1 exactly as sagms_decode would, on its
+ * own library stream forked from `stream` and joined back into it, so the jobs overlap on
+ * the GPU and the whole call can be captured into one CUDA graph.  Asynchronous on
+ * `stream`.  Errors: as sagms_decode for any job.
+ */
+int sagms_decode_multi(const sagms_job* jobs, int32_t njobs, void* stream);
+
+/* A captured, instantiated CUDA graph of one sagms_decode_multi call over fixed buffers. */
+typedef struct sagms_graph sagms_graph;
+int sagms_graph_create(const sagms_job* jobs, int32_t njobs, sagms_graph** out);
+int sagms_graph_launch(sagms_graph* graph, void* stream);   /* asynchronous on `stream` */
+void sagms_graph_destroy(sagms_graph* graph);
+
+/*
+ * Launch-plan autotuning (not part of the method: it picks how the decoder is launched).
+ * Decodes the caller's sample batch (buffers as in sagms_decode; the outputs are
+ * overwritten) under each candidate plan -- kernel family (two-slot continuous batching or
+ * one shot per CTA), CTAs per SM, shots per claimed chunk -- times them with CUDA events on
+ * `stream` (synchronising it), stores the fastest in the code handle for later decodes, and
+ * returns it in *plan (packed; sagms_set_plan accepts it) with its rate in *shots_per_s.
+ * Results of a decode do not depend on the plan.  With the environment variable
+ * SAGMS_AUTOTUNE_CACHE naming a file, the plan is also appended there and sagms_load_code
+ * of the same matrix starts from it.
+ */
+int sagms_autotune(const sagms_code* code, const sagms_params* params, int64_t shots,
+                   const uint32_t* d_syn, const float* d_L0, uint32_t* d_err, uint8_t* d_conv,
+                   int32_t* d_iters, int32_t* plan, float* shots_per_s, void* stream);
+int sagms_set_plan(sagms_code* code, int32_t plan);   /* 0 restores the defaults */
+
 /* Eq. 9: alpha*(L0, d_c) = 2 atanh(tanh(L0/2)^(d_c - 1)) / L0, the SMS scale matching one
  * BP CN update under uniform inputs (Remark 1).  Returns NaN for L0 <= 0 or d_c < 2. */
 double sagms_alpha_star(double L0, int32_t dc);

@@ -130,3 +130,74 @@ def decode_host(code: DeviceCode, syn, L0, params: Params | None = None, out=Non
         err, conv, iters = out
     _native.sagms_decode_host(code.handle, params.to_c(), shots, ptr(syn), ptr(L0), ptr(err), ptr(conv), ptr(iters))
     return err, conv, iters
+
+
+def decode_plan(plan: int) -> dict:
+    """Unpack a launch plan returned by sagms_autotune."""
+    return {"kernel": {0: "auto", 1: "one-shot-per-CTA", 2: "two-slot"}.get(plan & 3, "?"),
+            "ctas_per_sm": (plan >> 8) & 0xff, "chunk_lg": (plan >> 16) & 0xf}
+
+
+class Job:
+    """One batch of a mixed-code launch (sagms_decode_multi / sagms_graph_*): a loaded code,
+    parameters and device tensors (outputs allocated here unless given)."""
+
+    def __init__(self, code: DeviceCode, syn, L0, params: Params | None = None, out=None):
+        import torch
+        self.code, self.syn, self.L0 = code, syn, L0
+        self.params = params or Params()
+        shots = syn.shape[0]
+        if out is None:
+            out = (torch.empty((shots, code.nw), dtype=torch.int32, device=syn.device),
+                   torch.empty((shots,), dtype=torch.uint8, device=syn.device),
+                   torch.empty((shots,), dtype=torch.int32, device=syn.device))
+        self.err, self.conv, self.iters = out
+
+    def to_c(self):
+        from . import _native
+        return _native.sagms_job(self.code.handle, self.params.to_c(), self.syn.shape[0], self.syn.data_ptr(),
+                                 self.L0.data_ptr(), self.err.data_ptr(), self.conv.data_ptr(), self.iters.data_ptr())
+
+
+def decode_multi(jobs, stream=None):
+    """Run all jobs in one call (overlapping on the GPU); asynchronous on ``stream``."""
+    from . import _native
+    _native.sagms_decode_multi([j.to_c() for j in jobs], _stream_ptr(stream))
+
+
+class Graph:
+    """A CUDA graph of one decode_multi over the jobs' fixed buffers; launch() replays it."""
+
+    def __init__(self, jobs):
+        from . import _native
+        self._native = _native
+        self.jobs = list(jobs)
+        self.handle = _native.sagms_graph_create([j.to_c() for j in self.jobs])
+
+    def launch(self, stream=None):
+        self._native.sagms_graph_launch(self.handle, _stream_ptr(stream))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._native.sagms_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(code: DeviceCode, syn, L0, params: Params | None = None, stream=None):
+    """Pick and store the fastest launch plan for this code on a sample batch; returns
+    (plan, shots/s)."""
+    import torch
+    from . import _native
+    params = params or Params()
+    shots = syn.shape[0]
+    err = torch.empty((shots, code.nw), dtype=torch.int32, device=syn.device)
+    conv = torch.empty((shots,), dtype=torch.uint8, device=syn.device)
+    iters = torch.empty((shots,), dtype=torch.int32, device=syn.device)
+    return _native.sagms_autotune(code.handle, params.to_c(), shots, syn.data_ptr(), L0.data_ptr(), err.data_ptr(),
+                                  conv.data_ptr(), iters.data_ptr(), _stream_ptr(stream))

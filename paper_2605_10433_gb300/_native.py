@@ -35,6 +35,12 @@ class sagms_params(ctypes.Structure):
                 ("flags", ctypes.c_uint32)]
 
 
+class sagms_job(ctypes.Structure):
+    _fields_ = [("code", ctypes.c_void_p), ("params", sagms_params), ("shots", ctypes.c_int64),
+                ("d_syn", ctypes.c_void_p), ("d_L0", ctypes.c_void_p), ("d_err", ctypes.c_void_p),
+                ("d_conv", ctypes.c_void_p), ("d_iters", ctypes.c_void_p)]
+
+
 def _load_library():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libsagms.so is not built ({LIB_PATH}); run __graft_entry__.build() "
@@ -51,6 +57,13 @@ def _load_library():
         "sagms_decode_trace": (ctypes.c_int, [vp, P(sagms_params), i64, vp, vp, vp, vp, vp, vp, vp]),
         "sagms_decode_host": (ctypes.c_int, [vp, P(sagms_params), i64, vp, vp, vp, vp, vp]),
         "sagms_decode_noalloc": (ctypes.c_int, [vp, P(sagms_params), i64, vp, vp, vp, vp, vp, vp]),
+        "sagms_decode_multi": (ctypes.c_int, [P(sagms_job), i32, vp]),
+        "sagms_graph_create": (ctypes.c_int, [P(sagms_job), i32, P(vp)]),
+        "sagms_graph_launch": (ctypes.c_int, [vp, vp]),
+        "sagms_graph_destroy": (None, [vp]),
+        "sagms_autotune": (ctypes.c_int, [vp, P(sagms_params), i64, vp, vp, vp, vp, vp, P(i32),
+                                          P(ctypes.c_float), vp]),
+        "sagms_set_plan": (ctypes.c_int, [vp, i32]),
         "sagms_alpha_star": (ctypes.c_double, [ctypes.c_double, i32]),
         "sagms_last_error_string": (ctypes.c_char_p, []),
         "sagms_version": (ctypes.c_char_p, []),
@@ -120,6 +133,38 @@ def sagms_decode_noalloc(handle, params, shots, syn_ptr, L0_ptr, err_ptr, conv_p
     """sagms_decode for callers that cannot allocate device memory (fixed library scratch)."""
     _check(_lib.sagms_decode_noalloc(handle, ctypes.byref(params), int(shots), syn_ptr, L0_ptr, err_ptr, conv_ptr,
                                      iters_ptr, stream_ptr))
+
+
+def sagms_decode_multi(jobs, stream_ptr):
+    arr = (sagms_job * len(jobs))(*jobs)
+    _check(_lib.sagms_decode_multi(arr, len(jobs), stream_ptr))
+
+
+def sagms_graph_create(jobs):
+    arr = (sagms_job * len(jobs))(*jobs)
+    g = ctypes.c_void_p()
+    _check(_lib.sagms_graph_create(arr, len(jobs), ctypes.byref(g)))
+    return g.value
+
+
+def sagms_graph_launch(graph, stream_ptr):
+    _check(_lib.sagms_graph_launch(graph, stream_ptr))
+
+
+def sagms_graph_destroy(graph):
+    _lib.sagms_graph_destroy(graph)
+
+
+def sagms_autotune(handle, params, shots, syn_ptr, L0_ptr, err_ptr, conv_ptr, iters_ptr, stream_ptr):
+    plan = ctypes.c_int32()
+    rate = ctypes.c_float()
+    _check(_lib.sagms_autotune(handle, ctypes.byref(params), int(shots), syn_ptr, L0_ptr, err_ptr, conv_ptr,
+                               iters_ptr, ctypes.byref(plan), ctypes.byref(rate), stream_ptr))
+    return plan.value, rate.value
+
+
+def sagms_set_plan(handle, plan):
+    _check(_lib.sagms_set_plan(handle, int(plan)))
 
 
 def sagms_alpha_star(L0: float, dc: int) -> float:

@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cstdlib>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -67,6 +68,40 @@ KernelFn kernel_for(int variant, bool bp) {
 
 int round_up(int x, int k) { return (x + k - 1) / k * k; }
 
+constexpr int kMaxDevices = 64;
+
+// Autotune cache: when SAGMS_AUTOTUNE_CACHE names a file, sagms_autotune appends
+// "<code fingerprint hex> <packed plan>" lines to it and sagms_load_code takes the last
+// plan recorded for the code's fingerprint.
+uint32_t cached_plan(uint64_t key) {
+    const char* path = std::getenv("SAGMS_AUTOTUNE_CACHE");
+    if (!path || !*path) return 0u;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return 0u;
+    unsigned long long k = 0;
+    unsigned int pl = 0;
+    uint32_t found = 0u;
+    while (std::fscanf(f, "%llx %u", &k, &pl) == 2)
+        if ((uint64_t)k == key) found = pl;
+    std::fclose(f);
+    return found;
+}
+
+void store_cached_plan(uint64_t key, uint32_t pl) {
+    const char* path = std::getenv("SAGMS_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%016llx %u\n", (unsigned long long)key, pl);
+    std::fclose(f);
+}
+
+struct Plan { int kernel, ctas_per_sm, chunk_lg; };
+Plan unpack_plan(uint32_t v) { return Plan{(int)(v & 3u), (int)((v >> 8) & 0xffu), (int)((v >> 16) & 0xfu)}; }
+uint32_t pack_plan(const Plan& p) {
+    return (uint32_t)(p.kernel & 3) | ((uint32_t)(p.ctas_per_sm & 0xff) << 8) | ((uint32_t)(p.chunk_lg & 0xf) << 16);
+}
+
 // Largest launch of the two-slot kernel: its per-shot indexing (shot * words per pattern)
 // stays within 32-bit integers.
 long long max_slot_chunk(int m, int n) {
@@ -118,6 +153,12 @@ struct sagms_code {
     int slot_variant;      // -1: no two-slot kernel for this shape
     uint16_t* d_colB;      // [DC][MP] byte offsets into P2
     uint32_t* d_vneB;      // [DV][NP] byte offsets into C2
+    // Launch plan chosen by sagms_autotune (0 = defaults), packed so decodes on other
+    // threads read it atomically: bits 0-1 kernel (0 auto, 1 one-shot-per-CTA, 2 two-slot),
+    // bits 8-15 CTAs per SM (0 = occupancy limit), bits 16-19 log2 shots per claimed chunk
+    // (0 = automatic).
+    mutable std::atomic<uint32_t> plan;
+    uint64_t shape_key;    // code fingerprint for the autotune cache
 };
 
 extern "C" {
@@ -254,6 +295,16 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
     code->slot_variant = sv;
     code->d_colB = nullptr;
     code->d_vneB = nullptr;
+    code->plan.store(0u);
+    {
+        uint64_t h = 1469598103934665603ull;   // FNV-1a over the CSR
+        auto mix = [&](uint64_t x) { h = (h ^ x) * 1099511628211ull; };
+        mix((uint64_t)m); mix((uint64_t)n); mix((uint64_t)nnz);
+        for (int i = 0; i <= m; ++i) mix((uint64_t)(uint32_t)row_ptr[i]);
+        for (int64_t e = 0; e < nnz; ++e) mix((uint64_t)(uint32_t)col_idx[e]);
+        code->shape_key = h;
+    }
+    code->plan.store(cached_plan(code->shape_key));
     code->m = m; code->n = n; code->nnz = (int)nnz;
     code->dc_max = dc_max; code->dv_max = dv_max;
     code->variant = variant; code->DC = DC; code->DV = DV;
@@ -309,7 +360,7 @@ namespace {
 
 int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, const uint32_t* d_syn,
                   const float* d_L0, uint32_t* d_err, uint8_t* d_conv, int32_t* d_iters, float* d_trace,
-                  cudaStream_t stream) {
+                  cudaStream_t stream, const Plan* plan_override = nullptr) {
     if (!code) return fail(SAGMS_ERR_ARG, "code is NULL");
     int rc = sagms_check_params(p);
     if (rc != SAGMS_OK) return rc;
@@ -335,7 +386,9 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     a.work = nullptr;
     a.chunk_lg = 1;
 
-    const bool use_slots = !bp && code->slot_variant >= 0 && !(p->flags & SAGMS_FLAG_GENERIC_KERNEL);
+    const Plan plan = plan_override ? *plan_override : unpack_plan(code->plan.load());
+    const bool use_slots = !bp && code->slot_variant >= 0 && !(p->flags & SAGMS_FLAG_GENERIC_KERNEL) &&
+                           plan.kernel != 1;
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
@@ -367,6 +420,7 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
     if (ce != cudaSuccess) return cuda_fail(ce, "occupancy query");
     if (per_sm < 1) return fail(SAGMS_ERR_SIZE, "kernel does not fit on an SM");
+    if (plan.ctas_per_sm > 0) per_sm = std::min(per_sm, plan.ctas_per_sm);
     const long long grid = std::min<long long>(units, (long long)per_sm * sms);
     if (use_slots) {
         // 32-bit shot indexing inside the kernel: split batches into launches of at most
@@ -397,7 +451,7 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
             c.trace = a.trace ? a.trace + s0 * (long long)(a.max_iter + 1) * code->n : nullptr;
             c.work = d_work + ci;
             const long long g = std::min(grid, (cnt + 1) / 2);
-            c.chunk_lg = chunk_lg_for(cnt, g);
+            c.chunk_lg = plan.chunk_lg > 0 ? plan.chunk_lg : chunk_lg_for(cnt, g);
             slot_kernel_for(code->slot_variant)<<<(unsigned)g, threads, smem, stream>>>(c, lay);
         }
         ce = cudaGetLastError();
@@ -502,7 +556,6 @@ static __device__ __align__(256) int g_noalloc_scratch[kNoAllocCounters];
 
 namespace {
 
-constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 int* g_noalloc_ptr[kMaxDevices] = {nullptr};
 
@@ -601,6 +654,160 @@ int sagms_decode_noalloc(const sagms_code* code, const sagms_params* p, int64_t 
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return cuda_fail(ce, "decode launch");
     return SAGMS_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Launch-plan autotuning, multi-code launches and CUDA graphs.
+
+int sagms_autotune(const sagms_code* code, const sagms_params* params, int64_t shots, const uint32_t* d_syn,
+                   const float* d_L0, uint32_t* d_err, uint8_t* d_conv, int32_t* d_iters, int32_t* out_plan,
+                   float* out_shots_per_s, void* stream_v) {
+    if (!code) return fail(SAGMS_ERR_ARG, "code is NULL");
+    int rc = sagms_check_params(params);
+    if (rc != SAGMS_OK) return rc;
+    if (shots <= 0) return fail(SAGMS_ERR_ARG, "autotune needs a sample of at least one shot");
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    int dev = 0, sms = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    std::vector<Plan> cands;
+    const bool slots_ok = params->mode != SAGMS_BP && code->slot_variant >= 0;
+    for (int kernel : {2, 1}) {
+        if (kernel == 2 && !slots_ok) continue;
+        for (int cps : {0, 2, 1}) {
+            if (kernel == 2) {
+                for (int clg : {0, 1, 2, 4}) cands.push_back(Plan{kernel, cps, clg});
+            } else {
+                cands.push_back(Plan{kernel, cps, 0});
+            }
+        }
+    }
+    cudaEvent_t e0, e1;
+    ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaEventCreate");
+    float best_ms = 0.0f;
+    Plan best{0, 0, 0};
+    bool have = false;
+    for (const Plan& pl : cands) {
+        rc = launch_decode(code, params, shots, d_syn, d_L0, d_err, d_conv, d_iters, nullptr, stream, &pl);  // warm-up
+        if (rc != SAGMS_OK) continue;
+        cudaEventRecord(e0, stream);
+        for (int r = 0; r < 3 && rc == SAGMS_OK; ++r)
+            rc = launch_decode(code, params, shots, d_syn, d_L0, d_err, d_conv, d_iters, nullptr, stream, &pl);
+        cudaEventRecord(e1, stream);
+        ce = cudaEventSynchronize(e1);
+        if (ce != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_fail(ce, "autotune sync"); }
+        if (rc != SAGMS_OK) continue;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (!have || ms < best_ms) { best_ms = ms; best = pl; have = true; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!have) return fail(SAGMS_ERR_CUDA, "autotune: no candidate plan launched");
+    const uint32_t packed = pack_plan(best);
+    code->plan.store(packed);
+    store_cached_plan(code->shape_key, packed);
+    if (out_plan) *out_plan = (int32_t)packed;
+    if (out_shots_per_s) *out_shots_per_s = (float)(3.0 * (double)shots / (best_ms * 1e-3));
+    return SAGMS_OK;
+}
+
+int sagms_set_plan(sagms_code* code, int32_t plan) {
+    if (!code) return fail(SAGMS_ERR_ARG, "code is NULL");
+    const Plan pl = unpack_plan((uint32_t)plan);
+    if (pl.kernel == 3) return fail(SAGMS_ERR_ARG, "unknown kernel field in plan 0x%x", (unsigned)plan);
+    code->plan.store((uint32_t)plan);
+    return SAGMS_OK;
+}
+
+int sagms_decode_multi(const sagms_job* jobs, int32_t njobs, void* stream_v) {
+    if (njobs < 0 || (njobs > 0 && !jobs)) return fail(SAGMS_ERR_ARG, "bad job list");
+    if (njobs == 0) return SAGMS_OK;
+    for (int i = 0; i < njobs; ++i) {
+        if (!jobs[i].code) return fail(SAGMS_ERR_ARG, "job %d: code is NULL", i);
+        const int rc = sagms_check_params(&jobs[i].params);
+        if (rc != SAGMS_OK) return rc;
+    }
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
+    // Library streams of this host thread (created once per thread and device): the jobs fork
+    // from the caller's stream onto them and join back, so the call is capturable as one graph.
+    constexpr int kSide = 8;
+    thread_local std::vector<cudaStream_t> side[kMaxDevices];
+    if (dev >= kMaxDevices) return fail(SAGMS_ERR_ARG, "device ordinal %d out of range", dev);
+    while ((int)side[dev].size() < kSide) {
+        cudaStream_t st;
+        ce = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamCreate");
+        side[dev].push_back(st);
+    }
+    const int used = std::min(njobs, kSide);
+    std::vector<cudaEvent_t> ev(used + 1, nullptr);
+    for (auto& e : ev) {
+        ce = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaEventCreate");
+    }
+    int rc = SAGMS_OK;
+    ce = cudaEventRecord(ev[0], stream);
+    for (int k = 0; k < used && ce == cudaSuccess; ++k) ce = cudaStreamWaitEvent(side[dev][k], ev[0], 0);
+    if (ce != cudaSuccess) rc = cuda_fail(ce, "multi fork");
+    for (int i = 0; i < njobs && rc == SAGMS_OK; ++i) {
+        const sagms_job& j = jobs[i];
+        rc = launch_decode(j.code, &j.params, j.shots, j.d_syn, j.d_L0, j.d_err, j.d_conv, j.d_iters, nullptr,
+                           side[dev][i % kSide]);
+    }
+    for (int k = 0; k < used; ++k) {
+        cudaEventRecord(ev[k + 1], side[dev][k]);
+        cudaStreamWaitEvent(stream, ev[k + 1], 0);
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    ce = cudaGetLastError();
+    if (rc == SAGMS_OK && ce != cudaSuccess) rc = cuda_fail(ce, "multi join");
+    return rc;
+}
+
+struct sagms_graph {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+int sagms_graph_create(const sagms_job* jobs, int32_t njobs, sagms_graph** out) {
+    if (!out) return fail(SAGMS_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    cudaStream_t st;
+    cudaError_t ce = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamCreate");
+    ce = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) { cudaStreamDestroy(st); return cuda_fail(ce, "begin capture"); }
+    int rc = sagms_decode_multi(jobs, njobs, st);
+    cudaGraph_t g = nullptr;
+    ce = cudaStreamEndCapture(st, &g);
+    cudaStreamDestroy(st);
+    if (rc != SAGMS_OK) { if (g) cudaGraphDestroy(g); return rc; }
+    if (ce != cudaSuccess) return cuda_fail(ce, "end capture");
+    cudaGraphExec_t ex = nullptr;
+    ce = cudaGraphInstantiate(&ex, g, 0);
+    if (ce != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(ce, "graph instantiate"); }
+    *out = new sagms_graph{g, ex};
+    return SAGMS_OK;
+}
+
+int sagms_graph_launch(sagms_graph* g, void* stream) {
+    if (!g) return fail(SAGMS_ERR_ARG, "graph is NULL");
+    const cudaError_t ce = cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream));
+    return ce == cudaSuccess ? SAGMS_OK : cuda_fail(ce, "graph launch");
+}
+
+void sagms_graph_destroy(sagms_graph* g) {
+    if (!g) return;
+    cudaGraphExecDestroy(g->exec);
+    cudaGraphDestroy(g->graph);
+    delete g;
 }
 
 }  // extern "C"
