@@ -167,6 +167,70 @@ def bench_mixed_degree(S, I, steps, shots_per_code=1_000_000):
             "plans": plans, "fer_syn": fer, "mean_iters": iters}
 
 
+def bench_serving(S, I, nreq=3000, load=0.6, seed=5):
+    """Serving loop: Poisson-arriving requests from GB codes n in {126, 510, 1022, 2046}
+    (w = 3/4/5/5), batch size floor(exp U[ln 1, ln 4096]), p ~ U[0.005, 0.03], SAGMS
+    max_iter=100.  Plain per-request launches (one stream, one request at a time) give the
+    capacity; the same arrival schedule at `load` x that capacity is then replayed through the
+    continuous-batching server and through plain launches.  Latency = completion - submit,
+    measured by the server's clock, host copies included."""
+    import torch
+    rng = np.random.default_rng(seed)
+    params = S.Params(mode="sagms", max_iter=MAX_ITER, **SAGMS_KW)
+    codes = [I.gb_code(l, w) for l, w in ((63, 3), (255, 4), (511, 5), (1023, 5))]
+    dcodes = [S.DeviceCode.from_code(c) for c in codes]
+    cid = rng.integers(0, len(codes), size=nreq)
+    shots = np.floor(np.exp(rng.uniform(0, np.log(4096), size=nreq))).astype(np.int64)
+    pv = rng.uniform(0.005, 0.03, size=nreq)
+    reqs = []
+    for k in range(len(codes)):
+        sel = np.nonzero(cid == k)[0]
+        tot = int(shots[sel].sum())
+        q = np.repeat(pv[sel], shots[sel])
+        _, syn = I.sample(codes[k], q, tot, seed=seed * 1000 + k)
+        L0 = I.llr_prior(q).astype(np.float32)
+        hs = torch.from_numpy(syn.view(np.int32)).pin_memory()
+        hl = torch.from_numpy(L0).pin_memory()
+        he = torch.empty((tot, dcodes[k].nw), dtype=torch.int32).pin_memory()
+        hc = torch.empty(tot, dtype=torch.uint8).pin_memory()
+        hi = torch.empty(tot, dtype=torch.int32).pin_memory()
+        off = 0
+        for i in sel:
+            n = int(shots[i])
+            reqs.append((int(i), k, (hs[off:off + n], hl[off:off + n], he[off:off + n], hc[off:off + n], hi[off:off + n])))
+            off += n
+    reqs.sort()
+    total = int(shots.sum())
+
+    def run(mode, arrival_ns):
+        srv = S.Server(mem_budget=512 << 20, max_inflight=16, mode=mode, shots_per_cta=16)
+        ids = [srv.add_code(dc, params) for dc in dcodes]
+        tickets = srv.replay([ids[k] for _, k, _ in reqs], [r for _, _, r in reqs], arrival_ns)
+        for t in tickets:
+            srv.wait(t, 300)
+        times = np.array([srv.times(t) for t in tickets], dtype=np.int64)
+        srv.close()
+        lat_us = (times[:, 1] - times[:, 0]) / 1e3
+        span = (times[:, 1].max() - times[:, 0].min()) / 1e9
+        return {"p50_us": float(np.percentile(lat_us, 50)), "p99_us": float(np.percentile(lat_us, 99)),
+                "mean_us": float(lat_us.mean()), "shots_per_s": total / span}
+
+    burst = np.zeros(nreq, dtype=np.int64)
+    run("plain", burst)   # warm-up
+    cap = run("plain", burst)["shots_per_s"]
+    rate_req = load * cap / shots.mean()
+    arrival = np.cumsum(rng.exponential(1.0 / rate_req, size=nreq)) * 1e9
+    arrival = (arrival - arrival[0]).astype(np.int64)
+    cont = run("continuous", arrival)
+    plain = run("plain", arrival)
+    return {"workload": f"{nreq} Poisson requests, GB n in {{126,510,1022,2046}}, batch floor(exp U[ln1,ln4096]) "
+                        f"(mean {shots.mean():.0f} shots), p~U[0.005,0.03], SAGMS max_iter=100, "
+                        f"offered load {load:.0%} of plain-launch capacity",
+            "plain_capacity_shots_per_s": cap, "offered_shots_per_s": rate_req * shots.mean(),
+            "continuous": cont, "plain": plain,
+            "p99_speedup_vs_plain": plain["p99_us"] / cont["p99_us"]}
+
+
 def cpu_oracle_sample(code, syn, L0, shots, threads):
     import oracle
     t0 = time.perf_counter()
@@ -341,6 +405,7 @@ def main():
         torch.cuda.synchronize()
         if world == 1:
             out["config3_mixed_degree"] = bench_mixed_degree(S, I, args.mode_steps)
+            out["serving"] = bench_serving(S, I)
 
     # e2e: the C-ABI host entry point, host<->device copies inside the timed region
     h_syn = torch.from_numpy(syn.view(np.int32)).pin_memory()

@@ -62,7 +62,8 @@ enum {
     SAGMS_ERR_CUDA = -6,    /* a CUDA runtime call failed (no device, launch failure, ...) */
     SAGMS_ERR_TIMEOUT = -7, /* a bounded wait ran out */
     SAGMS_ERR_BUSY = -8,    /* resource temporarily unavailable */
-    SAGMS_ERR_SIZE = -9     /* code too large for one CTA's shared memory / thread block */
+    SAGMS_ERR_SIZE = -9,    /* code too large for one CTA's shared memory / thread block */
+    SAGMS_ERR_CANCELLED = -10 /* serving: the request was cancelled before it ran */
 };
 
 #define SAGMS_MAX_DC 32     /* largest check degree |M(i)| */
@@ -229,6 +230,49 @@ int sagms_autotune(const sagms_code* code, const sagms_params* params, int64_t s
                    const uint32_t* d_syn, const float* d_L0, uint32_t* d_err, uint8_t* d_conv,
                    int32_t* d_iters, int32_t* plan, float* shots_per_s, void* stream);
 int sagms_set_plan(sagms_code* code, int32_t plan);   /* 0 restores the defaults */
+
+/*
+ * Serving loop (continuous batching; not part of the method).  A server accepts decode
+ * requests -- a registered code, a batch of syndromes and priors in host memory, host output
+ * buffers -- at any time from any host thread and runs them on the current device:
+ *   - Admission is in arrival order and gated by free device memory: every request's device
+ *     buffers come from one arena of `mem_budget` bytes allocated at creation (no request
+ *     allocates), and at most `max_inflight` requests are on the GPU at once.
+ *   - SAGMS_SERVE_CONTINUOUS: admitted requests run concurrently, each on its own stream
+ *     (copy in, decode, copy out); each decode's grid is capped at one CTA per
+ *     `shots_per_cta` shots so CTAs of newer requests take SMs as older CTAs retire, and
+ *     inside a CTA the decoder refills its shot slots as shots converge.
+ *   - SAGMS_SERVE_PLAIN: the baseline -- one request at a time on one stream, full grid.
+ * Results are those of sagms_decode for the same code, parameters and inputs.
+ * Host buffers must stay valid until the request finishes (page-locked memory copies
+ * fastest).  Errors: ERR_ARG, ERR_SIZE (request larger than the budget), ERR_BUSY (server
+ * stopping, or cancel of a running request), ERR_TIMEOUT (poll), ERR_CANCELLED.
+ */
+enum { SAGMS_SERVE_CONTINUOUS = 0, SAGMS_SERVE_PLAIN = 1 };
+typedef struct sagms_server sagms_server;
+int sagms_server_create(size_t mem_budget, int32_t max_inflight, int32_t mode, int32_t shots_per_cta,
+                        sagms_server** out);
+int sagms_server_add_code(sagms_server* server, const sagms_code* code, const sagms_params* params,
+                          int32_t* code_id);
+int sagms_server_submit(sagms_server* server, int32_t code_id, int64_t shots, const uint32_t* h_syn,
+                        const float* h_L0, uint32_t* h_err, uint8_t* h_conv, int32_t* h_iters,
+                        uint64_t* ticket);
+/* Wait up to timeout_us (0: just check) for a request; SAGMS_OK once its results are in the
+ * host buffers, ERR_TIMEOUT while it is still queued or running. */
+int sagms_server_poll(sagms_server* server, uint64_t ticket, int64_t timeout_us);
+int sagms_server_cancel(sagms_server* server, uint64_t ticket);   /* queued requests only */
+/* Steady-clock nanoseconds at submit and at completion (0 while unfinished). */
+int sagms_server_times(sagms_server* server, uint64_t ticket, int64_t* submit_ns, int64_t* done_ns);
+int sagms_server_release(sagms_server* server, uint64_t ticket);  /* forget a finished request */
+/* Cancels queued requests, waits for running ones, frees the arena. */
+int sagms_server_destroy(sagms_server* server);
+/* Load generator for measurements: submits request i (arguments as sagms_server_submit,
+ * one array entry per request) once arrival_ns[i] nanoseconds have passed since the call
+ * began, spinning on the host clock; returns after the last submission with the tickets. */
+int sagms_server_replay(sagms_server* server, int32_t n, const int32_t* code_ids, const int64_t* shots,
+                        const int64_t* arrival_ns, const uint32_t* const* h_syn, const float* const* h_L0,
+                        uint32_t* const* h_err, uint8_t* const* h_conv, int32_t* const* h_iters,
+                        uint64_t* tickets);
 
 /* Eq. 9: alpha*(L0, d_c) = 2 atanh(tanh(L0/2)^(d_c - 1)) / L0, the SMS scale matching one
  * BP CN update under uniform inputs (Remark 1).  Returns NaN for L0 <= 0 or d_c < 2. */

@@ -201,3 +201,99 @@ def autotune(code: DeviceCode, syn, L0, params: Params | None = None, stream=Non
     iters = torch.empty((shots,), dtype=torch.int32, device=syn.device)
     return _native.sagms_autotune(code.handle, params.to_c(), shots, syn.data_ptr(), L0.data_ptr(), err.data_ptr(),
                                   conv.data_ptr(), iters.data_ptr(), _stream_ptr(stream))
+
+
+class Server:
+    """Continuous-batching decode server (sagms_server_*).  Requests carry host buffers
+    (numpy arrays or CPU torch tensors; page-locked memory copies fastest) that the server
+    keeps referenced until the request is released."""
+
+    MODES = {"continuous": 0, "plain": 1}
+
+    def __init__(self, mem_budget=1 << 30, max_inflight=16, mode="continuous", shots_per_cta=16):
+        import ctypes
+        from . import _native
+        self._native = _native
+        h = ctypes.c_void_p()
+        _native._check(_native.lib().sagms_server_create(int(mem_budget), int(max_inflight), self.MODES[mode],
+                                                         int(shots_per_cta), ctypes.byref(h)))
+        self.handle = h.value
+        self._bufs = {}
+
+    def add_code(self, code: DeviceCode, params: Params | None = None) -> int:
+        import ctypes
+        cid = ctypes.c_int32()
+        p = (params or Params()).to_c()
+        self._native._check(self._native.lib().sagms_server_add_code(self.handle, code.handle, ctypes.byref(p),
+                                                                     ctypes.byref(cid)))
+        return cid.value
+
+    @staticmethod
+    def _ptr(a):
+        return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+
+    def submit(self, code_id, syn, L0, err, conv, iters) -> int:
+        import ctypes
+        t = ctypes.c_uint64()
+        shots = syn.shape[0]
+        self._native._check(self._native.lib().sagms_server_submit(
+            self.handle, int(code_id), shots, self._ptr(syn), self._ptr(L0), self._ptr(err), self._ptr(conv),
+            self._ptr(iters), ctypes.byref(t)))
+        self._bufs[t.value] = (syn, L0, err, conv, iters)
+        return t.value
+
+    def poll(self, ticket, timeout_us=0) -> int:
+        return self._native.lib().sagms_server_poll(self.handle, ticket, int(timeout_us))
+
+    def wait(self, ticket, timeout_s=60.0):
+        rc = self.poll(ticket, int(timeout_s * 1e6))
+        self._native._check(rc)
+
+    def cancel(self, ticket) -> int:
+        return self._native.lib().sagms_server_cancel(self.handle, ticket)
+
+    def times(self, ticket):
+        import ctypes
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        self._native._check(self._native.lib().sagms_server_times(self.handle, ticket, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def release(self, ticket):
+        rc = self._native.lib().sagms_server_release(self.handle, ticket)
+        if rc == 0:
+            self._bufs.pop(ticket, None)
+        return rc
+
+    def replay(self, code_ids, requests, arrival_ns):
+        """Submit requests[i] = (syn, L0, err, conv, iters) at arrival_ns[i] after the call
+        starts (native pacing); returns the tickets."""
+        import ctypes
+        import numpy as np
+        n = len(requests)
+        VP = ctypes.c_void_p * n
+        cols = list(zip(*requests)) if n else [[]] * 5
+        ptrs = [VP(*[self._ptr(a) for a in col]) for col in cols]
+        ids = np.ascontiguousarray(code_ids, dtype=np.int32)
+        shots = np.ascontiguousarray([r[0].shape[0] for r in requests], dtype=np.int64)
+        arr = np.ascontiguousarray(arrival_ns, dtype=np.int64)
+        tickets = np.zeros(n, dtype=np.uint64)
+        P = ctypes.POINTER
+        self._native._check(self._native.lib().sagms_server_replay(
+            self.handle, n, ids.ctypes.data_as(P(ctypes.c_int32)), shots.ctypes.data_as(P(ctypes.c_int64)),
+            arr.ctypes.data_as(P(ctypes.c_int64)), ptrs[0], ptrs[1], ptrs[2], ptrs[3], ptrs[4],
+            tickets.ctypes.data_as(P(ctypes.c_uint64))))
+        for t, r in zip(tickets, requests):
+            self._bufs[int(t)] = r
+        return [int(t) for t in tickets]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._native.lib().sagms_server_destroy(self.handle)
+            self.handle = None
+            self._bufs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -19,7 +19,8 @@ SAGMS_FLAG_NO_EARLY_STOP = 2
 SAGMS_FLAG_GENERIC_KERNEL = 4
 SAGMS_OK = 0
 ERRORS = {-1: "ERR_ARG", -2: "ERR_CSR", -3: "ERR_DEGREE", -4: "ERR_PARAM", -5: "ERR_OOM", -6: "ERR_CUDA",
-          -7: "ERR_TIMEOUT", -8: "ERR_BUSY", -9: "ERR_SIZE"}
+          -7: "ERR_TIMEOUT", -8: "ERR_BUSY", -9: "ERR_SIZE", -10: "ERR_CANCELLED"}
+SAGMS_SERVE_CONTINUOUS, SAGMS_SERVE_PLAIN = 0, 1
 MODES = {"ms": SAGMS_MS, "sms": SAGMS_SMS, "sagms": SAGMS_SAGMS, "bp": SAGMS_BP}
 
 
@@ -64,6 +65,16 @@ def _load_library():
         "sagms_autotune": (ctypes.c_int, [vp, P(sagms_params), i64, vp, vp, vp, vp, vp, P(i32),
                                           P(ctypes.c_float), vp]),
         "sagms_set_plan": (ctypes.c_int, [vp, i32]),
+        "sagms_server_create": (ctypes.c_int, [ctypes.c_size_t, i32, i32, i32, P(vp)]),
+        "sagms_server_add_code": (ctypes.c_int, [vp, vp, P(sagms_params), P(i32)]),
+        "sagms_server_submit": (ctypes.c_int, [vp, i32, i64, vp, vp, vp, vp, vp, P(ctypes.c_uint64)]),
+        "sagms_server_poll": (ctypes.c_int, [vp, ctypes.c_uint64, i64]),
+        "sagms_server_cancel": (ctypes.c_int, [vp, ctypes.c_uint64]),
+        "sagms_server_times": (ctypes.c_int, [vp, ctypes.c_uint64, P(i64), P(i64)]),
+        "sagms_server_release": (ctypes.c_int, [vp, ctypes.c_uint64]),
+        "sagms_server_destroy": (ctypes.c_int, [vp]),
+        "sagms_server_replay": (ctypes.c_int, [vp, i32, P(i32), P(i64), P(i64), P(vp), P(vp), P(vp), P(vp),
+                                               P(vp), P(ctypes.c_uint64)]),
         "sagms_alpha_star": (ctypes.c_double, [ctypes.c_double, i32]),
         "sagms_last_error_string": (ctypes.c_char_p, []),
         "sagms_version": (ctypes.c_char_p, []),

@@ -1,0 +1,33 @@
+// Declarations shared by the library's translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/sagms.h"
+
+namespace sagms_internal {
+
+// How a decode is launched.  kernel: 0 automatic, 1 one shot per CTA, 2 two-slot;
+// ctas_per_sm: 0 = occupancy limit; chunk_lg: log2 shots per claimed chunk, 0 = automatic;
+// max_grid: cap on the number of CTAs, 0 = none (a small grid keeps a launch from holding
+// every SM, so concurrent launches share the GPU CTA by CTA).
+struct Plan {
+    int kernel = 0;
+    int ctas_per_sm = 0;
+    int chunk_lg = 0;
+    long long max_grid = 0;
+    int* work = nullptr;   // caller-owned chunk counters (>= one per launch chunk); null: allocate
+};
+
+// sagms_decode with an explicit launch plan (nullptr: the code's own plan).
+int launch(const sagms_code* code, const sagms_params* params, int64_t shots, const uint32_t* d_syn,
+           const float* d_L0, uint32_t* d_err, uint8_t* d_conv, int32_t* d_iters, cudaStream_t stream,
+           const Plan* plan);
+
+// Record `msg` as the calling thread's last error and return `code`.
+int set_error(int code, const char* msg);
+int cuda_error(cudaError_t e, const char* what);
+
+}  // namespace sagms_internal

@@ -20,6 +20,7 @@
 #include "../../include/sagms.h"
 #include "decode_kernel.cuh"
 #include "decode_slots.cuh"
+#include "internal.h"
 
 using namespace sagms;
 
@@ -96,8 +97,14 @@ void store_cached_plan(uint64_t key, uint32_t pl) {
     std::fclose(f);
 }
 
-struct Plan { int kernel, ctas_per_sm, chunk_lg; };
-Plan unpack_plan(uint32_t v) { return Plan{(int)(v & 3u), (int)((v >> 8) & 0xffu), (int)((v >> 16) & 0xfu)}; }
+using sagms_internal::Plan;
+Plan unpack_plan(uint32_t v) {
+    Plan p;
+    p.kernel = (int)(v & 3u);
+    p.ctas_per_sm = (int)((v >> 8) & 0xffu);
+    p.chunk_lg = (int)((v >> 16) & 0xfu);
+    return p;
+}
 uint32_t pack_plan(const Plan& p) {
     return (uint32_t)(p.kernel & 3) | ((uint32_t)(p.ctas_per_sm & 0xff) << 8) | ((uint32_t)(p.chunk_lg & 0xf) << 16);
 }
@@ -421,7 +428,8 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     if (ce != cudaSuccess) return cuda_fail(ce, "occupancy query");
     if (per_sm < 1) return fail(SAGMS_ERR_SIZE, "kernel does not fit on an SM");
     if (plan.ctas_per_sm > 0) per_sm = std::min(per_sm, plan.ctas_per_sm);
-    const long long grid = std::min<long long>(units, (long long)per_sm * sms);
+    long long grid = std::min<long long>(units, (long long)per_sm * sms);
+    if (plan.max_grid > 0) grid = std::min(grid, plan.max_grid);
     if (use_slots) {
         // 32-bit shot indexing inside the kernel: split batches into launches of at most
         // max_slot_chunk shots.  Each
@@ -430,12 +438,15 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
         SlotLayout lay{code->d_colB, code->d_vneB};
         const long long kMaxChunk = max_slot_chunk(code->m, code->n);
         const long long nchunks = (shots + kMaxChunk - 1) / kMaxChunk;
-        int* d_work = nullptr;
-        ce = cudaMallocAsync(reinterpret_cast<void**>(&d_work), (size_t)nchunks * sizeof(int), stream);
-        if (ce != cudaSuccess) return cuda_fail(ce, "work counter allocation");
+        int* d_work = plan.work;
+        const bool own_work = d_work == nullptr;
+        if (own_work) {
+            ce = cudaMallocAsync(reinterpret_cast<void**>(&d_work), (size_t)nchunks * sizeof(int), stream);
+            if (ce != cudaSuccess) return cuda_fail(ce, "work counter allocation");
+        }
         ce = cudaMemsetAsync(d_work, 0, (size_t)nchunks * sizeof(int), stream);
         if (ce != cudaSuccess) {
-            cudaFreeAsync(d_work, stream);
+            if (own_work) cudaFreeAsync(d_work, stream);
             return cuda_fail(ce, "work counter reset");
         }
         for (long long s0 = 0, ci = 0; s0 < shots; s0 += kMaxChunk, ++ci) {
@@ -455,7 +466,7 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
             slot_kernel_for(code->slot_variant)<<<(unsigned)g, threads, smem, stream>>>(c, lay);
         }
         ce = cudaGetLastError();
-        cudaFreeAsync(d_work, stream);
+        if (own_work) cudaFreeAsync(d_work, stream);
         if (ce != cudaSuccess) return cuda_fail(ce, "decode launch");
         return SAGMS_OK;
     } else {
@@ -467,6 +478,19 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
 }
 
 }  // namespace
+
+namespace sagms_internal {
+
+int launch(const sagms_code* code, const sagms_params* params, int64_t shots, const uint32_t* d_syn,
+           const float* d_L0, uint32_t* d_err, uint8_t* d_conv, int32_t* d_iters, cudaStream_t stream,
+           const Plan* plan) {
+    return launch_decode(code, params, shots, d_syn, d_L0, d_err, d_conv, d_iters, nullptr, stream, plan);
+}
+
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+int cuda_error(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+
+}  // namespace sagms_internal
 
 extern "C" {
 
@@ -677,9 +701,15 @@ int sagms_autotune(const sagms_code* code, const sagms_params* params, int64_t s
         if (kernel == 2 && !slots_ok) continue;
         for (int cps : {0, 2, 1}) {
             if (kernel == 2) {
-                for (int clg : {0, 1, 2, 4}) cands.push_back(Plan{kernel, cps, clg});
+                for (int clg : {0, 1, 2, 4}) {
+                    Plan pl;
+                    pl.kernel = kernel; pl.ctas_per_sm = cps; pl.chunk_lg = clg;
+                    cands.push_back(pl);
+                }
             } else {
-                cands.push_back(Plan{kernel, cps, 0});
+                Plan pl;
+                pl.kernel = kernel; pl.ctas_per_sm = cps;
+                cands.push_back(pl);
             }
         }
     }
@@ -688,7 +718,7 @@ int sagms_autotune(const sagms_code* code, const sagms_params* params, int64_t s
     if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaEventCreate");
     float best_ms = 0.0f;
-    Plan best{0, 0, 0};
+    Plan best;
     bool have = false;
     for (const Plan& pl : cands) {
         rc = launch_decode(code, params, shots, d_syn, d_L0, d_err, d_conv, d_iters, nullptr, stream, &pl);  // warm-up
