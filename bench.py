@@ -280,7 +280,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--shots", type=int, default=10_000_000)
-    ap.add_argument("--ref-sample", type=int, default=4000)
+    ap.add_argument("--ref-sample", type=int, default=40000)
     ap.add_argument("--cpu-sample", type=int, default=16000)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--mode-steps", type=int, default=3)
