@@ -200,10 +200,11 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
         float2 v[DC];
         uint32_t x0 = (sbits & 1u) << 31, x1 = (sbits >> 1) << 31;
 #pragma unroll
-        for (int j = 0; j < DC; ++j) {
-            v[j] = *reinterpret_cast<const float2*>(smem + colB[j * MP + t]);
-            x0 ^= __float_as_uint(v[j].x);
-            x1 ^= __float_as_uint(v[j].y);
+        for (int j = 0; j < DC; ++j) v[j] = *reinterpret_cast<const float2*>(smem + colB[j * MP + t]);
+#pragma unroll
+        for (int j = 0; j < DC; j += 2) {
+            x0 ^= __float_as_uint(v[j].x) ^ __float_as_uint(v[j + 1].x);
+            x1 ^= __float_as_uint(v[j].y) ^ __float_as_uint(v[j + 1].y);
         }
         const uint32_t b0 = __ballot_sync(0xffffffffu, x0 >> 31);
         const uint32_t b1 = __ballot_sync(0xffffffffu, x1 >> 31);
@@ -228,7 +229,8 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
 
         // A6 per slot: the common case (both slots decoding, neither finished) is one test.
         bool zero[2] = {false, false};
-        uint32_t fresh = 0u;   // bit k: slot k runs the first round of a newly loaded shot
+        uint32_t fresh = 0u;    // bit k: slot k runs the first round of a newly loaded shot
+        uint32_t consumed = 0u; // bit 2k: slot k took its prefetched shot; bit 2k+1: from buffer 1
         const bool fin0 = state[0] == kActive && ((gcnt[0] == 0 && early) || itk[0] == a.max_iter);
         const bool fin1 = state[1] == kActive && ((gcnt[1] == 0 && early) || itk[1] == a.max_iter);
         if (!(fin0 || fin1 || state[0] != kActive || state[1] != kActive)) {
@@ -260,17 +262,13 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
                 const int b = (pbits >> k) & 1;
                 const int s = pfidx[2 * k + b];
                 if (s >= nshots) { state[k] = kDone; continue; }
-                const int nx = assign();
-                if (t == 0) {
-                    pfidx[2 * k + (b ^ 1)] = nx;
-                    shotsm[2 * k + b] = s;
-                }
+                if (t == 0) shotsm[2 * k + b] = s;
                 pbits ^= 1u << k;
+                consumed |= (1u | ((uint32_t)b << 1)) << (2 * k);   // warp 0 claims and prefetches later
                 const uint32_t* row = pfsyn + (k * 2 + b) * 32;
                 const float l0 = per_qubit ? 0.0f : pfl0[k * 2 + b];
                 const uint32_t bit = (t < m) ? ((row[t >> 5] >> (t & 31)) & 1u) : 0u;
                 const uint32_t word = (lane < mw) ? row[lane] : 0u;
-                prefetch(k, b ^ 1, nx);
                 if (!(per_qubit ? (pq_ok != 0) : isfinite(l0))) {
                     for (int w = t; w < nw; w += MP) a.err[s * nw + w] = 0u;
                     if (t == 0) { a.conv[s] = 0; a.iters[s] = -1; }
@@ -323,17 +321,25 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
         for (int j = 0; j < DC; ++j) v[j] = add2(v[j], C2[j * MP + t]);   // P - L_old (C2 is negated)
         if (fresh) {
             // A freshly loaded slot's round-1 inputs are its priors (+inf on padding slots).
+            if (per_qubit || haspad) {
 #pragma unroll
-            for (int j = 0; j < DC; ++j) {
-                float p0 = prior[0], p1 = prior[1];
-                if (per_qubit || haspad) {
+                for (int j = 0; j < DC; ++j) {
                     const uint16_t off = colB[j * MP + t];
-                    const float pq = per_qubit ? PQ[off >> 3] : ((off == pad) ? inf : 0.0f);
-                    p0 = per_qubit ? pq : ((off == pad) ? inf : p0);
-                    p1 = per_qubit ? pq : ((off == pad) ? inf : p1);
+                    const float pq = per_qubit ? PQ[off >> 3] : 0.0f;
+                    const float p0 = (off == pad) ? inf : (per_qubit ? pq : prior[0]);
+                    const float p1 = (off == pad) ? inf : (per_qubit ? pq : prior[1]);
+                    if (fresh & 1u) v[j].x = p0;
+                    if (fresh & 2u) v[j].y = p1;
                 }
-                if (fresh & 1u) v[j].x = p0;
-                if (fresh & 2u) v[j].y = p1;
+            } else if (fresh == 1u) {
+#pragma unroll
+                for (int j = 0; j < DC; ++j) v[j].x = prior[0];
+            } else if (fresh == 2u) {
+#pragma unroll
+                for (int j = 0; j < DC; ++j) v[j].y = prior[1];
+            } else {
+#pragma unroll
+                for (int j = 0; j < DC; ++j) v[j] = make_float2(prior[0], prior[1]);
             }
         }
         uint32_t par0 = (sbits & 1u) << 31, par1 = (sbits >> 1) << 31;
@@ -344,14 +350,19 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
         }
         par0 &= kSign;
         par1 &= kSign;
+        // Smallest and second smallest |v| per slot, two edges at a time:
+        // lo/hi of the pair, then m2 = min(m2, hi, max(m1, lo)), m1 = min(m1, lo).
         float m1a = inf, m2a = inf, m1b = inf, m2b = inf;
 #pragma unroll
-        for (int j = 0; j < DC; ++j) {
-            const float aa = fabsf(v[j].x), ab = fabsf(v[j].y);
-            m2a = fminf(m2a, fmaxf(m1a, aa));
-            m1a = fminf(m1a, aa);
-            m2b = fminf(m2b, fmaxf(m1b, ab));
-            m1b = fminf(m1b, ab);
+        for (int j = 0; j < DC; j += 2) {
+            const float a0 = fabsf(v[j].x), a1 = fabsf(v[j + 1].x);
+            const float b0 = fabsf(v[j].y), b1 = fabsf(v[j + 1].y);
+            const float loa = fminf(a0, a1), hia = fmaxf(a0, a1);
+            const float lob = fminf(b0, b1), hib = fmaxf(b0, b1);
+            m2a = fminf(fminf(m2a, hia), fmaxf(m1a, loa));
+            m1a = fminf(m1a, loa);
+            m2b = fminf(fminf(m2b, hib), fmaxf(m1b, lob));
+            m1b = fminf(m1b, lob);
         }
         const float o1a = zero[0] ? 0.0f : __uint_as_float(__float_as_uint(fminf(g0 * m1a, kMsFamClip)) | par0);
         const float o2a = zero[0] ? 0.0f : __uint_as_float(__float_as_uint(fminf(g0 * m2a, kMsFamClip)) | par0);
@@ -366,6 +377,19 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
                                          __uint_as_float(__float_as_uint(mb) ^ (~__float_as_uint(v[j].y) & kSign)));
         }
         __syncthreads();
+
+        // Claims and prefetches for the slots that took a shot this round (warp 0 only; the
+        // next refill of a slot reads them after the next barrier).
+        if (consumed && t < 32) {
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (!((consumed >> (2 * k)) & 1u)) continue;
+                const int b = (consumed >> (2 * k + 1)) & 1u;
+                const int nx = assign();
+                if (t == 0) pfidx[2 * k + (b ^ 1)] = nx;
+                prefetch(k, b ^ 1, nx);
+            }
+        }
 
         // A4 variable-node update for both slots (qubits past n compute on the zero slot and
         // are never read: no bounds test in the loop)
