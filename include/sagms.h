@@ -167,7 +167,7 @@ int sagms_decode_host(const sagms_code* code, const sagms_params* params, int64_
  * the device), processes confined to a device-memory budget fixed at start-up, and host
  * frameworks that own every allocation.  Arguments, layouts and results are those of
  * sagms_decode; results are identical.  The only scratch -- the shot counters the
- * two-slot kernel claims shots from -- is a fixed array of SAGMS_NOALLOC_COUNTERS ints in
+ * continuous-batching kernels claim shots from -- is a fixed array of SAGMS_NOALLOC_COUNTERS ints in
  * the library's device memory, one counter per launch of up to (2^31 - 1) / W shots
  * (W = max(ceil(m/32), ceil(n/32)) words per pattern; 33.5 million shots at n = 2046), so
  * at most SAGMS_NOALLOC_COUNTERS times that per call; larger batches get SAGMS_ERR_SIZE.
@@ -218,10 +218,15 @@ void sagms_graph_destroy(sagms_graph* graph);
 /*
  * Launch-plan autotuning (not part of the method: it picks how the decoder is launched).
  * Decodes the caller's sample batch (buffers as in sagms_decode; the outputs are
- * overwritten) under each candidate plan -- kernel family (two-slot continuous batching or
- * one shot per CTA), CTAs per SM, shots per claimed chunk -- times them with CUDA events on
- * `stream` (synchronising it), stores the fastest in the code handle for later decodes, and
- * returns it in *plan (packed; sagms_set_plan accepts it) with its rate in *shots_per_s.
+ * overwritten) under each candidate plan -- kernel family (two-group or two-slot continuous
+ * batching, or one shot per CTA), CTAs per SM, shots per claimed chunk -- times them with
+ * CUDA events on `stream` (synchronising it), stores the fastest in the code handle for
+ * later decodes, and returns it in *plan with its rate in *shots_per_s.
+ * A plan packs: bits 0-1 the kernel (0 automatic, 1 one shot per CTA, 2 two-slot,
+ * 3 two-group), bits 8-15 CTAs per SM (0: occupancy limit), bits 16-19 log2 of the shots
+ * per claimed chunk (0: automatic); other bits must be zero.  A kernel the code or the
+ * parameters cannot use falls back to the next one in the order two-group, two-slot, one
+ * shot per CTA.
  * Results of a decode do not depend on the plan.  With the environment variable
  * SAGMS_AUTOTUNE_CACHE naming a file, the plan is also appended there and sagms_load_code
  * of the same matrix starts from it.

@@ -20,6 +20,7 @@
 #include "../../include/sagms.h"
 #include "decode_kernel.cuh"
 #include "decode_slots.cuh"
+#include "decode_groups.cuh"
 #include "internal.h"
 
 using namespace sagms;
@@ -68,6 +69,12 @@ KernelFn kernel_for(int variant, bool bp) {
 }
 
 int round_up(int x, int k) { return (x + k - 1) / k * k; }
+
+// Two-group kernel (decode_groups.cuh): one compiled shape, for MS-family codes with more
+// than 512 and at most 1024 checks, at most 2048 qubits and degrees up to (10, 5).
+constexpr int kGroupDC = 10, kGroupDV = 5;
+using GroupFn = void (*)(const DecodeArgs, const GroupLayout);
+GroupFn group_kernel_fn() { return group_kernel<kGroupDC, kGroupDV>; }
 
 constexpr int kMaxDevices = 64;
 
@@ -160,8 +167,12 @@ struct sagms_code {
     int slot_variant;      // -1: no two-slot kernel for this shape
     uint16_t* d_colB;      // [DC][MP] byte offsets into P2
     uint32_t* d_vneB;      // [DV][NP] byte offsets into C2
+    bool groups;           // the two-group kernel covers this code
+    uint16_t* d_colG;      // [2][kGroupDC][1024] byte offsets of P_g entries
+    uint32_t* d_vneG;      // [2][kGroupDV][2048] byte offsets of C_g entries
     // Launch plan chosen by sagms_autotune (0 = defaults), packed so decodes on other
-    // threads read it atomically: bits 0-1 kernel (0 auto, 1 one-shot-per-CTA, 2 two-slot),
+    // threads read it atomically: bits 0-1 kernel (0 auto, 1 one-shot-per-CTA, 2 two-slot,
+    // 3 two-group),
     // bits 8-15 CTAs per SM (0 = occupancy limit), bits 16-19 log2 shots per claimed chunk
     // (0 = automatic).
     mutable std::atomic<uint32_t> plan;
@@ -295,6 +306,31 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
         }
     }
 
+    // Two-group layout: the same graph once per group, as byte offsets from the start of
+    // shared memory into that group's posterior and message arrays.
+    const bool groups = dc_max <= kGroupDC && dv_max <= kGroupDV && m > 512 && m <= kGrpChecks && n <= kGrpQubits;
+    std::vector<uint16_t> colG;
+    std::vector<uint32_t> vneG;
+    if (groups) {
+        colG.resize((size_t)2 * kGroupDC * kGrpChecks);
+        vneG.resize((size_t)2 * kGroupDV * kGrpQubits);
+        for (int g = 0; g < 2; ++g) {
+            uint16_t* cg = colG.data() + (size_t)g * kGroupDC * kGrpChecks;
+            uint32_t* vg = vneG.data() + (size_t)g * kGroupDV * kGrpQubits;
+            const size_t pb = grp_P_off(g), cb = grp_C_off(kGroupDC, g);
+            std::fill(cg, cg + kGroupDC * kGrpChecks, (uint16_t)(pb + (size_t)kGrpQubits * 4));
+            for (int i = 0; i < m; ++i)
+                for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+                    cg[(size_t)(e - row_ptr[i]) * kGrpChecks + i] = (uint16_t)(pb + (size_t)col_idx[e] * 4);
+            std::fill(vg, vg + kGroupDV * kGrpQubits, (uint32_t)(cb + (size_t)kGroupDC * kGrpChecks * 4));
+            for (int c = 0; c < n; ++c) {
+                const auto& ve = vedges[c];
+                for (size_t q = 0; q < ve.size(); ++q)
+                    vg[q * kGrpQubits + c] = (uint32_t)(cb + ((size_t)ve[q].first * kGrpChecks + ve[q].second) * 4);
+            }
+        }
+    }
+
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
@@ -302,6 +338,9 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
     code->slot_variant = sv;
     code->d_colB = nullptr;
     code->d_vneB = nullptr;
+    code->groups = groups;
+    code->d_colG = nullptr;
+    code->d_vneG = nullptr;
     code->plan.store(0u);
     {
         uint64_t h = 1469598103934665603ull;   // FNV-1a over the CSR
@@ -327,11 +366,19 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
         if (ce == cudaSuccess) ce = cudaMemcpy(code->d_colB, colB.data(), colB.size() * 2, cudaMemcpyHostToDevice);
         if (ce == cudaSuccess) ce = cudaMemcpy(code->d_vneB, vneB.data(), vneB.size() * 4, cudaMemcpyHostToDevice);
     }
+    if (ce == cudaSuccess && groups) {
+        ce = cudaMalloc(&code->d_colG, colG.size() * sizeof(uint16_t));
+        if (ce == cudaSuccess) ce = cudaMalloc(&code->d_vneG, vneG.size() * sizeof(uint32_t));
+        if (ce == cudaSuccess) ce = cudaMemcpy(code->d_colG, colG.data(), colG.size() * 2, cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess) ce = cudaMemcpy(code->d_vneG, vneG.data(), vneG.size() * 4, cudaMemcpyHostToDevice);
+    }
     if (ce != cudaSuccess) {
         cudaFree(code->d_colT);
         cudaFree(code->d_vneT);
         cudaFree(code->d_colB);
         cudaFree(code->d_vneB);
+        cudaFree(code->d_colG);
+        cudaFree(code->d_vneG);
         delete code;
         return cuda_fail(ce, "sagms_load_code upload");
     }
@@ -348,6 +395,8 @@ void sagms_free_code(sagms_code* code) {
     cudaFree(code->d_vneT);
     cudaFree(code->d_colB);
     cudaFree(code->d_vneB);
+    cudaFree(code->d_colG);
+    cudaFree(code->d_vneG);
     if (prev >= 0 && prev != code->device) cudaSetDevice(prev);
     delete code;
 }
@@ -394,8 +443,11 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     a.chunk_lg = 1;
 
     const Plan plan = plan_override ? *plan_override : unpack_plan(code->plan.load());
-    const bool use_slots = !bp && code->slot_variant >= 0 && !(p->flags & SAGMS_FLAG_GENERIC_KERNEL) &&
-                           plan.kernel != 1;
+    // Kernel: the plan's choice where the code and parameters allow it, else the fastest
+    // that does (two-group, two-slot, one-shot-per-CTA).
+    const bool msfam_fast = !bp && !(p->flags & SAGMS_FLAG_GENERIC_KERNEL);
+    const bool use_groups = msfam_fast && code->groups && !per_qubit && (plan.kernel == 0 || plan.kernel == 3);
+    const bool use_slots = !use_groups && msfam_fast && code->slot_variant >= 0 && plan.kernel != 1;
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
@@ -407,12 +459,17 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     size_t smem;
     int threads;
     long long units;
-    if (use_slots) {
+    if (use_groups) {
+        fn = reinterpret_cast<const void*>(group_kernel_fn());
+        smem = grp_smem_bytes(kGroupDC, kGroupDV);
+        threads = 2 * kGrpThreads;
+        units = (shots + 1) / 2;   // two shots in flight per CTA
+    } else if (use_slots) {
         const SlotVariant& S = kSlotVariants[code->slot_variant];
         fn = reinterpret_cast<const void*>(slot_kernel_for(code->slot_variant));
         smem = slot_smem_bytes(S.dc, S.dv, S.mp, S.np, per_qubit);
         threads = S.mp;
-        units = (shots + 1) / 2;   // two shots in flight per CTA
+        units = (shots + 1) / 2;
     } else {
         fn = reinterpret_cast<const void*>(kernel_for(code->variant, bp));
         smem = smem_bytes(code->DC, code->DV, code->Mp, code->Np, per_qubit);
@@ -430,49 +487,52 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     if (plan.ctas_per_sm > 0) per_sm = std::min(per_sm, plan.ctas_per_sm);
     long long grid = std::min<long long>(units, (long long)per_sm * sms);
     if (plan.max_grid > 0) grid = std::min(grid, plan.max_grid);
-    if (use_slots) {
-        // 32-bit shot indexing inside the kernel: split batches into launches of at most
-        // max_slot_chunk shots.  Each
-        // launch gets a zeroed shot counter (scratch from the stream-ordered pool) that its
-        // CTAs claim shots from.
-        SlotLayout lay{code->d_colB, code->d_vneB};
-        const long long kMaxChunk = max_slot_chunk(code->m, code->n);
-        const long long nchunks = (shots + kMaxChunk - 1) / kMaxChunk;
-        int* d_work = plan.work;
-        const bool own_work = d_work == nullptr;
-        if (own_work) {
-            ce = cudaMallocAsync(reinterpret_cast<void**>(&d_work), (size_t)nchunks * sizeof(int), stream);
-            if (ce != cudaSuccess) return cuda_fail(ce, "work counter allocation");
-        }
-        ce = cudaMemsetAsync(d_work, 0, (size_t)nchunks * sizeof(int), stream);
-        if (ce != cudaSuccess) {
-            if (own_work) cudaFreeAsync(d_work, stream);
-            return cuda_fail(ce, "work counter reset");
-        }
-        for (long long s0 = 0, ci = 0; s0 < shots; s0 += kMaxChunk, ++ci) {
-            DecodeArgs c = a;
-            const long long cnt = std::min(kMaxChunk, shots - s0);
-            const int mw = (code->m + 31) / 32, nw = (code->n + 31) / 32;
-            c.shots = cnt;
-            c.syn = a.syn + s0 * mw;
-            c.L0 = per_qubit ? a.L0 : a.L0 + s0;
-            c.err = a.err + s0 * nw;
-            c.conv = a.conv + s0;
-            c.iters = a.iters + s0;
-            c.trace = a.trace ? a.trace + s0 * (long long)(a.max_iter + 1) * code->n : nullptr;
-            c.work = d_work + ci;
-            const long long g = std::min(grid, (cnt + 1) / 2);
-            c.chunk_lg = plan.chunk_lg > 0 ? plan.chunk_lg : chunk_lg_for(cnt, g);
-            slot_kernel_for(code->slot_variant)<<<(unsigned)g, threads, smem, stream>>>(c, lay);
-        }
+    if (!use_groups && !use_slots) {
+        kernel_for(code->variant, bp)<<<(unsigned)grid, threads, smem, stream>>>(a);
         ce = cudaGetLastError();
-        if (own_work) cudaFreeAsync(d_work, stream);
         if (ce != cudaSuccess) return cuda_fail(ce, "decode launch");
         return SAGMS_OK;
-    } else {
-        kernel_for(code->variant, bp)<<<(unsigned)grid, threads, smem, stream>>>(a);
+    }
+    // Continuous-batching kernels: 32-bit shot indexing inside the kernel, so batches are
+    // split into launches of at most max_slot_chunk shots.  Each launch gets a zeroed shot
+    // counter that its CTAs claim chunks of shots from: the plan's scratch when it has one,
+    // else scratch from the stream-ordered pool.
+    const long long kMaxChunk = max_slot_chunk(code->m, code->n);
+    const long long nchunks = (shots + kMaxChunk - 1) / kMaxChunk;
+    int* d_work = plan.work;
+    const bool own_work = d_work == nullptr;
+    if (own_work) {
+        ce = cudaMallocAsync(reinterpret_cast<void**>(&d_work), (size_t)nchunks * sizeof(int), stream);
+        if (ce != cudaSuccess) return cuda_fail(ce, "work counter allocation");
+    }
+    ce = cudaMemsetAsync(d_work, 0, (size_t)nchunks * sizeof(int), stream);
+    if (ce != cudaSuccess) {
+        if (own_work) cudaFreeAsync(d_work, stream);
+        return cuda_fail(ce, "work counter reset");
+    }
+    const SlotLayout slay{code->d_colB, code->d_vneB};
+    const GroupLayout glay{code->d_colG, code->d_vneG};
+    for (long long s0 = 0, ci = 0; s0 < shots; s0 += kMaxChunk, ++ci) {
+        DecodeArgs c = a;
+        const long long cnt = std::min(kMaxChunk, shots - s0);
+        const int mw = (code->m + 31) / 32, nw = (code->n + 31) / 32;
+        c.shots = cnt;
+        c.syn = a.syn + s0 * mw;
+        c.L0 = per_qubit ? a.L0 : a.L0 + s0;
+        c.err = a.err + s0 * nw;
+        c.conv = a.conv + s0;
+        c.iters = a.iters + s0;
+        c.trace = a.trace ? a.trace + s0 * (long long)(a.max_iter + 1) * code->n : nullptr;
+        c.work = d_work + ci;
+        const long long g = std::min(grid, (cnt + 1) / 2);
+        c.chunk_lg = plan.chunk_lg > 0 ? plan.chunk_lg : chunk_lg_for(cnt, g);
+        if (use_groups)
+            group_kernel_fn()<<<(unsigned)g, threads, smem, stream>>>(c, glay);
+        else
+            slot_kernel_for(code->slot_variant)<<<(unsigned)g, threads, smem, stream>>>(c, slay);
     }
     ce = cudaGetLastError();
+    if (own_work) cudaFreeAsync(d_work, stream);
     if (ce != cudaSuccess) return cuda_fail(ce, "decode launch");
     return SAGMS_OK;
 }
@@ -570,7 +630,8 @@ int sagms_decode_host(const sagms_code* code, const sagms_params* params, int64_
 // threads (cudaMalloc and pool growth of cudaMallocAsync can synchronise or stall the
 // device), processes that run under a fixed device-memory budget reserved at start-up, and
 // host frameworks that own every allocation themselves.  sagms_decode_noalloc takes its
-// only scratch -- the per-launch chunk counters the two-slot kernel claims shots from -- from
+// only scratch -- the per-launch chunk counters the continuous-batching kernels claim shots
+// from -- from
 // this file-scope array instead of allocating it.  Every GPU that loads the library holds
 // the array until the process exits.  All calls share it and it keeps the last call's
 // contents; each call zeroes the counters it uses on its stream before launching, so calls
@@ -614,70 +675,16 @@ int sagms_decode_noalloc(const sagms_code* code, const sagms_params* p, int64_t 
         return fail(SAGMS_ERR_SIZE, "sagms_decode_noalloc: %lld shots exceed the fixed scratch (%d counters of %lld shots)",
                     (long long)shots, kNoAllocCounters, kMaxChunk);
     cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
-    const bool bp = p->mode == SAGMS_BP;
-    const bool use_slots = !bp && code->slot_variant >= 0 && !(p->flags & SAGMS_FLAG_GENERIC_KERNEL);
-    if (!use_slots)   // the one-shot-per-CTA kernel uses no scratch and allocates nothing
-        return launch_decode(code, p, shots, d_syn, d_L0, d_err, d_conv, d_iters, nullptr, stream);
-
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
     if (dev != code->device) return fail(SAGMS_ERR_ARG, "code was loaded on device %d, current is %d", code->device, dev);
-    int* scratch = nullptr;
-    rc = noalloc_scratch(dev, &scratch);
+    // The code's launch plan with the fixed scratch as its shot counters: the launcher then
+    // only zeroes them (the one-shot-per-CTA kernel uses none).
+    Plan pl = unpack_plan(code->plan.load());
+    rc = noalloc_scratch(dev, &pl.work);
     if (rc != SAGMS_OK) return rc;
-
-    const bool per_qubit = (p->flags & SAGMS_FLAG_L0_PER_QUBIT) != 0;
-    const SlotVariant& S = kSlotVariants[code->slot_variant];
-    SlotFn fn = slot_kernel_for(code->slot_variant);
-    const size_t smem = slot_smem_bytes(S.dc, S.dv, S.mp, S.np, per_qubit);
-    int smem_optin = 0, sms = 0;
-    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (smem > (size_t)smem_optin)
-        return fail(SAGMS_ERR_SIZE, "code needs %zu B of shared memory per CTA (limit %d)", smem, smem_optin);
-    ce = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (ce != cudaSuccess) return cuda_fail(ce, "cudaFuncSetAttribute");
-    int per_sm = 0;
-    ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void*>(fn), S.mp, smem);
-    if (ce != cudaSuccess) return cuda_fail(ce, "occupancy query");
-    if (per_sm < 1) return fail(SAGMS_ERR_SIZE, "kernel does not fit on an SM");
-
-    const long long nchunks = (shots + kMaxChunk - 1) / kMaxChunk;
-    ce = cudaMemsetAsync(scratch, 0, (size_t)nchunks * sizeof(int), stream);   // counters start at zero
-    if (ce != cudaSuccess) return cuda_fail(ce, "no-alloc scratch reset");
-    DecodeArgs a;
-    a.colT = code->d_colT;
-    a.vneT = code->d_vneT;
-    a.m = code->m; a.n = code->n; a.Mp = code->Mp; a.Np = code->Np;
-    a.mode = p->mode;
-    a.alpha = p->alpha;
-    a.amin = p->alpha_min;
-    a.amax = p->alpha_max;
-    a.eta = (p->eta_unsat == 0.0f) ? 1.10f : p->eta_unsat;
-    a.inv_m = 1.0f / (float)code->m;
-    a.max_iter = p->max_iter;
-    a.flags = p->flags;
-    a.trace = nullptr;
-    const SlotLayout lay{code->d_colB, code->d_vneB};
-    const int mw = (code->m + 31) / 32, nw = (code->n + 31) / 32;
-    const long long grid = (long long)per_sm * sms;
-    for (long long s0 = 0, ci = 0; s0 < shots; s0 += kMaxChunk, ++ci) {
-        const long long cnt = std::min(kMaxChunk, shots - s0);
-        a.shots = cnt;
-        a.syn = d_syn + s0 * mw;
-        a.L0 = per_qubit ? d_L0 : d_L0 + s0;
-        a.err = d_err + s0 * nw;
-        a.conv = d_conv + s0;
-        a.iters = d_iters + s0;
-        a.work = scratch + ci;
-        const long long g = std::min(grid, (cnt + 1) / 2);
-        a.chunk_lg = chunk_lg_for(cnt, g);
-        fn<<<(unsigned)g, S.mp, smem, stream>>>(a, lay);
-    }
-    ce = cudaGetLastError();
-    if (ce != cudaSuccess) return cuda_fail(ce, "decode launch");
-    return SAGMS_OK;
+    return launch_decode(code, p, shots, d_syn, d_L0, d_err, d_conv, d_iters, nullptr, stream, &pl);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -697,10 +704,13 @@ int sagms_autotune(const sagms_code* code, const sagms_params* params, int64_t s
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     std::vector<Plan> cands;
     const bool slots_ok = params->mode != SAGMS_BP && code->slot_variant >= 0;
-    for (int kernel : {2, 1}) {
+    const bool groups_ok = params->mode != SAGMS_BP && code->groups && !(params->flags & SAGMS_FLAG_L0_PER_QUBIT);
+    for (int kernel : {3, 2, 1}) {
         if (kernel == 2 && !slots_ok) continue;
+        if (kernel == 3 && !groups_ok) continue;
         for (int cps : {0, 2, 1}) {
-            if (kernel == 2) {
+            if (kernel == 3 && cps != 0) continue;   // one 1024-thread CTA per SM
+            if (kernel >= 2) {
                 for (int clg : {0, 1, 2, 4}) {
                     Plan pl;
                     pl.kernel = kernel; pl.ctas_per_sm = cps; pl.chunk_lg = clg;
@@ -747,8 +757,7 @@ int sagms_autotune(const sagms_code* code, const sagms_params* params, int64_t s
 
 int sagms_set_plan(sagms_code* code, int32_t plan) {
     if (!code) return fail(SAGMS_ERR_ARG, "code is NULL");
-    const Plan pl = unpack_plan((uint32_t)plan);
-    if (pl.kernel == 3) return fail(SAGMS_ERR_ARG, "unknown kernel field in plan 0x%x", (unsigned)plan);
+    if ((uint32_t)plan & ~0xfff03u) return fail(SAGMS_ERR_ARG, "unknown bits in plan 0x%x", (unsigned)plan);
     code->plan.store((uint32_t)plan);
     return SAGMS_OK;
 }

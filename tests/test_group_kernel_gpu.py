@@ -1,0 +1,129 @@
+"""The two-group kernel (two 512-thread groups per CTA, one shot each) against the
+one-shot-per-CTA kernel and the two-slot kernel, on the codes it covers (more than 512 and at
+most 1024 checks, at most 2048 qubits).
+
+All three run each shot's arithmetic in the same order, so outputs and posterior traces must
+agree bit for bit; parity of the one-shot-per-CTA kernel against the FP64 oracle is covered
+in test_parity_gpu.py, and one oracle comparison here pins the group kernel directly."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2605_10433_gb300 as S
+from paper_2605_10433_gb300 import _native
+from paper_2605_10433_gb300 import inputs as I
+from tests import gpu_helpers as G
+
+pytestmark = pytest.mark.gpu
+
+KERNEL_GENERIC, KERNEL_SLOTS, KERNEL_GROUPS = 1, 2, 3
+PARAMS = {
+    "ms": S.Params(mode="ms", max_iter=60),
+    "sms": S.Params(mode="sms", alpha=0.75, max_iter=60),
+    "sagms": S.Params(mode="sagms", alpha_min=0.30, alpha_max=0.50, eta_unsat=1.10, max_iter=60),
+}
+
+
+def _with(p, **kw):
+    return S.Params(**{**p.__dict__, **kw})
+
+
+@pytest.fixture(scope="module")
+def group_codes():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    out = {}
+    # GB(1023, 5): the benchmark code (no padded edges); GB(1024, 4): every check padded
+    # from 8 to 10 edges and every qubit from 4 to 5; a random code with ragged degrees.
+    for key in [(1023, 5), (1024, 4)]:
+        c = I.gb_code(*key)
+        out[key] = c
+    rng = np.random.default_rng(2024)
+    m, n = 700, 1500
+    H = np.zeros((m, n), dtype=np.uint8)
+    for i in range(m):
+        H[i, rng.choice(n, size=int(rng.integers(1, 11)), replace=False)] = 1
+    while H.sum(axis=0).max() > 5:
+        j = int(np.argmax(H.sum(axis=0)))
+        H[np.nonzero(H[:, j])[0][0], j] = 0
+    out["ragged"] = I.code_from_dense(H)
+    return out
+
+
+def _decode_with_kernel(code, kernel, syn, L0, p, trace=False):
+    dc = S.DeviceCode.from_code(code)
+    _native.sagms_set_plan(dc.handle, kernel)
+    return G.gpu_decode(dc, syn, L0, p, trace=trace)
+
+
+def _same(a, b):
+    return all(np.array_equal(a[k], b[k]) for k in ("err", "conv", "iters"))
+
+
+@pytest.mark.parametrize("mode", ["ms", "sms", "sagms"])
+@pytest.mark.parametrize("key", [(1023, 5), (1024, 4), "ragged"])
+def test_group_kernel_bitwise_identical_to_other_kernels(group_codes, mode, key):
+    c = group_codes[key]
+    _, syn, L0, _ = I.workload(c, [0.005, 0.02, 0.05], 3001, seed=71)
+    p = PARAMS[mode]
+    ref = _decode_with_kernel(c, KERNEL_GENERIC, syn, L0, p)
+    for kernel in (KERNEL_SLOTS, KERNEL_GROUPS):
+        assert _same(_decode_with_kernel(c, kernel, syn, L0, p), ref), kernel
+    tr = _decode_with_kernel(c, KERNEL_GENERIC, syn[:24], L0[:24], p, trace=True)["trace"]
+    tg = _decode_with_kernel(c, KERNEL_GROUPS, syn[:24], L0[:24], p, trace=True)["trace"]
+    assert np.array_equal(np.nan_to_num(tr, nan=7.0), np.nan_to_num(tg, nan=7.0))
+
+
+@pytest.mark.parametrize("shots", [1, 2, 3, 5, 300, 305])
+def test_group_kernel_small_and_ragged_batches(group_codes, shots):
+    """Fewer shots than groups, one idle group, and batch tails that end mid-chunk."""
+    c = group_codes[(1023, 5)]
+    _, syn, L0, _ = I.workload(c, [0.03], shots, seed=shots)
+    p = PARAMS["sagms"]
+    assert _same(_decode_with_kernel(c, KERNEL_GROUPS, syn, L0, p),
+                 _decode_with_kernel(c, KERNEL_GENERIC, syn, L0, p))
+
+
+def test_group_kernel_edge_inputs(group_codes):
+    """Zero syndromes, negative and zero priors, invalid priors, max_iter = 0 and no early stop."""
+    c = group_codes[(1024, 4)]
+    _, syn, L0, _ = I.workload(c, [0.02], 400, seed=5)
+    syn = syn.copy()
+    L0 = L0.copy()
+    syn[::7] = 0
+    L0[5::11] = -L0[5::11]
+    L0[9::13] = 0.0
+    L0[[3, 50, 399]] = [np.nan, np.inf, -np.inf]
+    for p in (PARAMS["sagms"], _with(PARAMS["sagms"], max_iter=0),
+              _with(PARAMS["ms"], max_iter=9, flags=S.FLAG_NO_EARLY_STOP)):
+        g = _decode_with_kernel(c, KERNEL_GROUPS, syn, L0, p)
+        assert _same(g, _decode_with_kernel(c, KERNEL_GENERIC, syn, L0, p))
+        assert (g["iters"][[3, 50, 399]] == -1).all()
+
+
+def test_group_kernel_oracle_parity(group_codes):
+    """The group kernel directly against the FP64 oracle (same acceptance as the other
+    kernels: exact agreement except for shots traced to near-ties or ill-conditioning)."""
+    c = group_codes["ragged"]
+    dc = S.DeviceCode.from_code(c)
+    _native.sagms_set_plan(dc.handle, KERNEL_GROUPS)
+    _, syn, L0, _ = I.workload(c, [0.01, 0.03], 400, seed=88)
+    G.compare(c, dc, syn, L0, PARAMS["sagms"])
+
+
+def test_group_kernel_falls_back_for_per_qubit_priors(group_codes):
+    """Per-qubit priors are not a two-group shape: a two-group plan falls back to the
+    two-slot kernel, with identical results."""
+    c = group_codes[(1023, 5)]
+    _, syn = I.sample(c, 0.02, 500, seed=8)
+    L0q = I.llr_prior(np.random.default_rng(3).uniform(0.005, 0.05, size=c.n)).astype(np.float32)
+    p = _with(PARAMS["sagms"], flags=S.FLAG_L0_PER_QUBIT)
+    assert _same(_decode_with_kernel(c, KERNEL_GROUPS, syn, L0q, p),
+                 _decode_with_kernel(c, KERNEL_GENERIC, syn, L0q, p))
+
+
+def test_set_plan_rejects_unknown_bits(group_codes):
+    dc = S.DeviceCode.from_code(group_codes[(1023, 5)])
+    with pytest.raises(_native.SagmsError):
+        _native.sagms_set_plan(dc.handle, 1 << 4)
+    _native.sagms_set_plan(dc.handle, KERNEL_GROUPS | (1 << 16))
