@@ -222,11 +222,12 @@ void sagms_graph_destroy(sagms_graph* graph);
  * batching, or one shot per CTA), CTAs per SM, shots per claimed chunk -- times them with
  * CUDA events on `stream` (synchronising it), stores the fastest in the code handle for
  * later decodes, and returns it in *plan with its rate in *shots_per_s.
- * A plan packs: bits 0-1 the kernel (0 automatic, 1 one shot per CTA, 2 two-slot,
- * 3 two-group), bits 8-15 CTAs per SM (0: occupancy limit), bits 16-19 log2 of the shots
- * per claimed chunk (0: automatic); other bits must be zero.  A kernel the code or the
- * parameters cannot use falls back to the next one in the order two-group, two-slot, one
- * shot per CTA.
+ * A plan packs: bits 0-2 the kernel (0 automatic, 1 one shot per CTA, 2 two-slot,
+ * 3 two-group, 4 two-group with column-indexed messages), bits 8-15 CTAs per SM (0:
+ * occupancy limit), bits 16-19 log2 of the shots per claimed chunk (0: automatic); other
+ * bits must be zero and the kernel at most 4.  A kernel the code or the parameters cannot
+ * use falls back to the next one in the order column-indexed two-group, two-group,
+ * two-slot, one shot per CTA.
  * Results of a decode do not depend on the plan.  With the environment variable
  * SAGMS_AUTOTUNE_CACHE naming a file, the plan is also appended there and sagms_load_code
  * of the same matrix starts from it.

@@ -134,7 +134,8 @@ def decode_host(code: DeviceCode, syn, L0, params: Params | None = None, out=Non
 
 def decode_plan(plan: int) -> dict:
     """Unpack a launch plan returned by sagms_autotune."""
-    return {"kernel": {0: "auto", 1: "one-shot-per-CTA", 2: "two-slot", 3: "two-group"}[plan & 3],
+    return {"kernel": {0: "auto", 1: "one-shot-per-CTA", 2: "two-slot", 3: "two-group",
+                       4: "two-group-qc"}[plan & 7],
             "ctas_per_sm": (plan >> 8) & 0xff, "chunk_lg": (plan >> 16) & 0xf}
 
 

@@ -21,6 +21,7 @@
 #include "decode_kernel.cuh"
 #include "decode_slots.cuh"
 #include "decode_groups.cuh"
+#include "decode_qc.cuh"
 #include "internal.h"
 
 using namespace sagms;
@@ -76,6 +77,18 @@ constexpr int kGroupDC = 10, kGroupDV = 5;
 using GroupFn = void (*)(const DecodeArgs, const GroupLayout);
 GroupFn group_kernel_fn() { return group_kernel<kGroupDC, kGroupDV>; }
 
+// Column-indexed two-group kernels (decode_qc.cuh): (DC, DV) with DC = 2 DV.
+constexpr int kQcDV[] = {3, 4, 5};
+constexpr int kNumQc = sizeof(kQcDV) / sizeof(kQcDV[0]);
+using QcFn = void (*)(const DecodeArgs, const uint32_t*);
+QcFn qc_kernel_for(int v) {
+    switch (v) {
+        case 0: return qc_kernel<6, 3>;
+        case 1: return qc_kernel<8, 4>;
+        default: return qc_kernel<10, 5>;
+    }
+}
+
 constexpr int kMaxDevices = 64;
 
 // Autotune cache: when SAGMS_AUTOTUNE_CACHE names a file, sagms_autotune appends
@@ -107,13 +120,13 @@ void store_cached_plan(uint64_t key, uint32_t pl) {
 using sagms_internal::Plan;
 Plan unpack_plan(uint32_t v) {
     Plan p;
-    p.kernel = (int)(v & 3u);
+    p.kernel = (int)(v & 7u);
     p.ctas_per_sm = (int)((v >> 8) & 0xffu);
     p.chunk_lg = (int)((v >> 16) & 0xfu);
     return p;
 }
 uint32_t pack_plan(const Plan& p) {
-    return (uint32_t)(p.kernel & 3) | ((uint32_t)(p.ctas_per_sm & 0xff) << 8) | ((uint32_t)(p.chunk_lg & 0xf) << 16);
+    return (uint32_t)(p.kernel & 7) | ((uint32_t)(p.ctas_per_sm & 0xff) << 8) | ((uint32_t)(p.chunk_lg & 0xf) << 16);
 }
 
 // Largest launch of the two-slot kernel: its per-shot indexing (shot * words per pattern)
@@ -170,9 +183,11 @@ struct sagms_code {
     bool groups;           // the two-group kernel covers this code
     uint16_t* d_colG;      // [2][kGroupDC][1024] byte offsets of P_g entries
     uint32_t* d_vneG;      // [2][kGroupDV][2048] byte offsets of C_g entries
+    int qc_variant;        // -1: no column-indexed kernel for this code
+    uint32_t* d_colQ;      // [DC][512] packed byte offsets 4 * col of checks t and t + 512
     // Launch plan chosen by sagms_autotune (0 = defaults), packed so decodes on other
-    // threads read it atomically: bits 0-1 kernel (0 auto, 1 one-shot-per-CTA, 2 two-slot,
-    // 3 two-group),
+    // threads read it atomically: bits 0-2 kernel (0 auto, 1 one-shot-per-CTA, 2 two-slot,
+    // 3 two-group, 4 two-group with column-indexed messages),
     // bits 8-15 CTAs per SM (0 = occupancy limit), bits 16-19 log2 shots per claimed chunk
     // (0 = automatic).
     mutable std::atomic<uint32_t> plan;
@@ -331,10 +346,42 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
         }
     }
 
+    // Column-indexed layout, when every edge in check slot j is its qubit's edge number
+    // j mod DV and a qubit's edges in increasing slot have increasing numbers (the smallest
+    // compiled DV that covers the degrees and has that structure).
+    int qv = -1;
+    if (m > 512 && m <= kGrpChecks && n <= kGrpQubits) {
+        for (int v = 0; v < kNumQc && qv < 0; ++v) {
+            const int DVq = kQcDV[v];
+            if (dc_max > 2 * DVq || dv_max > DVq) continue;
+            bool ok = true;
+            for (int c = 0; c < n && ok; ++c) {
+                const auto& ve = vedges[c];   // sorted by slot
+                for (size_t q = 1; q < ve.size() && ok; ++q)
+                    ok = (ve[q].first % DVq) > (ve[q - 1].first % DVq);
+            }
+            if (ok) qv = v;
+        }
+    }
+    std::vector<uint32_t> colQ;
+    if (qv >= 0) {
+        const int DCq = 2 * kQcDV[qv];
+        colQ.assign((size_t)DCq * kGrpThreads, 0u);
+        for (int i = 0; i < kGrpChecks; ++i) {
+            const int d = (i < m) ? row_ptr[i + 1] - row_ptr[i] : 0;
+            for (int j = 0; j < DCq; ++j) {
+                const uint32_t o = (j < d) ? (uint32_t)col_idx[row_ptr[i] + j] * 4u : kQcPadOff;
+                colQ[(size_t)j * kGrpThreads + (i % kGrpThreads)] |= (i < kGrpThreads) ? o : (o << 16);
+            }
+        }
+    }
+
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
     sagms_code* code = new sagms_code();
+    code->qc_variant = qv;
+    code->d_colQ = nullptr;
     code->slot_variant = sv;
     code->d_colB = nullptr;
     code->d_vneB = nullptr;
@@ -372,6 +419,10 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
         if (ce == cudaSuccess) ce = cudaMemcpy(code->d_colG, colG.data(), colG.size() * 2, cudaMemcpyHostToDevice);
         if (ce == cudaSuccess) ce = cudaMemcpy(code->d_vneG, vneG.data(), vneG.size() * 4, cudaMemcpyHostToDevice);
     }
+    if (ce == cudaSuccess && qv >= 0) {
+        ce = cudaMalloc(&code->d_colQ, colQ.size() * sizeof(uint32_t));
+        if (ce == cudaSuccess) ce = cudaMemcpy(code->d_colQ, colQ.data(), colQ.size() * 4, cudaMemcpyHostToDevice);
+    }
     if (ce != cudaSuccess) {
         cudaFree(code->d_colT);
         cudaFree(code->d_vneT);
@@ -379,6 +430,7 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
         cudaFree(code->d_vneB);
         cudaFree(code->d_colG);
         cudaFree(code->d_vneG);
+        cudaFree(code->d_colQ);
         delete code;
         return cuda_fail(ce, "sagms_load_code upload");
     }
@@ -397,6 +449,7 @@ void sagms_free_code(sagms_code* code) {
     cudaFree(code->d_vneB);
     cudaFree(code->d_colG);
     cudaFree(code->d_vneG);
+    cudaFree(code->d_colQ);
     if (prev >= 0 && prev != code->device) cudaSetDevice(prev);
     delete code;
 }
@@ -446,8 +499,10 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     // Kernel: the plan's choice where the code and parameters allow it, else the fastest
     // that does (two-group, two-slot, one-shot-per-CTA).
     const bool msfam_fast = !bp && !(p->flags & SAGMS_FLAG_GENERIC_KERNEL);
-    const bool use_groups = msfam_fast && code->groups && !per_qubit && (plan.kernel == 0 || plan.kernel == 3);
-    const bool use_slots = !use_groups && msfam_fast && code->slot_variant >= 0 && plan.kernel != 1;
+    const bool use_qc = msfam_fast && code->qc_variant >= 0 && !per_qubit && (plan.kernel == 0 || plan.kernel == 4);
+    const bool use_groups = !use_qc && msfam_fast && code->groups && !per_qubit &&
+                            (plan.kernel == 0 || plan.kernel == 3 || plan.kernel == 4);
+    const bool use_slots = !use_qc && !use_groups && msfam_fast && code->slot_variant >= 0 && plan.kernel != 1;
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
@@ -459,7 +514,13 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     size_t smem;
     int threads;
     long long units;
-    if (use_groups) {
+    if (use_qc) {
+        const int DVq = kQcDV[code->qc_variant];
+        fn = reinterpret_cast<const void*>(qc_kernel_for(code->qc_variant));
+        smem = qc_smem_bytes(2 * DVq, DVq);
+        threads = 2 * kGrpThreads;
+        units = (shots + 1) / 2;   // two shots in flight per CTA
+    } else if (use_groups) {
         fn = reinterpret_cast<const void*>(group_kernel_fn());
         smem = grp_smem_bytes(kGroupDC, kGroupDV);
         threads = 2 * kGrpThreads;
@@ -487,7 +548,7 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     if (plan.ctas_per_sm > 0) per_sm = std::min(per_sm, plan.ctas_per_sm);
     long long grid = std::min<long long>(units, (long long)per_sm * sms);
     if (plan.max_grid > 0) grid = std::min(grid, plan.max_grid);
-    if (!use_groups && !use_slots) {
+    if (!use_qc && !use_groups && !use_slots) {
         kernel_for(code->variant, bp)<<<(unsigned)grid, threads, smem, stream>>>(a);
         ce = cudaGetLastError();
         if (ce != cudaSuccess) return cuda_fail(ce, "decode launch");
@@ -526,7 +587,9 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
         c.work = d_work + ci;
         const long long g = std::min(grid, (cnt + 1) / 2);
         c.chunk_lg = plan.chunk_lg > 0 ? plan.chunk_lg : chunk_lg_for(cnt, g);
-        if (use_groups)
+        if (use_qc)
+            qc_kernel_for(code->qc_variant)<<<(unsigned)g, threads, smem, stream>>>(c, code->d_colQ);
+        else if (use_groups)
             group_kernel_fn()<<<(unsigned)g, threads, smem, stream>>>(c, glay);
         else
             slot_kernel_for(code->slot_variant)<<<(unsigned)g, threads, smem, stream>>>(c, slay);
@@ -705,11 +768,13 @@ int sagms_autotune(const sagms_code* code, const sagms_params* params, int64_t s
     std::vector<Plan> cands;
     const bool slots_ok = params->mode != SAGMS_BP && code->slot_variant >= 0;
     const bool groups_ok = params->mode != SAGMS_BP && code->groups && !(params->flags & SAGMS_FLAG_L0_PER_QUBIT);
-    for (int kernel : {3, 2, 1}) {
+    const bool qc_ok = params->mode != SAGMS_BP && code->qc_variant >= 0 && !(params->flags & SAGMS_FLAG_L0_PER_QUBIT);
+    for (int kernel : {4, 3, 2, 1}) {
         if (kernel == 2 && !slots_ok) continue;
         if (kernel == 3 && !groups_ok) continue;
+        if (kernel == 4 && !qc_ok) continue;
         for (int cps : {0, 2, 1}) {
-            if (kernel == 3 && cps != 0) continue;   // one 1024-thread CTA per SM
+            if (kernel >= 3 && cps != 0) continue;   // one 1024-thread CTA per SM
             if (kernel >= 2) {
                 for (int clg : {0, 1, 2, 4}) {
                     Plan pl;
@@ -757,7 +822,8 @@ int sagms_autotune(const sagms_code* code, const sagms_params* params, int64_t s
 
 int sagms_set_plan(sagms_code* code, int32_t plan) {
     if (!code) return fail(SAGMS_ERR_ARG, "code is NULL");
-    if ((uint32_t)plan & ~0xfff03u) return fail(SAGMS_ERR_ARG, "unknown bits in plan 0x%x", (unsigned)plan);
+    if (((uint32_t)plan & ~0xfff07u) || ((uint32_t)plan & 7u) > 4u)
+        return fail(SAGMS_ERR_ARG, "unknown bits in plan 0x%x", (unsigned)plan);
     code->plan.store((uint32_t)plan);
     return SAGMS_OK;
 }

@@ -1,10 +1,11 @@
-"""The two-group kernel (two 512-thread groups per CTA, one shot each) against the
-one-shot-per-CTA kernel and the two-slot kernel, on the codes it covers (more than 512 and at
-most 1024 checks, at most 2048 qubits).
+"""The two-group kernels (two 512-thread groups per CTA, one shot each; the general layout
+and the column-indexed one for codes whose edges line up slot by slot) against the
+one-shot-per-CTA kernel and the two-slot kernel, on the codes they cover (more than 512 and
+at most 1024 checks, at most 2048 qubits).
 
-All three run each shot's arithmetic in the same order, so outputs and posterior traces must
-agree bit for bit; parity of the one-shot-per-CTA kernel against the FP64 oracle is covered
-in test_parity_gpu.py, and one oracle comparison here pins the group kernel directly."""
+All of them run each shot's arithmetic in the same order, so outputs and posterior traces
+must agree bit for bit; parity of the one-shot-per-CTA kernel against the FP64 oracle is
+covered in test_parity_gpu.py, and oracle comparisons here pin the group kernels directly."""
 import numpy as np
 import pytest
 import torch
@@ -16,7 +17,7 @@ from tests import gpu_helpers as G
 
 pytestmark = pytest.mark.gpu
 
-KERNEL_GENERIC, KERNEL_SLOTS, KERNEL_GROUPS = 1, 2, 3
+KERNEL_GENERIC, KERNEL_SLOTS, KERNEL_GROUPS, KERNEL_QC = 1, 2, 3, 4
 PARAMS = {
     "ms": S.Params(mode="ms", max_iter=60),
     "sms": S.Params(mode="sms", alpha=0.75, max_iter=60),
@@ -47,7 +48,28 @@ def group_codes():
         j = int(np.argmax(H.sum(axis=0)))
         H[np.nonzero(H[:, j])[0][0], j] = 0
     out["ragged"] = I.code_from_dense(H)
+    out["gb-truncated"] = _truncated_gb(1023, 5)
     return out
+
+
+def _truncated_gb(l, w):
+    """GB(l, w) with trailing edges dropped from some rows (rows keep polynomial-term order,
+    so the column-indexed layout still applies): check degrees 2w, 2w - 1, 1 and 0, qubit
+    degrees w and below."""
+    g = I.gb_code(l, w)
+    rows = []
+    for i in range(g.m):
+        r = list(g.col_idx[g.row_ptr[i]:g.row_ptr[i + 1]])
+        if i % 13 == 5:
+            r = []
+        elif i % 11 == 3:
+            r = r[:1]
+        elif i % 7 == 0:
+            r = r[:-1]
+        rows.append(r)
+    row_ptr = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    col_idx = np.concatenate([np.asarray(r, dtype=np.int32) for r in rows])
+    return I.Code(m=g.m, n=g.n, row_ptr=row_ptr, col_idx=col_idx, name=f"truncated GB({l},{w})")
 
 
 def _decode_with_kernel(code, kernel, syn, L0, p, trace=False):
@@ -61,32 +83,36 @@ def _same(a, b):
 
 
 @pytest.mark.parametrize("mode", ["ms", "sms", "sagms"])
-@pytest.mark.parametrize("key", [(1023, 5), (1024, 4), "ragged"])
+@pytest.mark.parametrize("key", [(1023, 5), (1024, 4), "ragged", "gb-truncated"])
 def test_group_kernel_bitwise_identical_to_other_kernels(group_codes, mode, key):
     c = group_codes[key]
     _, syn, L0, _ = I.workload(c, [0.005, 0.02, 0.05], 3001, seed=71)
     p = PARAMS[mode]
     ref = _decode_with_kernel(c, KERNEL_GENERIC, syn, L0, p)
-    for kernel in (KERNEL_SLOTS, KERNEL_GROUPS):
+    for kernel in (KERNEL_SLOTS, KERNEL_GROUPS, KERNEL_QC):
         assert _same(_decode_with_kernel(c, kernel, syn, L0, p), ref), kernel
     tr = _decode_with_kernel(c, KERNEL_GENERIC, syn[:24], L0[:24], p, trace=True)["trace"]
-    tg = _decode_with_kernel(c, KERNEL_GROUPS, syn[:24], L0[:24], p, trace=True)["trace"]
-    assert np.array_equal(np.nan_to_num(tr, nan=7.0), np.nan_to_num(tg, nan=7.0))
+    for kernel in (KERNEL_GROUPS, KERNEL_QC):
+        tg = _decode_with_kernel(c, kernel, syn[:24], L0[:24], p, trace=True)["trace"]
+        assert np.array_equal(np.nan_to_num(tr, nan=7.0), np.nan_to_num(tg, nan=7.0)), kernel
 
 
+@pytest.mark.parametrize("kernel", [KERNEL_GROUPS, KERNEL_QC])
 @pytest.mark.parametrize("shots", [1, 2, 3, 5, 300, 305])
-def test_group_kernel_small_and_ragged_batches(group_codes, shots):
+def test_group_kernel_small_and_ragged_batches(group_codes, shots, kernel):
     """Fewer shots than groups, one idle group, and batch tails that end mid-chunk."""
     c = group_codes[(1023, 5)]
     _, syn, L0, _ = I.workload(c, [0.03], shots, seed=shots)
     p = PARAMS["sagms"]
-    assert _same(_decode_with_kernel(c, KERNEL_GROUPS, syn, L0, p),
+    assert _same(_decode_with_kernel(c, kernel, syn, L0, p),
                  _decode_with_kernel(c, KERNEL_GENERIC, syn, L0, p))
 
 
-def test_group_kernel_edge_inputs(group_codes):
+@pytest.mark.parametrize("kernel", [KERNEL_GROUPS, KERNEL_QC])
+@pytest.mark.parametrize("key", [(1024, 4), "gb-truncated"])
+def test_group_kernel_edge_inputs(group_codes, key, kernel):
     """Zero syndromes, negative and zero priors, invalid priors, max_iter = 0 and no early stop."""
-    c = group_codes[(1024, 4)]
+    c = group_codes[key]
     _, syn, L0, _ = I.workload(c, [0.02], 400, seed=5)
     syn = syn.copy()
     L0 = L0.copy()
@@ -96,17 +122,19 @@ def test_group_kernel_edge_inputs(group_codes):
     L0[[3, 50, 399]] = [np.nan, np.inf, -np.inf]
     for p in (PARAMS["sagms"], _with(PARAMS["sagms"], max_iter=0),
               _with(PARAMS["ms"], max_iter=9, flags=S.FLAG_NO_EARLY_STOP)):
-        g = _decode_with_kernel(c, KERNEL_GROUPS, syn, L0, p)
+        g = _decode_with_kernel(c, kernel, syn, L0, p)
         assert _same(g, _decode_with_kernel(c, KERNEL_GENERIC, syn, L0, p))
         assert (g["iters"][[3, 50, 399]] == -1).all()
 
 
-def test_group_kernel_oracle_parity(group_codes):
-    """The group kernel directly against the FP64 oracle (same acceptance as the other
+@pytest.mark.parametrize("key,kernel", [("ragged", KERNEL_GROUPS), ("gb-truncated", KERNEL_QC),
+                                        ((1023, 5), KERNEL_QC)])
+def test_group_kernel_oracle_parity(group_codes, key, kernel):
+    """The group kernels directly against the FP64 oracle (same acceptance as the other
     kernels: exact agreement except for shots traced to near-ties or ill-conditioning)."""
-    c = group_codes["ragged"]
+    c = group_codes[key]
     dc = S.DeviceCode.from_code(c)
-    _native.sagms_set_plan(dc.handle, KERNEL_GROUPS)
+    _native.sagms_set_plan(dc.handle, kernel)
     _, syn, L0, _ = I.workload(c, [0.01, 0.03], 400, seed=88)
     G.compare(c, dc, syn, L0, PARAMS["sagms"])
 
@@ -118,12 +146,14 @@ def test_group_kernel_falls_back_for_per_qubit_priors(group_codes):
     _, syn = I.sample(c, 0.02, 500, seed=8)
     L0q = I.llr_prior(np.random.default_rng(3).uniform(0.005, 0.05, size=c.n)).astype(np.float32)
     p = _with(PARAMS["sagms"], flags=S.FLAG_L0_PER_QUBIT)
-    assert _same(_decode_with_kernel(c, KERNEL_GROUPS, syn, L0q, p),
-                 _decode_with_kernel(c, KERNEL_GENERIC, syn, L0q, p))
+    for kernel in (KERNEL_GROUPS, KERNEL_QC):
+        assert _same(_decode_with_kernel(c, kernel, syn, L0q, p),
+                     _decode_with_kernel(c, KERNEL_GENERIC, syn, L0q, p))
 
 
 def test_set_plan_rejects_unknown_bits(group_codes):
     dc = S.DeviceCode.from_code(group_codes[(1023, 5)])
-    with pytest.raises(_native.SagmsError):
-        _native.sagms_set_plan(dc.handle, 1 << 4)
-    _native.sagms_set_plan(dc.handle, KERNEL_GROUPS | (1 << 16))
+    for bad in (1 << 4, 5, 7):
+        with pytest.raises(_native.SagmsError):
+            _native.sagms_set_plan(dc.handle, bad)
+    _native.sagms_set_plan(dc.handle, KERNEL_QC | (1 << 16))

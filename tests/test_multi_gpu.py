@@ -80,7 +80,7 @@ def test_every_launch_plan_gives_identical_results(jobs_spec):
     dc, syn, L0, p = jobs_spec[4]
     ref = S.decode(dc, syn, L0, p)
     torch.cuda.synchronize()
-    for kernel in (0, 1, 2, 3):
+    for kernel in (0, 1, 2, 3, 4):
         for cps in (0, 1, 2):
             for clg in (0, 1, 3, 4):
                 _native.sagms_set_plan(dc.handle, kernel | (cps << 8) | (clg << 16))
