@@ -40,8 +40,9 @@ SAGMS_KW = dict(alpha_min=0.30, alpha_max=0.50, eta_unsat=1.10)
 SMS_ALPHA = 0.75
 MAX_ITER = 100
 NOISE_SEED = 20260513
-PROFILE = os.path.join(ROOT, "profiles", "slot_kernel_gb1023_sagms.md")
-KERNEL_SRC = [os.path.join(ROOT, "paper_2605_10433_gb300", "csrc", f) for f in ("decode_slots.cuh", "decode_kernel.cuh")]
+PROFILE = os.path.join(ROOT, "profiles", "qc_kernel_gb1023_sagms.md")
+KERNEL_SRC = [os.path.join(ROOT, "paper_2605_10433_gb300", "csrc", f)
+              for f in ("decode_qc.cuh", "decode_groups.cuh", "decode_slots.cuh", "decode_kernel.cuh")]
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -368,12 +369,19 @@ def main():
     peak = roofline.alu_peak_ops(props.multi_processor_count, sm_max)
     traffic = profile_traffic(shots)
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
-            "frac": achieved / peak, "traffic": traffic,
+            "frac": achieved / peak, "traffic": traffic, "kernel": "sagms::qc_kernel<10,5,4>",
             "note": (f"ops = sum over shots of iters x {ops_it} per iteration (Eq. 15 / Table I CN cost + VN sum, "
                      f"decision, residual XOR, popcount); peak = {props.multi_processor_count} SMs x 128 lanes x "
-                     f"{sm_max:.0f} MHz; HBM bound {roofline.hbm_bytes_per_shot(code.m, code.n)} B/shot at "
+                     f"{sm_max:.0f} MHz (derived from unit counts and clock); HBM bound "
+                     f"{roofline.hbm_bytes_per_shot(code.m, code.n)} B/shot at "
                      f"{peaks.get('hbm_gbs', 'n/a')} GB/s is "
                      f"{(peaks.get('hbm_gbs', 6793.1) * 1e9 / roofline.hbm_bytes_per_shot(code.m, code.n)):.3g} shots/s")}
+    smem_b = roofline.smem_bytes(it_host, code.nnz, code.n)
+    smem_peak = roofline.smem_peak_bytes(props.multi_processor_count, sm_max)
+    roof_smem = {"bound": "smem", "achieved": smem_b / (ms_step / 1e3) / 1e9, "peak": smem_peak / 1e9, "unit": "GB/s",
+                 "frac": smem_b / (ms_step / 1e3) / smem_peak,
+                 "note": ("diagnostic roof: on-chip bytes of the flooding schedule (16E r - 4E + 4n r per shot of r "
+                          "iterations) over SMs x 128 B x clock (derived)")}
 
     fer = {}
     for k, p in enumerate(P_VALUES):
@@ -390,6 +398,7 @@ def main():
                       "l2": f"inputs larger than L2: {syn.nbytes / 1e9:.2f} GB syndromes per GPU",
                       "parallelism": f"shot-sharded x{world}"},
            "gpu_launches": args.steps, "mean_iters": float(it_host.mean()), "fer": fer, "roofline": roof,
+           "roofline_smem": roof_smem,
            "clocks": clk, "input_gen_s": gen_s}
 
     if not args.no_extras:

@@ -5,23 +5,23 @@
 // structure (slot j < w is term j of a(x) and qubit c < l meets it as its j-th edge; slot
 // w + k is term k of b(x)), with DC = 2w and DV = w.
 //
-// Groups and shots are those of decode_groups.cuh: a 1024-thread CTA holds two independent
-// 512-thread groups, each decoding one shot at a time with its own named barriers.  Thread
-// tg of a group owns checks tg and tg + 512 and the qubit pairs (2tg, 2tg + 1) and
-// (1024 + 2tg, 1024 + 2tg + 1).
+// A CTA holds two independent groups of T = 1024 / K threads; each group decodes one shot at
+// a time and refills as shots finish (as in decode_groups.cuh), synchronised by its own named
+// barriers, so one group's arithmetic-bound check-node phase overlaps the other's
+// shared-memory-bound phases.  Thread tg of a group owns the K checks tg + kT and the K qubit
+// pairs (2tg + 2hT, 2tg + 2hT + 1), h < K.  The byte offsets of its checks' columns stay in
+// registers for the whole launch (K * DC of them: with K = 4 the 512-thread CTA has 128
+// registers per thread).
 //
 // Shared memory per group g (byte offsets are compile-time for each group):
 //   P_g[2048 + 4]          posteriors; P_g[2048] = +inf is the column padded check slots read
 //   C_g[q][2048 + 4]       negated message D = -L_{i->c} of qubit c's q-th edge at [q][c];
 //                          column 2048 is scratch for padded check slots
-// and, shared by both groups,
-//   colQ[DC][512]          u32: byte offsets 4 * col of checks tg (low half) and tg + 512
-//                          (high half) in slot j (2048 for a padded slot)
 // A check thread reaches P_g[col] and C_g[j mod DV][col] from the same offset register, and a
-// qubit thread reads its messages at fixed offsets: no index loads in the variable-node
-// update.  A freshly loaded shot's first round has every check send the same message on all
-// of its edges (all inputs are the prior), so that round stores one closed-form value per
-// check instead of running the check-node minimum search.
+// qubit thread reads its messages at fixed offsets: no index loads at all.  A freshly loaded
+// shot's first round has every check send the same message on all of its edges (all inputs
+// are the prior), so that round stores one closed-form value per check instead of running
+// the check-node minimum search.
 //
 // The arithmetic of every check and qubit is, operation for operation, that of
 // decode_kernel.cuh: results are bitwise identical to the other kernels.
@@ -33,23 +33,23 @@ namespace sagms {
 
 constexpr int kQcRowBytes = (kGrpQubits + 4) * 4;    // one qubit-indexed row plus padding column
 constexpr uint32_t kQcPadOff = (uint32_t)kGrpQubits * 4;
+constexpr int kQcMisc = 320;                          // per-group bookkeeping bytes
 
 __host__ __device__ constexpr size_t qc_group_bytes(int DV) { return (size_t)(1 + DV) * kQcRowBytes; }
 __host__ __device__ constexpr size_t qc_P_off(int DV, int g) { return (size_t)g * qc_group_bytes(DV); }
 __host__ __device__ constexpr size_t qc_C_off(int DV, int g, int q) {
     return qc_P_off(DV, g) + (size_t)(1 + q) * kQcRowBytes;
 }
-__host__ __device__ constexpr size_t qc_col_off(int DV) { return 2 * qc_group_bytes(DV); }
-__host__ __device__ constexpr size_t qc_misc_off(int DC, int DV) {
-    return qc_col_off(DV) + (size_t)DC * kGrpThreads * 4;
-}
-__host__ __device__ constexpr size_t qc_smem_bytes(int DC, int DV) {
-    return qc_misc_off(DC, DV) + 2 * kGrpMiscPerGroup + 32 * 4;
-}
+__host__ __device__ constexpr size_t qc_misc_off(int DV) { return 2 * qc_group_bytes(DV); }
+__host__ __device__ constexpr size_t qc_smem_bytes(int DV) { return qc_misc_off(DV) + 2 * kQcMisc + 32 * 4; }
 
-template <int DC, int DV, int G>
+// Bits of a per-check field for check k of a thread (K <= 4 checks, 8 bits each).
+__device__ __forceinline__ uint32_t qc_byte(uint32_t x, int k) { return (x >> (8 * k)) & 0xffu; }
+
+template <int DC, int DV, int K, int G>
 __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* smem, const int tg,
-                                         const uint32_t degs) {
+                                         const uint32_t (&off)[K][DC], const uint32_t degs) {
+    constexpr int T = 1024 / K;               // threads per group
     constexpr int NP = kGrpQubits;
     constexpr size_t PO = qc_P_off(DV, G);
     const bool early = (a.flags & kFlagNoEarlyStop) == 0;
@@ -58,15 +58,14 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
     const int mw = (m + 31) >> 5, nw = (n + 31) >> 5;
     const float inf = __uint_as_float(0x7f800000u);
     float* P = reinterpret_cast<float*>(smem + PO);
-    const uint32_t* colQ = reinterpret_cast<const uint32_t*>(smem + qc_col_off(DV));
-    unsigned char* misc = smem + qc_misc_off(DC, DV);
-    int* cnt = reinterpret_cast<int*>(misc + G * kGrpMiscPerGroup);   // [2 parity]
+    unsigned char* misc = smem + qc_misc_off(DV);
+    int* cnt = reinterpret_cast<int*>(misc + G * kQcMisc);   // [2 parity]
     int* claim = cnt + 2;
     int* pfidx = cnt + 4;
     int* shotsm = cnt + 6;
     float* pfl0 = reinterpret_cast<float*>(cnt + 8);
     uint32_t* pfsyn = reinterpret_cast<uint32_t*>(cnt + 16);
-    const uint32_t* flipw = reinterpret_cast<const uint32_t*>(misc + 2 * kGrpMiscPerGroup);
+    const uint32_t* flipw = reinterpret_cast<const uint32_t*>(misc + 2 * kQcMisc);
     auto Pat = [&](uint32_t o) -> float& { return *reinterpret_cast<float*>(smem + PO + o); };
     auto Cat = [&](int j, uint32_t o) -> float& {
         return *reinterpret_cast<float*>(smem + qc_C_off(DV, G, j % DV) + o);
@@ -82,7 +81,10 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
         claim[0] = dynamic ? atomicAdd(a.work, 1) : gid;
         claim[1] = dynamic ? atomicAdd(a.work, 1) : gid + gstride;
     }
-    group_barrier(G);
+    asm volatile("bar.sync %0, %1;" ::"n"(1 + G), "n"(T) : "memory");
+    // Shots: chunks of 2^chunk_lg consecutive shots, claimed dynamically through the work
+    // counter (one atomic per chunk, a chunk ahead of its use, via the two-entry ring
+    // `claim`), or statically: group b = 2 * CTA + g takes chunks b, b + 2G, ...
     int seqp = 0;
     auto assign = [&]() -> int {
         const int p = seqp++;
@@ -92,6 +94,8 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
             claim[(c + 1) & 1] = dynamic ? atomicAdd(a.work, 1) : gid + (c + 1) * gstride;
         return idx < (long long)nshots ? (int)idx : nshots;
     };
+    // The next shot's syndrome row and prior are copied into shared memory by warp 0 with
+    // cp.async one refill ahead (double-buffered).
     auto prefetch = [&](int b, int s) {
         if (tg < 32 && s < nshots) {
             if (lane < mw) cp_async4(pfsyn + b * 32 + lane, a.syn + s * mw + lane);
@@ -109,38 +113,37 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
     int state = kPending;
     int itk = 0;
     float prior = 0.0f;
-    uint32_t sbits = 0;   // bit 0: syndrome bit of check tg, bit 1: of check tg + 512
+    uint32_t sbits = 0;   // bit k: syndrome bit of check tg + kT
     int pbuf = 0;
     int ph = 0;
-    // degs: degree of check tg in bits 0-7, of check tg + 512 in bits 8-15; a negative
-    // prior flips a check's first residual bit when its degree is odd.
+    const bool tracing = a.trace != nullptr;
 
     while (true) {
-        // A5: gather the two checks' posteriors, residual bits, unsatisfied count
-        uint32_t wq[DC];
-        float2 v[DC];
+        // A5: gather the checks' posteriors, residual bits, unsatisfied count
+        float2 v[K / 2][DC];
+        uint32_t xb = 0;   // bit k: residual bit of check k
 #pragma unroll
-        for (int j = 0; j < DC; ++j) {
-            wq[j] = colQ[j * kGrpThreads + tg];
-            v[j] = make_float2(Pat(wq[j] & 0xffffu), Pat(wq[j] >> 16));
-        }
-        uint32_t x0 = (sbits & 1u) << 31, x1 = (sbits >> 1) << 31;
+        for (int p = 0; p < K / 2; ++p) {
 #pragma unroll
-        for (int j = 0; j < DC; j += 2) {
-            x0 ^= __float_as_uint(v[j].x) ^ __float_as_uint(v[j + 1].x);
-            x1 ^= __float_as_uint(v[j].y) ^ __float_as_uint(v[j + 1].y);
+            for (int j = 0; j < DC; ++j) v[p][j] = make_float2(Pat(off[2 * p][j]), Pat(off[2 * p + 1][j]));
+            uint32_t x0 = ((sbits >> (2 * p)) & 1u) << 31, x1 = ((sbits >> (2 * p + 1)) & 1u) << 31;
+#pragma unroll
+            for (int j = 0; j < DC; j += 2) {
+                x0 ^= __float_as_uint(v[p][j].x) ^ __float_as_uint(v[p][j + 1].x);
+                x1 ^= __float_as_uint(v[p][j].y) ^ __float_as_uint(v[p][j + 1].y);
+            }
+            xb |= ((x0 >> 31) << (2 * p)) | ((x1 >> 31) << (2 * p + 1));
         }
-        const uint32_t b0 = __ballot_sync(0xffffffffu, x0 >> 31);
-        const uint32_t b1 = __ballot_sync(0xffffffffu, x1 >> 31);
-        if (lane == 0) atomicAdd(&cnt[ph], __popc(b0) + __popc(b1));
+        const int part = __reduce_add_sync(0xffffffffu, __popc(xb));
+        if (lane == 0) atomicAdd(&cnt[ph], part);
         if (tg < 32) cp_async_wait_all();
-        group_barrier(G);
+        asm volatile("bar.sync %0, %1;" ::"n"(1 + G), "n"(T) : "memory");
         int gcnt = cnt[ph];
-        uint32_t st0 = x0 >> 31, st1 = x1 >> 31;
+        uint32_t stb = xb;   // bit k: residual bit of check k this round
         if (tg == 0) cnt[ph ^ 1] = 0;
-        if (a.trace && state == kActive) {
+        if (tracing && state == kActive) {
             float* tr = a.trace + ((size_t)shotsm[pbuf ^ 1] * (size_t)(a.max_iter + 1) + (size_t)itk) * (size_t)n;
-            for (int c = tg; c < n; c += kGrpThreads) tr[c] = P[c];
+            for (int c = tg; c < n; c += T) tr[c] = P[c];
         }
 
         // A6: finish, refill, or count the round about to run.
@@ -153,8 +156,8 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
             if (fin) {
                 const int s = shotsm[pbuf ^ 1];
 #pragma unroll
-                for (int vv = 0; vv < 4; ++vv) {
-                    const int c = vv * kGrpThreads + tg;
+                for (int vv = 0; vv < NP / T; ++vv) {
+                    const int c = vv * T + tg;
                     const uint32_t word = __ballot_sync(0xffffffffu, (c < n) && (__float_as_uint(P[c]) >> 31));
                     if (lane == 0 && c < n) a.err[s * nw + (c >> 5)] = word;
                 }
@@ -172,11 +175,9 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
                 consumed = b;
                 const uint32_t* row = pfsyn + b * 32;
                 const float l0 = pfl0[b];
-                const uint32_t bit0 = (tg < m) ? ((row[tg >> 5] >> (tg & 31)) & 1u) : 0u;
-                const uint32_t bit1 = (tg + 512 < m) ? ((row[(tg + 512) >> 5] >> ((tg + 512) & 31)) & 1u) : 0u;
                 const uint32_t word = (lane < mw) ? row[lane] : 0u;
                 if (!isfinite(l0)) {
-                    for (int w = tg; w < nw; w += kGrpThreads) a.err[s * nw + w] = 0u;
+                    for (int w = tg; w < nw; w += T) a.err[s * nw + w] = 0u;
                     if (tg == 0) { a.conv[s] = 0; a.iters[s] = -1; }
                 } else {
                     const float pi = (l0 > 0.0f) ? 1.0f : ((l0 < 0.0f) ? -1.0f : 0.0f);
@@ -184,12 +185,12 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
                     // First check (l = 0), Eqs. 1 and 6: popcount of s XOR flip.
                     const uint32_t flip_lane = (flipped && lane < mw) ? flipw[lane] : 0u;
                     const int c0 = __reduce_add_sync(0xffffffffu, (int)__popc(word ^ flip_lane));
-                    if (a.trace) {
+                    if (tracing) {
                         float* tr = a.trace + (size_t)s * (size_t)(a.max_iter + 1) * (size_t)n;
-                        for (int c = tg; c < n; c += kGrpThreads) tr[c] = pi;
+                        for (int c = tg; c < n; c += T) tr[c] = pi;
                     }
                     if ((c0 == 0 && early) || a.max_iter == 0) {
-                        for (int w = tg; w < nw; w += kGrpThreads)
+                        for (int w = tg; w < nw; w += T)
                             a.err[s * nw + w] =
                                 (pi < 0.0f) ? ((w == nw - 1 && (n & 31)) ? ((1u << (n & 31)) - 1u) : 0xffffffffu) : 0u;
                         if (tg == 0) { a.conv[s] = (c0 == 0) ? 1 : 0; a.iters[s] = 0; }
@@ -200,10 +201,16 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
                         idle = false;
                         fresh = true;
                         prior = pi;
-                        sbits = bit0 | (bit1 << 1);
                         gcnt = c0;
-                        st0 = bit0 ^ (flipped ? (degs & 1u) : 0u);
-                        st1 = bit1 ^ (flipped ? ((degs >> 8) & 1u) : 0u);
+                        sbits = 0;
+                        stb = 0;
+#pragma unroll
+                        for (int k = 0; k < K; ++k) {
+                            const int i = tg + k * T;
+                            const uint32_t bit = (i < m) ? ((row[i >> 5] >> (i & 31)) & 1u) : 0u;
+                            sbits |= bit << k;
+                            stb |= (bit ^ (flipped ? (qc_byte(degs, k) & 1u) : 0u)) << k;
+                        }
                     }
                 }
             }
@@ -211,15 +218,15 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
         if (state == kDone) break;
 
         if (!idle) {
-            // A2 gains of the two checks (Eq. 7)
-            float g0 = 1.0f, g1 = 1.0f;
+            // A2 gains (Eq. 7)
+            float g[K];
             if (a.mode == kModeSAGMS) {
                 const float base = a.amax - (a.amax - a.amin) * ((float)gcnt * a.inv_m);
-                g0 = base * (st0 ? a.eta : 1.0f);
-                g1 = base * (st1 ? a.eta : 1.0f);
-            } else if (a.mode == kModeSMS) {
-                g0 = a.alpha;
-                g1 = a.alpha;
+#pragma unroll
+                for (int k = 0; k < K; ++k) g[k] = base * (((stb >> k) & 1u) ? a.eta : 1.0f);
+            } else {
+#pragma unroll
+                for (int k = 0; k < K; ++k) g[k] = (a.mode == kModeSMS) ? a.alpha : 1.0f;
             }
             if (fresh) {
                 // A3 on round-1 inputs: every real edge carries the prior s, padded slots +inf.
@@ -228,59 +235,61 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
                 // edge, and every real edge gets the second-minimum output (|v_j| = m1).
                 const uint32_t sgn = __float_as_uint(prior) & kSign;
                 const float ms = fabsf(prior);
-                const uint32_t deg0 = degs & 0xffu, deg1 = degs >> 8;
-                const uint32_t par0 = ((sbits & 1u) << 31) ^ ((deg0 & 1u) ? sgn : 0u);
-                const uint32_t par1 = ((sbits >> 1) << 31) ^ ((deg1 & 1u) ? sgn : 0u);
-                const float m2a = (deg0 >= 2) ? ms : inf;
-                const float m2b = (deg1 >= 2) ? ms : inf;
-                const float o2a = __uint_as_float(__float_as_uint(fminf(g0 * m2a, kMsFamClip)) | par0);
-                const float o2b = __uint_as_float(__float_as_uint(fminf(g1 * m2b, kMsFamClip)) | par1);
-                const float d0 = __uint_as_float(__float_as_uint(o2a) ^ (~__float_as_uint(prior) & kSign));
-                const float d1 = __uint_as_float(__float_as_uint(o2b) ^ (~__float_as_uint(prior) & kSign));
 #pragma unroll
-                for (int j = 0; j < DC; ++j) {
-                    Cat(j, wq[j] & 0xffffu) = d0;
-                    Cat(j, wq[j] >> 16) = d1;
+                for (int k = 0; k < K; ++k) {
+                    const uint32_t deg = qc_byte(degs, k);
+                    const uint32_t par = (((sbits >> k) & 1u) << 31) ^ ((deg & 1u) ? sgn : 0u);
+                    const float m2 = (deg >= 2) ? ms : inf;
+                    const float o2 = __uint_as_float(__float_as_uint(fminf(g[k] * m2, kMsFamClip)) | par);
+                    const float d = __uint_as_float(__float_as_uint(o2) ^ (~__float_as_uint(prior) & kSign));
+#pragma unroll
+                    for (int j = 0; j < DC; ++j) Cat(j, off[k][j]) = d;
                 }
             } else {
-                // A3 check-node update (C holds negated messages: P - L = P + D)
 #pragma unroll
-                for (int j = 0; j < DC; ++j)
-                    v[j] = add2(v[j], make_float2(Cat(j, wq[j] & 0xffffu), Cat(j, wq[j] >> 16)));
-                uint32_t par0 = (sbits & 1u) << 31, par1 = (sbits >> 1) << 31;
+                for (int p = 0; p < K / 2; ++p) {
+                    // A3 check-node update for checks 2p and 2p + 1 (C holds negated
+                    // messages: P - L = P + D)
 #pragma unroll
-                for (int j = 0; j < DC; j += 2) {
-                    par0 ^= __float_as_uint(v[j].x) ^ __float_as_uint(v[j + 1].x);
-                    par1 ^= __float_as_uint(v[j].y) ^ __float_as_uint(v[j + 1].y);
-                }
-                par0 &= kSign;
-                par1 &= kSign;
-                float m1a = inf, m2a = inf, m1b = inf, m2b = inf;
+                    for (int j = 0; j < DC; ++j)
+                        v[p][j] = add2(v[p][j], make_float2(Cat(j, off[2 * p][j]), Cat(j, off[2 * p + 1][j])));
+                    uint32_t par0 = ((sbits >> (2 * p)) & 1u) << 31, par1 = ((sbits >> (2 * p + 1)) & 1u) << 31;
 #pragma unroll
-                for (int j = 0; j < DC; j += 2) {
-                    const float a0 = fabsf(v[j].x), a1 = fabsf(v[j + 1].x);
-                    const float c0 = fabsf(v[j].y), c1 = fabsf(v[j + 1].y);
-                    const float loa = fminf(a0, a1), hia = fmaxf(a0, a1);
-                    const float lob = fminf(c0, c1), hib = fmaxf(c0, c1);
-                    m2a = fminf(fminf(m2a, hia), fmaxf(m1a, loa));
-                    m1a = fminf(m1a, loa);
-                    m2b = fminf(fminf(m2b, hib), fmaxf(m1b, lob));
-                    m1b = fminf(m1b, lob);
-                }
-                const float o1a = __uint_as_float(__float_as_uint(fminf(g0 * m1a, kMsFamClip)) | par0);
-                const float o2a = __uint_as_float(__float_as_uint(fminf(g0 * m2a, kMsFamClip)) | par0);
-                const float o1b = __uint_as_float(__float_as_uint(fminf(g1 * m1b, kMsFamClip)) | par1);
-                const float o2b = __uint_as_float(__float_as_uint(fminf(g1 * m2b, kMsFamClip)) | par1);
+                    for (int j = 0; j < DC; j += 2) {
+                        par0 ^= __float_as_uint(v[p][j].x) ^ __float_as_uint(v[p][j + 1].x);
+                        par1 ^= __float_as_uint(v[p][j].y) ^ __float_as_uint(v[p][j + 1].y);
+                    }
+                    par0 &= kSign;
+                    par1 &= kSign;
+                    // Smallest and second smallest |v|, two edges at a time:
+                    // m2 = min(m2, hi, max(m1, lo)), m1 = min(m1, lo).
+                    float m1a = inf, m2a = inf, m1b = inf, m2b = inf;
 #pragma unroll
-                for (int j = 0; j < DC; ++j) {
-                    const float ma = (fabsf(v[j].x) == m1a) ? o2a : o1a;
-                    const float mb = (fabsf(v[j].y) == m1b) ? o2b : o1b;
-                    Cat(j, wq[j] & 0xffffu) = __uint_as_float(__float_as_uint(ma) ^ (~__float_as_uint(v[j].x) & kSign));
-                    Cat(j, wq[j] >> 16) = __uint_as_float(__float_as_uint(mb) ^ (~__float_as_uint(v[j].y) & kSign));
+                    for (int j = 0; j < DC; j += 2) {
+                        const float a0 = fabsf(v[p][j].x), a1 = fabsf(v[p][j + 1].x);
+                        const float c0 = fabsf(v[p][j].y), c1 = fabsf(v[p][j + 1].y);
+                        const float loa = fminf(a0, a1), hia = fmaxf(a0, a1);
+                        const float lob = fminf(c0, c1), hib = fmaxf(c0, c1);
+                        m2a = fminf(fminf(m2a, hia), fmaxf(m1a, loa));
+                        m1a = fminf(m1a, loa);
+                        m2b = fminf(fminf(m2b, hib), fmaxf(m1b, lob));
+                        m1b = fminf(m1b, lob);
+                    }
+                    const float o1a = __uint_as_float(__float_as_uint(fminf(g[2 * p] * m1a, kMsFamClip)) | par0);
+                    const float o2a = __uint_as_float(__float_as_uint(fminf(g[2 * p] * m2a, kMsFamClip)) | par0);
+                    const float o1b = __uint_as_float(__float_as_uint(fminf(g[2 * p + 1] * m1b, kMsFamClip)) | par1);
+                    const float o2b = __uint_as_float(__float_as_uint(fminf(g[2 * p + 1] * m2b, kMsFamClip)) | par1);
+#pragma unroll
+                    for (int j = 0; j < DC; ++j) {
+                        const float ma = (fabsf(v[p][j].x) == m1a) ? o2a : o1a;
+                        const float mb = (fabsf(v[p][j].y) == m1b) ? o2b : o1b;
+                        Cat(j, off[2 * p][j]) = __uint_as_float(__float_as_uint(ma) ^ (~__float_as_uint(v[p][j].x) & kSign));
+                        Cat(j, off[2 * p + 1][j]) = __uint_as_float(__float_as_uint(mb) ^ (~__float_as_uint(v[p][j].y) & kSign));
+                    }
                 }
             }
         }
-        group_barrier(G);
+        asm volatile("bar.sync %0, %1;" ::"n"(1 + G), "n"(T) : "memory");
 
         // Claim and prefetch the group's next shot (warp 0 of the group).
         if (consumed >= 0 && tg < 32) {
@@ -290,11 +299,11 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
         }
 
         if (!idle) {
-            // A4 variable-node update: qubit pairs (2tg, 2tg + 1) and (1024 + 2tg, 1025 + 2tg)
+            // A4 variable-node update: qubit pairs (2tg + 2hT, 2tg + 2hT + 1)
             const float2 npr = make_float2(-prior, -prior);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int c = h * (NP / 2) + 2 * tg;
+            for (int h = 0; h < K; ++h) {
+                const int c = h * 2 * T + 2 * tg;
                 float2 acc = npr;
 #pragma unroll
                 for (int q = 0; q < DV; ++q)
@@ -303,53 +312,57 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
                     __ffma2_rn(acc, make_float2(-1.0f, -1.0f), make_float2(0.0f, 0.0f));
             }
         }
-        group_barrier(G);
+        asm volatile("bar.sync %0, %1;" ::"n"(1 + G), "n"(T) : "memory");
         ph ^= 1;
     }
 }
 
-template <int DC, int DV>
-__global__ void __launch_bounds__(1024, 1) qc_kernel(const DecodeArgs a, const uint32_t* __restrict__ colQ) {
-    static_assert(DC == 2 * DV && DC % 2 == 0, "slot j meets its qubit as edge j mod DV");
+// colQ: [K][DC][T] u32, byte offset 4 * col of check tg + kT in slot j (kQcPadOff for a
+// padded slot or a check past m).
+template <int DC, int DV, int K>
+__global__ void __launch_bounds__(2048 / K, 1) qc_kernel(const DecodeArgs a, const uint32_t* __restrict__ colQ) {
+    static_assert(DC == 2 * DV && DC % 2 == 0 && (K == 2 || K == 4), "shape");
+    constexpr int T = 1024 / K;
     extern __shared__ __align__(16) unsigned char smem[];
     const int t = threadIdx.x;
-    const int tg = t % kGrpThreads;
+    const int tg = t % T;
     const float inf = __uint_as_float(0x7f800000u);
-    {
-        const int4* s = reinterpret_cast<const int4*>(colQ);
-        int4* d = reinterpret_cast<int4*>(smem + qc_col_off(DV));
-        for (int k = t; k < DC * kGrpThreads * 4 / 16; k += 1024) d[k] = __ldg(s + k);
+    uint32_t off[K][DC];
+    uint32_t degs = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        uint32_t d = 0;
+#pragma unroll
+        for (int j = 0; j < DC; ++j) {
+            off[k][j] = __ldg(colQ + (k * DC + j) * T + tg);
+            d += (off[k][j] != kQcPadOff) ? 1u : 0u;
+        }
+        degs |= d << (8 * k);
     }
-    // Posteriors (sentinel +inf), messages and bookkeeping of both groups start at zero.
+    // Posteriors, messages and bookkeeping of both groups start at zero; the padding columns
+    // of the posteriors hold +inf.
     {
         float* z = reinterpret_cast<float*>(smem);
-        for (int k = t; k < (int)(2 * qc_group_bytes(DV) / 4); k += 1024) z[k] = 0.0f;
-        int* misc = reinterpret_cast<int*>(smem + qc_misc_off(DC, DV));
-        if (t < 2 * kGrpMiscPerGroup / 4) misc[t] = 0;
+        for (int k = t; k < (int)(2 * qc_group_bytes(DV) / 4); k += 2 * T) z[k] = 0.0f;
+        int* misc = reinterpret_cast<int*>(smem + qc_misc_off(DV));
+        for (int k = t; k < 2 * kQcMisc / 4; k += 2 * T) misc[k] = 0;
     }
     __syncthreads();
     if (t < 2) *reinterpret_cast<float*>(smem + qc_P_off(DV, t) + kQcPadOff) = inf;
-    // Check degrees (first-check flips for a negative prior: degree parity; the closed-form
-    // first round needs the degree itself).
-    const uint32_t* cq = reinterpret_cast<const uint32_t*>(smem + qc_col_off(DV));
-    uint32_t deg0 = 0, deg1 = 0;
+    // First residual bits under a negative prior: a check's degree parity.
+    uint32_t* flipw = reinterpret_cast<uint32_t*>(smem + qc_misc_off(DV) + 2 * kQcMisc);
+    if (t < T) {
 #pragma unroll
-    for (int j = 0; j < DC; ++j) {
-        const uint32_t w = cq[j * kGrpThreads + tg];
-        deg0 += ((w & 0xffffu) != kQcPadOff) ? 1u : 0u;
-        deg1 += ((w >> 16) != kQcPadOff) ? 1u : 0u;
-    }
-    uint32_t* flipw = reinterpret_cast<uint32_t*>(smem + qc_misc_off(DC, DV) + 2 * kGrpMiscPerGroup);
-    if (t < kGrpThreads) {
-        const uint32_t w0 = __ballot_sync(0xffffffffu, deg0 & 1u);
-        const uint32_t w1 = __ballot_sync(0xffffffffu, deg1 & 1u);
-        if ((t & 31) == 0) { flipw[t >> 5] = w0; flipw[(t + kGrpThreads) >> 5] = w1; }
+        for (int k = 0; k < K; ++k) {
+            const uint32_t w = __ballot_sync(0xffffffffu, qc_byte(degs, k) & 1u);
+            if ((t & 31) == 0) flipw[(t + k * T) >> 5] = w;
+        }
     }
     __syncthreads();
-    if (t < kGrpThreads)
-        qc_group<DC, DV, 0>(a, smem, tg, deg0 | (deg1 << 8));
+    if (t < T)
+        qc_group<DC, DV, K, 0>(a, smem, tg, off, degs);
     else
-        qc_group<DC, DV, 1>(a, smem, tg, deg0 | (deg1 << 8));
+        qc_group<DC, DV, K, 1>(a, smem, tg, off, degs);
 }
 
 }  // namespace sagms

@@ -77,16 +77,29 @@ constexpr int kGroupDC = 10, kGroupDV = 5;
 using GroupFn = void (*)(const DecodeArgs, const GroupLayout);
 GroupFn group_kernel_fn() { return group_kernel<kGroupDC, kGroupDV>; }
 
-// Column-indexed two-group kernels (decode_qc.cuh): (DC, DV) with DC = 2 DV.
+// Column-indexed two-group kernels (decode_qc.cuh): (DC, DV) with DC = 2 DV, four checks per
+// thread (with two checks per thread, 1024-thread CTAs, it measured 5-15% slower).
 constexpr int kQcDV[] = {3, 4, 5};
 constexpr int kNumQc = sizeof(kQcDV) / sizeof(kQcDV[0]);
+constexpr int kQcK = 4;
 using QcFn = void (*)(const DecodeArgs, const uint32_t*);
 QcFn qc_kernel_for(int v) {
     switch (v) {
-        case 0: return qc_kernel<6, 3>;
-        case 1: return qc_kernel<8, 4>;
-        default: return qc_kernel<10, 5>;
+        case 0: return qc_kernel<6, 3, kQcK>;
+        case 1: return qc_kernel<8, 4, kQcK>;
+        default: return qc_kernel<10, 5, kQcK>;
     }
+}
+
+// colQ layout of the column-indexed kernel: [K][DC][1024 / K], byte offset 4 * col of check
+// tg + k * (1024 / K) in slot j (kQcPadOff for padding).
+std::vector<uint32_t> qc_layout(int m, const int32_t* row_ptr, const int32_t* col_idx, int DC) {
+    constexpr int K = kQcK, T = 1024 / kQcK;
+    std::vector<uint32_t> out((size_t)K * DC * T, kQcPadOff);
+    for (int i = 0; i < m; ++i)
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+            out[((size_t)(i / T) * DC + (e - row_ptr[i])) * T + (i % T)] = (uint32_t)col_idx[e] * 4u;
+    return out;
 }
 
 constexpr int kMaxDevices = 64;
@@ -184,7 +197,7 @@ struct sagms_code {
     uint16_t* d_colG;      // [2][kGroupDC][1024] byte offsets of P_g entries
     uint32_t* d_vneG;      // [2][kGroupDV][2048] byte offsets of C_g entries
     int qc_variant;        // -1: no column-indexed kernel for this code
-    uint32_t* d_colQ;      // [DC][512] packed byte offsets 4 * col of checks t and t + 512
+    uint32_t* d_colQ;      // qc_layout
     // Launch plan chosen by sagms_autotune (0 = defaults), packed so decodes on other
     // threads read it atomically: bits 0-2 kernel (0 auto, 1 one-shot-per-CTA, 2 two-slot,
     // 3 two-group, 4 two-group with column-indexed messages),
@@ -364,17 +377,7 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
         }
     }
     std::vector<uint32_t> colQ;
-    if (qv >= 0) {
-        const int DCq = 2 * kQcDV[qv];
-        colQ.assign((size_t)DCq * kGrpThreads, 0u);
-        for (int i = 0; i < kGrpChecks; ++i) {
-            const int d = (i < m) ? row_ptr[i + 1] - row_ptr[i] : 0;
-            for (int j = 0; j < DCq; ++j) {
-                const uint32_t o = (j < d) ? (uint32_t)col_idx[row_ptr[i] + j] * 4u : kQcPadOff;
-                colQ[(size_t)j * kGrpThreads + (i % kGrpThreads)] |= (i < kGrpThreads) ? o : (o << 16);
-            }
-        }
-    }
+    if (qv >= 0) colQ = qc_layout(m, row_ptr, col_idx, 2 * kQcDV[qv]);
 
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
@@ -501,7 +504,7 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     const bool msfam_fast = !bp && !(p->flags & SAGMS_FLAG_GENERIC_KERNEL);
     const bool use_qc = msfam_fast && code->qc_variant >= 0 && !per_qubit && (plan.kernel == 0 || plan.kernel == 4);
     const bool use_groups = !use_qc && msfam_fast && code->groups && !per_qubit &&
-                            (plan.kernel == 0 || plan.kernel == 3 || plan.kernel == 4);
+                            (plan.kernel == 0 || plan.kernel >= 3);
     const bool use_slots = !use_qc && !use_groups && msfam_fast && code->slot_variant >= 0 && plan.kernel != 1;
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
@@ -517,8 +520,8 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     if (use_qc) {
         const int DVq = kQcDV[code->qc_variant];
         fn = reinterpret_cast<const void*>(qc_kernel_for(code->qc_variant));
-        smem = qc_smem_bytes(2 * DVq, DVq);
-        threads = 2 * kGrpThreads;
+        smem = qc_smem_bytes(DVq);
+        threads = 2048 / kQcK;
         units = (shots + 1) / 2;   // two shots in flight per CTA
     } else if (use_groups) {
         fn = reinterpret_cast<const void*>(group_kernel_fn());

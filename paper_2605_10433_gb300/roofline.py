@@ -40,6 +40,26 @@ def alu_peak_ops(sms: int, sm_mhz: float) -> float:
     return sms * THREAD_OPS_PER_SM_CLK * sm_mhz * 1e6
 
 
+SMEM_BYTES_PER_SM_CLK = 128  # shared-memory pipe: one 128-byte wavefront per clock per SM
+
+
+def smem_bytes(iters, edges: int, n: int) -> float:
+    """On-chip bytes of the flooding schedule with messages held in shared memory, summed
+    over shots.  A shot with r >= 1 iterations reads P_j for each of its r residual checks
+    (4E per check; rounds 2..r take their check-node inputs from the same read), reads
+    L_old (4E) in rounds 2..r (round 1 starts from zero messages), writes L_new (4E) and
+    reads it back in the variable-node sum (4E) in every round, and writes P (4n) in every
+    round: 16E r - 4E + 4n r bytes.  A shot stopped at its first check (r = 0) moves none."""
+    r = np.asarray(iters, dtype=np.int64)
+    r = r[r > 0]
+    return float((16 * edges + 4 * n) * r.sum() - 4 * edges * r.size)
+
+
+def smem_peak_bytes(sms: int, sm_mhz: float) -> float:
+    """Shared-memory bandwidth of the whole GPU: SMs x 128 B x clock."""
+    return sms * SMEM_BYTES_PER_SM_CLK * sm_mhz * 1e6
+
+
 def hbm_bytes_per_shot(m: int, n: int) -> int:
     """Syndrome in, prior in, packed estimate + flag + count out."""
     return ((m + 31) // 32) * 4 + 4 + ((n + 31) // 32) * 4 + 1 + 4

@@ -131,3 +131,10 @@ def test_op_count_model_matches_eq15_and_table1():
     # m (2 d_c + 3) + n (2 d_v + 1) + E + m at d_c = 10, d_v = 5
     assert roofline.ops_per_iteration("sagms", c.row_ptr, c.col_idx, c.n) == 1023 * 23 + 2046 * 11 + 10230 + 1023
     assert roofline.hbm_bytes_per_shot(c.m, c.n) == 128 + 4 + 256 + 1 + 4   # 393 B
+    # on-chip bytes: r = 1 moves 12E + 4n (no old-message read), each further round 16E + 4n,
+    # a shot that stops at its first check moves nothing
+    E, n = c.nnz, c.n
+    assert roofline.smem_bytes([0], E, n) == 0
+    assert roofline.smem_bytes([1], E, n) == 12 * E + 4 * n
+    assert roofline.smem_bytes([1, 3, 0], E, n) == (12 * E + 4 * n) + (12 * E + 4 * n + 2 * (16 * E + 4 * n))
+    assert roofline.smem_peak_bytes(152, 2070) == 152 * 128 * 2070e6

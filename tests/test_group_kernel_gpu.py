@@ -1,4 +1,4 @@
-"""The two-group kernels (two 512-thread groups per CTA, one shot each; the general layout
+"""The two-group kernels (two independent shot groups per CTA, one shot each; the general layout
 and the column-indexed one for codes whose edges line up slot by slot) against the
 one-shot-per-CTA kernel and the two-slot kernel, on the codes they cover (more than 512 and
 at most 1024 checks, at most 2048 qubits).
@@ -128,7 +128,7 @@ def test_group_kernel_edge_inputs(group_codes, key, kernel):
 
 
 @pytest.mark.parametrize("key,kernel", [("ragged", KERNEL_GROUPS), ("gb-truncated", KERNEL_QC),
-                                        ((1023, 5), KERNEL_QC)])
+                                        ((1023, 5), KERNEL_QC), ((1023, 5))])
 def test_group_kernel_oracle_parity(group_codes, key, kernel):
     """The group kernels directly against the FP64 oracle (same acceptance as the other
     kernels: exact agreement except for shots traced to near-ties or ill-conditioning)."""
