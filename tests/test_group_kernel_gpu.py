@@ -128,7 +128,7 @@ def test_group_kernel_edge_inputs(group_codes, key, kernel):
 
 
 @pytest.mark.parametrize("key,kernel", [("ragged", KERNEL_GROUPS), ("gb-truncated", KERNEL_QC),
-                                        ((1023, 5), KERNEL_QC), ((1023, 5))])
+                                        ((1023, 5), KERNEL_QC)])
 def test_group_kernel_oracle_parity(group_codes, key, kernel):
     """The group kernels directly against the FP64 oracle (same acceptance as the other
     kernels: exact agreement except for shots traced to near-ties or ill-conditioning)."""
