@@ -18,8 +18,10 @@
  *     entry point says so.
  *   - Packed bit layout: bit k of a pattern is bit (k % 32) of uint32 word k / 32.
  *     A syndrome occupies ceil(m/32) words per shot, an error estimate ceil(n/32).
- *   - A code handle is immutable after sagms_load_code and may be used from several
- *     host threads and streams at once.
+ *   - A code handle may be used from several host threads and streams at once.  Its
+ *     decoding behaviour is fixed by sagms_load_code; sagms_set_plan (atomic) and
+ *     sagms_mc_set_logicals (not concurrently with a Monte Carlo call on the handle) are
+ *     the only mutations.
  */
 #ifndef SAGMS_H
 #define SAGMS_H
@@ -283,6 +285,80 @@ int sagms_server_replay(sagms_server* server, int32_t n, const int32_t* code_ids
 /* Eq. 9: alpha*(L0, d_c) = 2 atanh(tanh(L0/2)^(d_c - 1)) / L0, the SMS scale matching one
  * BP CN update under uniform inputs (Remark 1).  Returns NaN for L0 <= 0 or d_c < 2. */
 double sagms_alpha_star(double L0, int32_t dc);
+
+/*
+ * ---- Fused Monte Carlo frame-error estimation (not part of the decoder itself) ----
+ *
+ * The simulation protocol of Sec. V (setup): for one noise level, draw frames (iid Z flips
+ * of each qubit with probability q, the Z part of the memoryless channel of Sec. II), form
+ * their syndromes s = H e, decode them with Algorithm 1, and count frame failures until a
+ * target number of failures or a maximum number of frames.  Sampling, syndrome formation,
+ * decoding and the logical check all run on the GPU; only the counters return to the host.
+ *
+ * A frame fails when the decoder stops without a zero residual syndrome (the failure exit of
+ * Algorithm 1) or when it converges but e XOR e_hat is a nontrivial logical operator (not in
+ * the row space of H_Z).  Both kinds are counted separately.
+ */
+typedef struct {
+    int64_t shots;          /* frames decoded */
+    int64_t failures;       /* not_converged + logical */
+    int64_t not_converged;  /* Algorithm 1 returned its failure exit */
+    int64_t logical;        /* converged, but e XOR e_hat is a nontrivial logical operator */
+    int64_t iters_sum;      /* sum of the decoder's iteration counts */
+} sagms_mc_counts;
+
+/*
+ * X-type logical operators of a CSS code: a basis of ker(H_Z) modulo the row space of H_X,
+ * k = n - rank(H_X) - rank(H_Z) vectors.  H_X is the decoder's matrix (mx x n), H_Z the
+ * other stabilizer matrix (mz x n), both CSR over GF(2).  A Z-type residual r with
+ * H_X r = 0 is a stabilizer exactly when x . r = 0 (mod 2) for every returned x.  Host-only
+ * (no GPU needed); writes min(k, max_k) packed vectors [k][ceil(n/32)] to `logicals` (may
+ * be NULL with max_k = 0 to query k) and k to *k.  Errors: SAGMS_ERR_ARG, SAGMS_ERR_CSR for
+ * malformed matrices, SAGMS_ERR_PARAM when H_X H_Z^T != 0 (not a CSS pair).
+ */
+int sagms_x_logicals(int32_t n, int32_t mx, const int32_t* hx_row_ptr, const int32_t* hx_col_idx,
+                     int32_t mz, const int32_t* hz_row_ptr, const int32_t* hz_col_idx, int32_t max_k,
+                     uint32_t* logicals, int32_t* k);
+
+/* Attach k >= 0 logical operators (host array [k][ceil(n/32)], copied) to a code for the
+ * logical check; k = 0 counts only decoder failures.  Replaces earlier ones. */
+int sagms_mc_set_logicals(sagms_code* code, int32_t k, const uint32_t* logicals);
+
+/*
+ * Draw frames shot0 .. shot0 + shots - 1 of the generator keyed by `seed`: iid flips with
+ * probability q in [0, 1), from Philox4x32-10 (Salmon et al., SC'11) with counter
+ * (draw / 4, shot low word, shot high word, 0x53414721) and key (seed low, seed high),
+ * each uniform u32 draw giving a run of unflipped qubits by geometric-gap lookup in
+ * T[g] = floor((1 - q)^g 2^32) (powers by repeated IEEE double multiplication; T[0] =
+ * 2^32 - 1; the run is the largest g <= n with u < T[g]).  This is, bit for bit, the
+ * generator the tests use to build inputs.  Writes d_err [shots][ceil(n/32)],
+ * d_syn [shots][ceil(m/32)] = H e, and d_L0 [shots] = L0 (the decoder's prior for the
+ * level; any of the three may be NULL).  Asynchronous on `stream`.
+ */
+int sagms_mc_sample(const sagms_code* code, uint64_t seed, double q, float L0, int64_t shot0, int64_t shots,
+                    uint32_t* d_err, uint32_t* d_syn, float* d_L0, void* stream);
+
+/*
+ * Logical check of decoded frames against their true errors (device arrays as produced by
+ * sagms_mc_sample and sagms_decode): per frame a flag (0 success, 1 not converged,
+ * 2 converged to a nontrivial logical) in d_fail (may be NULL), and the counts added to
+ * *d_counts (device memory; shots included).  Needs attached logicals.  Asynchronous.
+ */
+int sagms_mc_check(const sagms_code* code, int64_t shots, const uint32_t* d_err, const uint32_t* d_err_hat,
+                   const uint8_t* d_conv, const int32_t* d_iters, uint8_t* d_fail, sagms_mc_counts* d_counts,
+                   void* stream);
+
+/*
+ * The protocol for one noise level: batches of `batch` frames through sample -> decode ->
+ * check until counts->failures >= target_failures or counts->shots >= max_shots.  counts
+ * is in/out (host): frames already counted are skipped, so the next frame index is
+ * counts->shots and repeated calls continue the same sequence.  The stop is checked between
+ * batches, so the last batch can overshoot the failure target.  Synchronous; device
+ * buffers come from the stream-ordered pool on a library stream and are released before
+ * returning.  Needs attached logicals.
+ */
+int sagms_mc_run(const sagms_code* code, const sagms_params* params, uint64_t seed, double q, float L0,
+                 int64_t target_failures, int64_t max_shots, int64_t batch, sagms_mc_counts* counts);
 
 /* Message of the last failure on the calling thread ("" if none). */
 const char* sagms_last_error_string(void);

@@ -55,6 +55,10 @@ class DeviceCode:
     def nw(self):
         return (self.n + 31) // 32
 
+    def set_logicals(self, logicals):
+        """Attach logical operators (uint32 [k][ceil(n/32)]) for the Monte Carlo check."""
+        self._native.sagms_mc_set_logicals(self.handle, logicals)
+
     def close(self):
         if getattr(self, "handle", None):
             self._native.sagms_free_code(self.handle)
@@ -298,3 +302,63 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# --------------------------------------------------------------------------- Monte Carlo
+def x_logicals(code):
+    """X-logical operators of a CSS code object with ``hz_rows`` (H_Z rows as Python-int
+    bitsets, as the GB generator provides): uint32 [k][ceil(n/32)] (computed in the library)."""
+    import numpy as np
+    from . import _native
+    rows = [[j for j in range(code.n) if (r >> j) & 1] for r in code.hz_rows]
+    hz_rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    hz_ci = np.asarray([j for r in rows for j in r], dtype=np.int32)
+    return _native.sagms_x_logicals(code.n, code.row_ptr, code.col_idx, hz_rp, hz_ci)
+
+
+def llr(q: float) -> float:
+    """The channel prior of a flip probability: ln((1 - q) / q) (Sec. II), for 0 < q < 1."""
+    import math
+    if not 0.0 < q < 1.0:
+        raise ValueError(f"no finite prior for flip probability {q}: pass L0 explicitly")
+    return math.log((1.0 - q) / q)
+
+
+def mc_sample(code: DeviceCode, seed: int, q: float, shot0: int, shots: int, L0: float | None = None, stream=None):
+    """Frames shot0 .. shot0 + shots - 1 of the on-device generator: (err int32 [shots, nw],
+    syn int32 [shots, mw], L0 float32 [shots]) CUDA tensors.  Asynchronous on ``stream``."""
+    import torch
+    from . import _native
+    err = torch.empty((shots, code.nw), dtype=torch.int32, device="cuda")
+    syn = torch.empty((shots, code.mw), dtype=torch.int32, device="cuda")
+    l0 = torch.empty((shots,), dtype=torch.float32, device="cuda")
+    _native.sagms_mc_sample(code.handle, seed, q, llr(q) if L0 is None else L0, shot0, shots, err.data_ptr(),
+                            syn.data_ptr(), l0.data_ptr(), _stream_ptr(stream))
+    return err, syn, l0
+
+
+def mc_check(code: DeviceCode, err, err_hat, conv, iters, stream=None):
+    """Logical check of decoded frames (logicals attached): (fail uint8 [shots] with 0 success,
+    1 not converged, 2 logical error; counts dict).  Synchronises ``stream``."""
+    import torch
+    from . import _native
+    shots = err.shape[0]
+    fail = torch.empty((shots,), dtype=torch.uint8, device="cuda")
+    counts = torch.zeros((5,), dtype=torch.int64, device="cuda")
+    _native.sagms_mc_check(code.handle, shots, err.data_ptr(), err_hat.data_ptr(), conv.data_ptr(), iters.data_ptr(),
+                           fail.data_ptr(), counts.data_ptr(), _stream_ptr(stream))
+    c = counts.cpu().tolist()
+    return fail, dict(zip(("shots", "failures", "not_converged", "logical", "iters_sum"), c))
+
+
+def mc_run(code: DeviceCode, params: Params, seed: int, q: float, L0: float | None = None,
+           target_failures: int = 500, max_shots: int = 20_000_000, batch: int = 1 << 22, counts=None):
+    """The frame-error protocol of Sec. V (setup) for one noise level, entirely on the GPU:
+    sample, decode and check batches until ``target_failures`` failures or ``max_shots``
+    frames.  ``counts`` (a dict from an earlier call) continues the same frame sequence.
+    Returns the counts dict."""
+    from . import _native
+    c = _native.sagms_mc_counts(**(counts or {}))
+    _native.sagms_mc_run(code.handle, params.to_c(), seed, q, llr(q) if L0 is None else L0, target_failures,
+                         max_shots, batch, c)
+    return c.as_dict()

@@ -42,6 +42,14 @@ class sagms_job(ctypes.Structure):
                 ("d_conv", ctypes.c_void_p), ("d_iters", ctypes.c_void_p)]
 
 
+class sagms_mc_counts(ctypes.Structure):
+    _fields_ = [("shots", ctypes.c_int64), ("failures", ctypes.c_int64), ("not_converged", ctypes.c_int64),
+                ("logical", ctypes.c_int64), ("iters_sum", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
 def _load_library():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libsagms.so is not built ({LIB_PATH}); run __graft_entry__.build() "
@@ -78,6 +86,13 @@ def _load_library():
         "sagms_alpha_star": (ctypes.c_double, [ctypes.c_double, i32]),
         "sagms_last_error_string": (ctypes.c_char_p, []),
         "sagms_version": (ctypes.c_char_p, []),
+        "sagms_x_logicals": (ctypes.c_int, [i32, i32, P(i32), P(i32), i32, P(i32), P(i32), i32, vp, P(i32)]),
+        "sagms_mc_set_logicals": (ctypes.c_int, [vp, i32, vp]),
+        "sagms_mc_sample": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_double, ctypes.c_float, i64, i64,
+                                           vp, vp, vp, vp]),
+        "sagms_mc_check": (ctypes.c_int, [vp, i64, vp, vp, vp, vp, vp, vp, vp]),
+        "sagms_mc_run": (ctypes.c_int, [vp, P(sagms_params), ctypes.c_uint64, ctypes.c_double, ctypes.c_float,
+                                        i64, i64, i64, P(sagms_mc_counts)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -188,3 +203,44 @@ def sagms_version() -> str:
 
 def sagms_last_error_string() -> str:
     return _lib.sagms_last_error_string().decode()
+
+
+def _i32(a):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def sagms_x_logicals(n, hx_row_ptr, hx_col_idx, hz_row_ptr, hz_col_idx):
+    """Basis of X-logical operators (ker H_Z modulo rowspace H_X) as uint32 [k][ceil(n/32)]."""
+    import numpy as np
+    keep = [_i32(a) for a in (hx_row_ptr, hx_col_idx, hz_row_ptr, hz_col_idx)]
+    (hxr, hxr_p), (hxc, hxc_p), (hzr, hzr_p), (hzc, hzc_p) = keep
+    k = ctypes.c_int32(0)
+    _check(_lib.sagms_x_logicals(int(n), len(hxr) - 1, hxr_p, hxc_p, len(hzr) - 1, hzr_p, hzc_p, 0, None,
+                                 ctypes.byref(k)))
+    out = np.zeros((k.value, (int(n) + 31) // 32), dtype=np.uint32)
+    _check(_lib.sagms_x_logicals(int(n), len(hxr) - 1, hxr_p, hxc_p, len(hzr) - 1, hzr_p, hzc_p, k.value,
+                                 out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(k)))
+    return out
+
+
+def sagms_mc_set_logicals(handle, logicals):
+    import numpy as np
+    L = np.ascontiguousarray(logicals, dtype=np.uint32)
+    _check(_lib.sagms_mc_set_logicals(handle, L.shape[0], L.ctypes.data_as(ctypes.c_void_p) if L.size else None))
+
+
+def sagms_mc_sample(handle, seed, q, L0, shot0, shots, err_ptr, syn_ptr, L0_ptr, stream_ptr):
+    _check(_lib.sagms_mc_sample(handle, int(seed) & 0xFFFFFFFFFFFFFFFF, float(q), float(L0), int(shot0), int(shots),
+                                err_ptr, syn_ptr, L0_ptr, stream_ptr))
+
+
+def sagms_mc_check(handle, shots, err_ptr, ehat_ptr, conv_ptr, iters_ptr, fail_ptr, counts_ptr, stream_ptr):
+    _check(_lib.sagms_mc_check(handle, int(shots), err_ptr, ehat_ptr, conv_ptr, iters_ptr, fail_ptr, counts_ptr,
+                               stream_ptr))
+
+
+def sagms_mc_run(handle, params, seed, q, L0, target_failures, max_shots, batch, counts):
+    _check(_lib.sagms_mc_run(handle, ctypes.byref(params), int(seed) & 0xFFFFFFFFFFFFFFFF, float(q), float(L0),
+                             int(target_failures), int(max_shots), int(batch), ctypes.byref(counts)))

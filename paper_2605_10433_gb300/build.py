@@ -13,7 +13,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libsagms.so")
-SOURCES = [os.path.join(HERE, "csrc", "sagms.cu"), os.path.join(HERE, "csrc", "server.cu")]
+SOURCES = [os.path.join(HERE, "csrc", f) for f in ("sagms.cu", "server.cu", "mc.cu")]
 DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in os.listdir(os.path.join(HERE, "csrc"))] + \
     [os.path.join(ROOT, "include", "sagms.h")]
 

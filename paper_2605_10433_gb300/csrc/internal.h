@@ -9,7 +9,8 @@
 
 namespace sagms_internal {
 
-// How a decode is launched.  kernel: 0 automatic, 1 one shot per CTA, 2 two-slot;
+// How a decode is launched.  kernel: 0 automatic, 1 one shot per CTA, 2 two-slot, 3 two-group,
+// 4 two-group with column-indexed messages;
 // ctas_per_sm: 0 = occupancy limit; chunk_lg: log2 shots per claimed chunk, 0 = automatic;
 // max_grid: cap on the number of CTAs, 0 = none (a small grid keeps a launch from holding
 // every SM, so concurrent launches share the GPU CTA by CTA).
@@ -25,6 +26,17 @@ struct Plan {
 int launch(const sagms_code* code, const sagms_params* params, int64_t shots, const uint32_t* d_syn,
            const float* d_L0, uint32_t* d_err, uint8_t* d_conv, int32_t* d_iters, cudaStream_t stream,
            const Plan* plan);
+
+// What the Monte Carlo engine reads of a loaded code.
+struct CodeView {
+    int m, n, dv_max, device;
+    const uint16_t* d_qchk;     // [dv_max][n]: checks of each qubit (0xFFFF past its degree)
+    int k_logicals;             // -1: none attached
+    const uint32_t* d_logicals; // [k][ceil(n/32)]
+};
+CodeView code_view(const sagms_code* code);
+// Attach logical operators (device copy owned by the code handle).
+int attach_logicals(sagms_code* code, int k, const uint32_t* h_logicals);
 
 // Record `msg` as the calling thread's last error and return `code`.
 int set_error(int code, const char* msg);

@@ -198,6 +198,9 @@ struct sagms_code {
     uint32_t* d_vneG;      // [2][kGroupDV][2048] byte offsets of C_g entries
     int qc_variant;        // -1: no column-indexed kernel for this code
     uint32_t* d_colQ;      // qc_layout
+    uint16_t* d_qchk;      // [dv_max][n] checks of each qubit, 0xFFFF padding (Monte Carlo sampler)
+    int k_logicals;        // logical operators attached for the Monte Carlo check (-1: none)
+    uint32_t* d_logicals;  // [k][ceil(n/32)]
     // Launch plan chosen by sagms_autotune (0 = defaults), packed so decodes on other
     // threads read it atomically: bits 0-2 kernel (0 auto, 1 one-shot-per-CTA, 2 two-slot,
     // 3 two-group, 4 two-group with column-indexed messages),
@@ -379,11 +382,19 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
     std::vector<uint32_t> colQ;
     if (qv >= 0) colQ = qc_layout(m, row_ptr, col_idx, 2 * kQcDV[qv]);
 
+    // Checks of each qubit, for syndrome formation in the Monte Carlo sampler.
+    std::vector<uint16_t> qchk((size_t)dv_max * n, (uint16_t)0xFFFFu);
+    for (int c = 0; c < n; ++c)
+        for (size_t q = 0; q < vedges[c].size(); ++q) qchk[q * n + c] = (uint16_t)vedges[c][q].second;
+
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
     sagms_code* code = new sagms_code();
     code->qc_variant = qv;
+    code->d_qchk = nullptr;
+    code->k_logicals = -1;
+    code->d_logicals = nullptr;
     code->d_colQ = nullptr;
     code->slot_variant = sv;
     code->d_colB = nullptr;
@@ -426,7 +437,12 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
         ce = cudaMalloc(&code->d_colQ, colQ.size() * sizeof(uint32_t));
         if (ce == cudaSuccess) ce = cudaMemcpy(code->d_colQ, colQ.data(), colQ.size() * 4, cudaMemcpyHostToDevice);
     }
+    if (ce == cudaSuccess) {
+        ce = cudaMalloc(&code->d_qchk, qchk.size() * sizeof(uint16_t));
+        if (ce == cudaSuccess) ce = cudaMemcpy(code->d_qchk, qchk.data(), qchk.size() * 2, cudaMemcpyHostToDevice);
+    }
     if (ce != cudaSuccess) {
+        cudaFree(code->d_qchk);
         cudaFree(code->d_colT);
         cudaFree(code->d_vneT);
         cudaFree(code->d_colB);
@@ -453,6 +469,8 @@ void sagms_free_code(sagms_code* code) {
     cudaFree(code->d_colG);
     cudaFree(code->d_vneG);
     cudaFree(code->d_colQ);
+    cudaFree(code->d_qchk);
+    cudaFree(code->d_logicals);
     if (prev >= 0 && prev != code->device) cudaSetDevice(prev);
     delete code;
 }
@@ -606,6 +624,27 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
 }  // namespace
 
 namespace sagms_internal {
+
+CodeView code_view(const sagms_code* code) {
+    return CodeView{code->m, code->n, code->dv_max, code->device, code->d_qchk, code->k_logicals, code->d_logicals};
+}
+
+int attach_logicals(sagms_code* code, int k, const uint32_t* h_logicals) {
+    const size_t words = (size_t)k * ((code->n + 31) / 32);
+    uint32_t* d = nullptr;
+    if (words > 0) {
+        cudaError_t ce = cudaMalloc(&d, words * 4);
+        if (ce == cudaSuccess) ce = cudaMemcpy(d, h_logicals, words * 4, cudaMemcpyHostToDevice);
+        if (ce != cudaSuccess) {
+            cudaFree(d);
+            return cuda_fail(ce, "logical operators upload");
+        }
+    }
+    cudaFree(code->d_logicals);
+    code->d_logicals = d;
+    code->k_logicals = k;
+    return SAGMS_OK;
+}
 
 int launch(const sagms_code* code, const sagms_params* params, int64_t shots, const uint32_t* d_syn,
            const float* d_L0, uint32_t* d_err, uint8_t* d_conv, int32_t* d_iters, cudaStream_t stream,

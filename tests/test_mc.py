@@ -1,0 +1,207 @@
+"""Fused Monte Carlo engine: the logical basis (CPU), the on-device frame sampler against the
+input generator (bit for bit), and the sample -> decode -> check pipeline against its parts,
+the FP64 oracle and the rank test of the logical condition."""
+import numpy as np
+import pytest
+
+import paper_2605_10433_gb300 as S
+from paper_2605_10433_gb300 import _native
+from paper_2605_10433_gb300 import inputs as I
+from paper_2605_10433_gb300.stats import logical_ok
+
+
+def _csr(rows, n):
+    rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    ci = np.asarray([j for r in rows for j in r], dtype=np.int32)
+    return rp, ci
+
+
+def _bits(vec_words, n):
+    return np.unpackbits(np.asarray(vec_words, dtype=np.uint32).view(np.uint8), bitorder="little")[:n]
+
+
+def _rank(rows_bits):
+    pivots = {}
+    rank = 0
+    for r in rows_bits:
+        x = int("".join("1" if b else "0" for b in reversed(r.tolist())), 2) if len(r) else 0
+        while x:
+            top = x.bit_length() - 1
+            if top in pivots:
+                x ^= pivots[top]
+            else:
+                pivots[top] = x
+                rank += 1
+                break
+    return rank
+
+
+def _dense(rp, ci, n):
+    H = np.zeros((len(rp) - 1, n), dtype=np.uint8)
+    for i in range(len(rp) - 1):
+        H[i, ci[rp[i]:rp[i + 1]]] = 1
+    return H
+
+
+# ----------------------------------------------------------------------------- CPU: logicals
+def test_steane_code_has_one_logical_anticommuting_with_all_ones():
+    """[[7,1,3]]: H_X = H_Z = the Hamming(7,4) checks; k = 1 and the X-logical has odd overlap
+    with the all-ones Z-logical (they must anticommute)."""
+    ham = [[3, 4, 5, 6], [1, 2, 5, 6], [0, 2, 4, 6]]
+    rp, ci = _csr(ham, 7)
+    L = _native.sagms_x_logicals(7, rp, ci, rp, ci)
+    assert L.shape == (1, 1)
+    x = _bits(L[0], 7)
+    assert x.sum() % 2 == 1
+    assert not (_dense(rp, ci, 7) @ x % 2).any()
+
+
+@pytest.mark.parametrize("lw", [(63, 3), (127, 4), (255, 5)])
+def test_gb_logicals_span_kernel_modulo_stabilizers(lw):
+    c = I.gb_code(*lw)
+    L = S.x_logicals(c)
+    n = c.n
+    hz_rows = [[j for j in range(n) if (r >> j) & 1] for r in c.hz_rows]
+    hz_rp, hz_ci = _csr(hz_rows, n)
+    HX = _dense(c.row_ptr, c.col_idx, n)
+    HZ = _dense(hz_rp, hz_ci, n)
+    rx, rz = _rank(list(HX)), _rank(list(HZ))
+    assert L.shape[0] == n - rx - rz == c.k
+    X = np.array([_bits(v, n) for v in L])
+    assert not (HZ.astype(np.int64) @ X.T % 2).any()          # every logical is in ker H_Z
+    assert _rank(list(HX) + list(X)) == rx + L.shape[0]       # independent modulo rowspace H_X
+
+
+def test_logicals_reject_non_css_and_bad_csr():
+    rp, ci = _csr([[0, 1]], 3)
+    rz, cz = _csr([[1, 2]], 3)   # overlap 1: H_X H_Z^T = 1
+    with pytest.raises(_native.SagmsError, match="ERR_PARAM"):
+        _native.sagms_x_logicals(3, rp, ci, rz, cz)
+    bad = np.array([0, 2], dtype=np.int32)
+    with pytest.raises(_native.SagmsError, match="ERR_CSR"):
+        _native.sagms_x_logicals(3, bad, np.array([0, 5], dtype=np.int32), rz, cz)
+
+
+# ----------------------------------------------------------------------------- GPU
+gpu = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@gpu
+@pytest.mark.parametrize("lw,q,seed,shot0", [((63, 3), 0.05, 7, 0), ((63, 3), 0.0, 7, 0),
+                                             ((255, 5), 0.3, 11, 123457), ((1023, 5), 0.01, 2**40 + 3, 2**33 + 5),
+                                             ((1023, 5), 0.0005, 99, 17)])
+def test_sampler_matches_input_generator(dev, lw, q, seed, shot0):
+    c = I.gb_code(*lw)
+    dc = S.DeviceCode.from_code(c)
+    shots = 3001
+    err, syn, L0 = S.mc_sample(dc, seed, q, shot0, shots, L0=None if q > 0 else 3.0)
+    e_ref, s_ref = I.sample(c, q, shots, seed=seed, shot0=shot0)
+    assert np.array_equal(err.cpu().numpy().view(np.uint32), e_ref)
+    assert np.array_equal(syn.cpu().numpy().view(np.uint32), s_ref)
+    if q > 0:
+        assert np.allclose(L0.cpu().numpy(), np.float32(np.log((1 - q) / q)))
+
+
+@gpu
+def test_sampler_on_irregular_code(dev):
+    c = I.tree_code(60, 3, max_deg=5, deg1_prob=0.3)
+    dc = S.DeviceCode.from_code(c)
+    err, syn, _ = S.mc_sample(dc, 5, 0.1, 0, 500)
+    e_ref, s_ref = I.sample(c, 0.1, 500, seed=5)
+    assert np.array_equal(err.cpu().numpy().view(np.uint32), e_ref)
+    assert np.array_equal(syn.cpu().numpy().view(np.uint32), s_ref)
+
+
+def _pipeline(dc, params, seed, q, shots):
+    err, syn, L0 = S.mc_sample(dc, seed, q, 0, shots)
+    ehat, conv, iters = S.decode(dc, syn, L0, params)
+    fail, counts = S.mc_check(dc, err, ehat, conv, iters)
+    return err, syn, ehat, conv, iters, fail, counts
+
+
+def _steane():
+    """[[7,1,3]] with H_X = H_Z = the Hamming(7,4) checks: distance 3, so weight-2 errors
+    often decode to a logical error."""
+    ham = [[3, 4, 5, 6], [1, 2, 5, 6], [0, 2, 4, 6]]
+    rp, ci = _csr(ham, 7)
+    hz = [sum(1 << j for j in r) for r in ham]
+    return I.Code(m=3, n=7, row_ptr=rp, col_idx=ci, name="Steane", hz_rows=hz)
+
+
+@gpu
+@pytest.mark.parametrize("which,q,need_logical", [("steane", 0.12, True), ("gb63", 0.06, False)])
+def test_check_matches_rank_test_and_counts(dev, which, q, need_logical):
+    """Fail flags against conv and the rank test of e XOR e_hat in rowspace(H_Z) on the host."""
+    c = _steane() if which == "steane" else I.gb_code(63, 3)
+    dc = S.DeviceCode.from_code(c)
+    dc.set_logicals(S.x_logicals(c))
+    p = S.Params(mode="sagms", max_iter=50)
+    err, _, ehat, conv, iters, fail, counts = _pipeline(dc, p, 21, q, 2000)
+    e = err.cpu().numpy().view(np.uint32)
+    eh = ehat.cpu().numpy().view(np.uint32)
+    cv = conv.cpu().numpy()
+    f = fail.cpu().numpy()
+    r_bits = np.unpackbits((e ^ eh).view(np.uint8), axis=1, bitorder="little")[:, :c.n]
+    ok = logical_ok(c.hz_rows, r_bits)
+    want = np.where(cv == 0, 1, np.where(ok, 0, 2))
+    assert np.array_equal(f, want)
+    assert (want == 1).sum() > 0
+    if need_logical:
+        assert (want == 2).sum() > 0
+    assert counts == {"shots": 2000, "failures": int((want != 0).sum()), "not_converged": int((want == 1).sum()),
+                      "logical": int((want == 2).sum()), "iters_sum": int(iters.cpu().numpy().sum())}
+
+
+@gpu
+def test_pipeline_decodes_like_the_oracle(dev):
+    """The engine's decoder outputs on its own frames against the FP64 oracle."""
+    from tests import gpu_helpers as G
+    c = I.gb_code(255, 5)
+    dc = S.DeviceCode.from_code(c)
+    p = S.Params(mode="sagms", max_iter=100)
+    err, syn, L0 = S.mc_sample(dc, 31, 0.02, 0, 600)
+    G.compare(c, dc, syn.cpu().numpy().view(np.uint32), L0.cpu().numpy(), p)
+
+
+@gpu
+def test_run_equals_manual_batches_and_continues(dev):
+    c = I.gb_code(127, 4)
+    dc = S.DeviceCode.from_code(c)
+    dc.set_logicals(S.x_logicals(c))
+    p = S.Params(mode="sagms", max_iter=60)
+    q = 0.04
+    _, _, _, _, _, _, manual = _pipeline(dc, p, 77, q, 10000)
+    whole = S.mc_run(dc, p, 77, q, target_failures=10**9, max_shots=10000, batch=3333)
+    assert whole == manual
+    part = S.mc_run(dc, p, 77, q, target_failures=10**9, max_shots=4000, batch=1024)
+    rest = S.mc_run(dc, p, 77, q, target_failures=10**9, max_shots=10000, batch=1500, counts=part)
+    assert rest == manual
+
+
+@gpu
+def test_run_stops_between_batches_at_the_failure_target(dev):
+    c = I.gb_code(63, 3)
+    dc = S.DeviceCode.from_code(c)
+    dc.set_logicals(np.zeros((0, c.nw), dtype=np.uint32))    # k = 0: decoder failures only
+    p = S.Params(mode="ms", max_iter=20)
+    r = S.mc_run(dc, p, 5, 0.08, target_failures=50, max_shots=10**6, batch=256)
+    assert r["failures"] >= 50 and r["logical"] == 0
+    assert r["shots"] % 256 == 0 and r["shots"] < 10**6
+    prev = S.mc_run(dc, p, 5, 0.08, target_failures=10**9, max_shots=r["shots"] - 256, batch=256)
+    assert prev["failures"] < 50
+
+
+@gpu
+def test_run_needs_logicals(dev):
+    c = I.gb_code(63, 3)
+    dc = S.DeviceCode.from_code(c)
+    with pytest.raises(_native.SagmsError, match="logical"):
+        S.mc_run(dc, S.Params(), 1, 0.01, max_shots=10)
