@@ -168,6 +168,27 @@ def bench_mixed_degree(S, I, steps, shots_per_code=1_000_000):
             "plans": plans, "fer_syn": fer, "mean_iters": iters}
 
 
+def bench_mc(S, I, frames=10_000_000, q=0.01, seed=NOISE_SEED + 1):
+    """The fused Monte Carlo engine (sample -> decode -> logical check on the GPU, counters
+    back to the host) on the headline code: frames/s of the whole protocol and its FER."""
+    from paper_2605_10433_gb300.stats import wilson_interval
+    code = I.gb_code(L, W)
+    dc = S.DeviceCode.from_code(code)
+    logicals = S.x_logicals(code)
+    dc.set_logicals(logicals)
+    p = S.Params(mode="sagms", max_iter=MAX_ITER, **SAGMS_KW)
+    S.mc_run(dc, p, seed, q, target_failures=10**15, max_shots=1 << 20, batch=1 << 20)   # warm-up
+    t0 = time.perf_counter()
+    r = S.mc_run(dc, p, seed, q, target_failures=10**15, max_shots=frames, batch=1 << 22)
+    dt = time.perf_counter() - t0
+    lo, hi = wilson_interval(r["failures"], r["shots"])
+    return {"workload": f"GB l={L} w={W}, iid Z flips q={q}, L0=ln((1-q)/q), SAGMS max_iter={MAX_ITER}, "
+                        f"{frames:.0e} frames in batches of 2^22 (sagms_mc_run)",
+            "frames_per_s": r["shots"] / dt, "fer": r["failures"] / r["shots"], "wilson95": [lo, hi],
+            "not_converged": r["not_converged"], "logical": r["logical"], "mean_iters": r["iters_sum"] / r["shots"],
+            "k_logicals": int(logicals.shape[0])}
+
+
 def bench_serving(S, I, nreq=3000, load=0.6, seed=5):
     """Serving loop: Poisson-arriving requests from GB codes n in {126, 510, 1022, 2046}
     (w = 3/4/5/5), batch size floor(exp U[ln 1, ln 4096]), p ~ U[0.005, 0.03], SAGMS
@@ -415,6 +436,7 @@ def main():
         if world == 1:
             out["config3_mixed_degree"] = bench_mixed_degree(S, I, args.mode_steps)
             out["serving"] = bench_serving(S, I)
+            out["monte_carlo"] = bench_mc(S, I)
 
     # e2e: the C-ABI host entry point, host<->device copies inside the timed region
     h_syn = torch.from_numpy(syn.view(np.int32)).pin_memory()
