@@ -50,7 +50,13 @@ enum {
     SAGMS_FLAG_NO_EARLY_STOP = 2u,
     /* Use the one-shot-per-CTA kernel even where a two-slot kernel exists (cross-checks:
      * both kernels give bitwise identical results). */
-    SAGMS_FLAG_GENERIC_KERNEL = 4u
+    SAGMS_FLAG_GENERIC_KERNEL = 4u,
+    /* SAGMS only, per-shot priors only: the gain ceiling of Corollary 1.  Each shot's
+     * alpha_max is alpha*(|L0|, d_c) of Eq. 9 for its own prior L0 and the code's largest
+     * check degree d_c (alpha* decreases in d_c, Prop. 1, so on an irregular code this is
+     * the most conservative ceiling), clamped to [alpha_min, 1/eta_unsat]; a zero prior gets
+     * alpha_min.  params.alpha_max is then ignored. */
+    SAGMS_FLAG_AUTO_CEILING = 16u
 };
 
 /* Status codes. */
@@ -72,7 +78,7 @@ enum {
 #define SAGMS_MAX_DV 16     /* largest qubit degree |N(j)| */
 #define SAGMS_MAX_M 1024    /* one thread per check within a CTA */
 
-typedef struct sagms_code sagms_code; /* opaque, library-owned, immutable after load */
+typedef struct sagms_code sagms_code; /* opaque, library-owned */
 
 /*
  * Decoder parameters.

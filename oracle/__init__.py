@@ -25,6 +25,7 @@ MS, SMS, SAGMS, BP = 0, 1, 2, 3
 FLAG_L0_PER_QUBIT = 1
 FLAG_NO_EARLY_STOP = 2
 FLAG_NATURAL_UNITS = 8
+FLAG_AUTO_CEILING = 16
 
 MSFAM_CLIP = 1.0e6
 BP_CLIP = 23.718998

@@ -47,7 +47,10 @@
  *   - degree-1 checks: the leave-one-out set is empty, so min = +inf
  *     (MS family) or prod = 1 (BP) and the output saturates at the clip;
  *   - input validation (not part of the method): a non-finite prior marks the
- *     shot invalid (e_hat = 0, conv = 0, iters = -1).
+ *     shot invalid (e_hat = 0, conv = 0, iters = -1);
+ *   - ORACLE_FLAG_AUTO_CEILING (SAGMS, per-shot prior): the gain ceiling of
+ *     Corollary 1, alpha_max = alpha*(|L0|, d_c) of Eq. 9 per shot with d_c the
+ *     largest check degree, clamped to [alpha_min, 1/eta]; L0 = 0 gives alpha_min.
  */
 #include <math.h>
 #include <stdint.h>
@@ -62,6 +65,9 @@
 #define ORACLE_FLAG_L0_PER_QUBIT 1u
 #define ORACLE_FLAG_NO_EARLY_STOP 2u
 #define ORACLE_FLAG_NATURAL_UNITS 8u  /* oracle only: keep the MS family in LLR units */
+#define ORACLE_FLAG_AUTO_CEILING 16u
+
+double oracle_alpha_star(double L0, int dc);
 
 static const double MSFAM_CLIP = 1.0e6;
 static const double BP_CLIP = 23.718998;
@@ -123,6 +129,10 @@ int oracle_decode(int m, int n, const int32_t* row_ptr, const int32_t* col_idx,
 
     const int msfam = (mode != ORACLE_MODE_BP);
     const int per_qubit = (flags & ORACLE_FLAG_L0_PER_QUBIT) != 0;
+    const int auto_ceiling = (flags & ORACLE_FLAG_AUTO_CEILING) && mode == ORACLE_MODE_SAGMS && !per_qubit;
+    int dc_max = 0;
+    for (int i = 0; i < m; ++i)
+        if (row_ptr[i + 1] - row_ptr[i] > dc_max) dc_max = row_ptr[i + 1] - row_ptr[i];
     const int normalise = msfam && !per_qubit && !(flags & ORACLE_FLAG_NATURAL_UNITS);
     const int early_stop = !(flags & ORACLE_FLAG_NO_EARLY_STOP);
 
@@ -140,6 +150,15 @@ int oracle_decode(int m, int n, const int32_t* row_ptr, const int32_t* col_idx,
             conv[s] = 0;
             iters[s] = -1;
             continue;
+        }
+        /* the shot's gain ceiling (Corollary 1 with Eq. 9), or the alpha_max parameter */
+        double amax = alpha_max;
+        if (auto_ceiling) {
+            const double x = fabs(L0[s]);
+            double a = (x > 0.0) ? oracle_alpha_star(x, dc_max) : 0.0;
+            if (!(a >= alpha_min)) a = alpha_min;
+            if (a > 1.0 / eta_unsat) a = 1.0 / eta_unsat;
+            amax = a;
         }
         /* prior L0_j in the units the decoder runs in */
         for (int j = 0; j < n; ++j) {
@@ -177,7 +196,7 @@ int oracle_decode(int m, int n, const int32_t* row_ptr, const int32_t* col_idx,
                 if (mode == ORACLE_MODE_MS) gain[i] = 1.0;
                 else if (mode == ORACLE_MODE_SMS) gain[i] = alpha;
                 else if (mode == ORACLE_MODE_SAGMS)
-                    gain[i] = (alpha_max - (alpha_max - alpha_min) * gamma) * (sres[i] ? eta_unsat : 1.0);
+                    gain[i] = (amax - (amax - alpha_min) * gamma) * (sres[i] ? eta_unsat : 1.0);
                 else gain[i] = 1.0;
             }
 

@@ -13,6 +13,7 @@ MODES = {"ms": 0, "sms": 1, "sagms": 2, "bp": 3}
 FLAG_L0_PER_QUBIT = 1
 FLAG_NO_EARLY_STOP = 2
 FLAG_GENERIC_KERNEL = 4
+FLAG_AUTO_CEILING = 16
 
 
 @dataclass

@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(1024, 1) group_kernel(const DecodeArgs a, cons
     int* pfidx = cnt + 4;                                              // [2 buffers]
     int* shotsm = cnt + 6;                                             // [2 buffers]
     float* pfl0 = reinterpret_cast<float*>(cnt + 8);                   // [2 buffers]
+    float* amaxsh = reinterpret_cast<float*>(cnt + 10);                // alpha_max of the group's shot
     uint32_t* pfsyn = reinterpret_cast<uint32_t*>(cnt + 16);           // [2 buffers][32]
     uint32_t* flipw = reinterpret_cast<uint32_t*>(misc + 2 * kGrpMiscPerGroup);   // [32]
     const uint16_t pad = (uint16_t)(grp_P_off(g) + (size_t)NP * 4);
@@ -222,6 +223,9 @@ __global__ void __launch_bounds__(1024, 1) group_kernel(const DecodeArgs a, cons
                     } else {
                         const float pi = (l0 > 0.0f) ? 1.0f : ((l0 < 0.0f) ? -1.0f : 0.0f);
                         prior = pi;
+                        // alpha_max of the new shot.  Every thread of the group stores the
+                        // same value, so each thread's own read-back is that value.
+                        if (a.flags & kFlagAutoCeiling) *amaxsh = shot_alpha_max(a, l0);
                         sbits = bit0 | (bit1 << 1);
                         const bool flipped = pi < 0.0f;
                         // First check (l = 0), Eqs. 1 and 6: popcount of s XOR flip.
@@ -255,7 +259,8 @@ __global__ void __launch_bounds__(1024, 1) group_kernel(const DecodeArgs a, cons
         // A2 gains of the two checks (Eq. 7)
         float g0 = 1.0f, g1 = 1.0f;
         if (a.mode == kModeSAGMS) {
-            const float base = a.amax - (a.amax - a.amin) * ((float)gcnt * a.inv_m);
+            const float amax = (a.flags & kFlagAutoCeiling) ? *amaxsh : a.amax;
+            const float base = amax - (amax - a.amin) * ((float)gcnt * a.inv_m);
             g0 = base * (st0 ? a.eta : 1.0f);
             g1 = base * (st1 ? a.eta : 1.0f);
         } else if (a.mode == kModeSMS) {

@@ -41,6 +41,7 @@ struct DecodeArgs {
     int m, n, Mp, Np;
     int mode;
     float alpha, amin, amax, eta, inv_m;
+    int dcmax;     // largest check degree (the auto gain ceiling's d_c)
     int max_iter;
     unsigned flags;
     long long shots;
@@ -55,7 +56,28 @@ struct DecodeArgs {
 };
 
 enum { kModeMS = 0, kModeSMS = 1, kModeSAGMS = 2, kModeBP = 3 };
-enum { kFlagPerQubit = 1u, kFlagNoEarlyStop = 2u };
+enum { kFlagPerQubit = 1u, kFlagNoEarlyStop = 2u, kFlagAutoCeiling = 16u };
+
+// alpha_max of a shot under the automatic ceiling (Corollary 1): alpha*(|L0|, d_c) of Eq. 9,
+// clamped to [alpha_min, 1/eta].  alpha* = 2 atanh(t) / x with t = tanh(x/2)^(d_c - 1) is
+// evaluated as (ln(2 - w) - ln w) / x with w = 1 - t = -expm1((d_c - 1) log1p(-u)) and
+// u = 1 - tanh(x/2) = 2 / (e^x + 1), which keeps its accuracy when t rounds to 1 in FP32
+// (|L0| above about 18).  x = 0 gives alpha_min.
+__device__ __forceinline__ float auto_alpha_max(float l0, int dc, float amin, float eta) {
+    const float x = fabsf(l0);
+    float a = 0.0f;
+    if (x > 0.0f) {
+        const float u = 2.0f / (expf(x) + 1.0f);
+        const float w = -expm1f((float)(dc - 1) * log1pf(-u));
+        a = (logf(2.0f - w) - logf(w)) / x;
+    }
+    return fminf(fmaxf(a, amin), 1.0f / eta);
+}
+
+// alpha_max of a shot: the parameter, or the automatic ceiling of its prior.
+__device__ __forceinline__ float shot_alpha_max(const DecodeArgs& a, float l0) {
+    return (a.flags & kFlagAutoCeiling) ? auto_alpha_max(l0, a.dcmax, a.amin, a.eta) : a.amax;
+}
 
 __host__ __device__ inline size_t smem_bytes(int DC, int DV, int Mp, int Np, bool per_qubit) {
     size_t floats = (size_t)Np + (size_t)DC * Mp + 4 + (per_qubit ? (size_t)Np : 0);
@@ -110,6 +132,7 @@ __global__ void __launch_bounds__(1024, 1) decode_kernel(const DecodeArgs a) {
 
     for (long long shot = blockIdx.x; shot < a.shots; shot += gridDim.x) {
         float prior = 0.0f;
+        float amax = a.amax;
         bool valid;
         if (per_qubit) {
             valid = pq_ok != 0;
@@ -118,6 +141,7 @@ __global__ void __launch_bounds__(1024, 1) decode_kernel(const DecodeArgs a) {
             valid = isfinite(l0);
             if (BP) prior = l0 + 0.0f;
             else prior = (l0 > 0.0f) ? 1.0f : ((l0 < 0.0f) ? -1.0f : 0.0f);
+            if (valid) amax = shot_alpha_max(a, l0);
         }
         if (!valid) {
             for (int w = t; w < nw; w += T) a.err[shot * nw + w] = 0u;
@@ -159,7 +183,7 @@ __global__ void __launch_bounds__(1024, 1) decode_kernel(const DecodeArgs a) {
             // A2: gain
             float g;
             if (a.mode == kModeSAGMS)
-                g = (a.amax - (a.amax - a.amin) * ((float)cnt * a.inv_m)) * (st ? a.eta : 1.0f);
+                g = (amax - (amax - a.amin) * ((float)cnt * a.inv_m)) * (st ? a.eta : 1.0f);
             else if (a.mode == kModeSMS)
                 g = a.alpha;
             else

@@ -46,7 +46,7 @@ __host__ __device__ constexpr size_t qc_smem_bytes(int DV) { return qc_misc_off(
 // Bits of a per-check field for check k of a thread (K <= 4 checks, 8 bits each).
 __device__ __forceinline__ uint32_t qc_byte(uint32_t x, int k) { return (x >> (8 * k)) & 0xffu; }
 
-template <int DC, int DV, int K, int G>
+template <int DC, int DV, int K, int G, bool AUTO>
 __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* smem, const int tg,
                                          const uint32_t (&off)[K][DC], const uint32_t degs) {
     constexpr int T = 1024 / K;               // threads per group
@@ -64,6 +64,7 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
     int* pfidx = cnt + 4;
     int* shotsm = cnt + 6;
     float* pfl0 = reinterpret_cast<float*>(cnt + 8);
+    float* amaxsh = reinterpret_cast<float*>(cnt + 10);   // alpha_max of the group's shot (Eq. 7)
     uint32_t* pfsyn = reinterpret_cast<uint32_t*>(cnt + 16);
     const uint32_t* flipw = reinterpret_cast<const uint32_t*>(misc + 2 * kQcMisc);
     auto Pat = [&](uint32_t o) -> float& { return *reinterpret_cast<float*>(smem + PO + o); };
@@ -201,6 +202,9 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
                         idle = false;
                         fresh = true;
                         prior = pi;
+                        // alpha_max of the new shot.  Every thread of the group stores the
+                        // same value, so each thread's own read-back is that value.
+                        if (AUTO) *amaxsh = shot_alpha_max(a, l0);
                         gcnt = c0;
                         sbits = 0;
                         stb = 0;
@@ -221,7 +225,8 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
             // A2 gains (Eq. 7)
             float g[K];
             if (a.mode == kModeSAGMS) {
-                const float base = a.amax - (a.amax - a.amin) * ((float)gcnt * a.inv_m);
+                const float amax = AUTO ? *amaxsh : a.amax;
+            const float base = amax - (amax - a.amin) * ((float)gcnt * a.inv_m);
 #pragma unroll
                 for (int k = 0; k < K; ++k) g[k] = base * (((stb >> k) & 1u) ? a.eta : 1.0f);
             } else {
@@ -318,8 +323,9 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
 }
 
 // colQ: [K][DC][T] u32, byte offset 4 * col of check tg + kT in slot j (kQcPadOff for a
-// padded slot or a check past m).
-template <int DC, int DV, int K>
+// padded slot or a check past m).  AUTO: the gain ceiling of each shot comes from its prior
+// (SAGMS_FLAG_AUTO_CEILING), a separate instantiation so the default one carries no trace of it.
+template <int DC, int DV, int K, bool AUTO>
 __global__ void __launch_bounds__(2048 / K, 1) qc_kernel(const DecodeArgs a, const uint32_t* __restrict__ colQ) {
     static_assert(DC == 2 * DV && DC % 2 == 0 && (K == 2 || K == 4), "shape");
     constexpr int T = 1024 / K;
@@ -360,9 +366,9 @@ __global__ void __launch_bounds__(2048 / K, 1) qc_kernel(const DecodeArgs a, con
     }
     __syncthreads();
     if (t < T)
-        qc_group<DC, DV, K, 0>(a, smem, tg, off, degs);
+        qc_group<DC, DV, K, 0, AUTO>(a, smem, tg, off, degs);
     else
-        qc_group<DC, DV, K, 1>(a, smem, tg, off, degs);
+        qc_group<DC, DV, K, 1, AUTO>(a, smem, tg, off, degs);
 }
 
 }  // namespace sagms

@@ -41,6 +41,7 @@ __host__ __device__ inline size_t slot_smem_bytes(int DC, int DV, int MP, int NP
            + (size_t)DC * MP * 2                     // colB
            + (size_t)DV * NP * 4                     // vneB
            + 16 + 32 * 4 + 64 * 4 + 16 + 16 + 16     // cnt, flipw, negw, claim, pfidx, shotsm
+           + 16                                      // amaxsh
            + 2 * 2 * 32 * 4 + 2 * 2 * 4;             // prefetch buffers (syndrome rows, priors)
 }
 
@@ -80,6 +81,7 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
     float* pfl0 = reinterpret_cast<float*>(pfsyn + 128);      // [2 slots][2 buffers] priors
     int* pfidx = reinterpret_cast<int*>(pfl0 + 4);            // [2 slots][2 buffers] shot in each buffer
     int* shotsm = pfidx + 4;                                  // [2 slots][2] shot being decoded
+    float* amaxsh = reinterpret_cast<float*>(shotsm + 4);     // [2 slots] alpha_max of the slot's shot
     const unsigned char* c2base = reinterpret_cast<const unsigned char*>(C2);
 
     const int t = threadIdx.x;
@@ -276,6 +278,9 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
                 }
                 const float pi = per_qubit ? 0.0f : ((l0 > 0.0f) ? 1.0f : ((l0 < 0.0f) ? -1.0f : 0.0f));
                 prior[k] = pi;
+                // alpha_max of the new shot.  Every thread stores the same value, so each
+                // thread's own read-back below is that value without a barrier.
+                if (a.flags & kFlagAutoCeiling) amaxsh[k] = shot_alpha_max(a, l0);
                 sbits = (sbits & ~(1u << k)) | (bit << k);
                 const bool flipped = per_qubit || pi < 0.0f;
                 // First check (l = 0) of the new shot, Eqs. 1 and 6: popcount of s XOR flip.
@@ -310,8 +315,11 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
         // A2 gains (Eq. 7 with this round's count and residual bit)
         float g0 = 1.0f, g1 = 1.0f;
         if (a.mode == kModeSAGMS) {
-            g0 = (a.amax - (a.amax - a.amin) * ((float)gcnt[0] * a.inv_m)) * (gst[0] ? a.eta : 1.0f);
-            g1 = (a.amax - (a.amax - a.amin) * ((float)gcnt[1] * a.inv_m)) * (gst[1] ? a.eta : 1.0f);
+            const bool autoc = (a.flags & kFlagAutoCeiling) != 0;
+            const float am0 = autoc ? amaxsh[0] : a.amax;
+            const float am1 = autoc ? amaxsh[1] : a.amax;
+            g0 = (am0 - (am0 - a.amin) * ((float)gcnt[0] * a.inv_m)) * (gst[0] ? a.eta : 1.0f);
+            g1 = (am1 - (am1 - a.amin) * ((float)gcnt[1] * a.inv_m)) * (gst[1] ? a.eta : 1.0f);
         } else if (a.mode == kModeSMS) {
             g0 = a.alpha;
             g1 = a.alpha;

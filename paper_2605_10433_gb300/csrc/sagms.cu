@@ -83,11 +83,14 @@ constexpr int kQcDV[] = {3, 4, 5};
 constexpr int kNumQc = sizeof(kQcDV) / sizeof(kQcDV[0]);
 constexpr int kQcK = 4;
 using QcFn = void (*)(const DecodeArgs, const uint32_t*);
-QcFn qc_kernel_for(int v) {
-    switch (v) {
-        case 0: return qc_kernel<6, 3, kQcK>;
-        case 1: return qc_kernel<8, 4, kQcK>;
-        default: return qc_kernel<10, 5, kQcK>;
+QcFn qc_kernel_for(int v, bool auto_ceiling) {
+    switch (v * 2 + (auto_ceiling ? 1 : 0)) {
+        case 0: return qc_kernel<6, 3, kQcK, false>;
+        case 1: return qc_kernel<6, 3, kQcK, true>;
+        case 2: return qc_kernel<8, 4, kQcK, false>;
+        case 3: return qc_kernel<8, 4, kQcK, true>;
+        case 4: return qc_kernel<10, 5, kQcK, false>;
+        default: return qc_kernel<10, 5, kQcK, true>;
     }
 }
 
@@ -232,8 +235,14 @@ double sagms_alpha_star(double L0, int32_t dc) {
 
 int sagms_check_params(const sagms_params* p) {
     if (!p) return fail(SAGMS_ERR_ARG, "params is NULL");
-    if (p->flags & ~(uint32_t)(SAGMS_FLAG_L0_PER_QUBIT | SAGMS_FLAG_NO_EARLY_STOP | SAGMS_FLAG_GENERIC_KERNEL))
+    if (p->flags & ~(uint32_t)(SAGMS_FLAG_L0_PER_QUBIT | SAGMS_FLAG_NO_EARLY_STOP | SAGMS_FLAG_GENERIC_KERNEL |
+                               SAGMS_FLAG_AUTO_CEILING))
         return fail(SAGMS_ERR_ARG, "unknown flag bits 0x%x", p->flags);
+    const bool auto_ceiling = (p->flags & SAGMS_FLAG_AUTO_CEILING) != 0;
+    if (auto_ceiling && p->mode != SAGMS_SAGMS)
+        return fail(SAGMS_ERR_PARAM, "SAGMS_FLAG_AUTO_CEILING applies to the SAGMS mode only");
+    if (auto_ceiling && (p->flags & SAGMS_FLAG_L0_PER_QUBIT))
+        return fail(SAGMS_ERR_PARAM, "SAGMS_FLAG_AUTO_CEILING needs one prior per shot");
     if (p->max_iter < 0 || p->max_iter > 100000)
         return fail(SAGMS_ERR_PARAM, "max_iter %d outside [0, 100000]", p->max_iter);
     switch (p->mode) {
@@ -246,6 +255,17 @@ int sagms_check_params(const sagms_params* p) {
             return SAGMS_OK;
         case SAGMS_SAGMS: {
             const float eta = (p->eta_unsat == 0.0f) ? 1.10f : p->eta_unsat;
+            if (auto_ceiling) {
+                // alpha_max comes from each shot's prior, clamped to [alpha_min, 1/eta]
+                if (!(p->alpha_min > 0.0f && p->alpha_min <= 1.0f))
+                    return fail(SAGMS_ERR_PARAM, "need 0 < alpha_min <= 1 (got %g)", (double)p->alpha_min);
+                if (!(eta >= 1.0f) || !std::isfinite(eta))
+                    return fail(SAGMS_ERR_PARAM, "eta_unsat %g must be >= 1", (double)eta);
+                if ((double)p->alpha_min * (double)eta > 1.0 + 1e-6)
+                    return fail(SAGMS_ERR_PARAM, "stability constraint alpha_min * eta_unsat <= 1 violated (%g)",
+                                (double)p->alpha_min * (double)eta);
+                return SAGMS_OK;
+            }
             if (!(p->alpha_min > 0.0f && p->alpha_min <= p->alpha_max && p->alpha_max <= 1.0f))
                 return fail(SAGMS_ERR_PARAM, "need 0 < alpha_min <= alpha_max <= 1 (got %g, %g)",
                             (double)p->alpha_min, (double)p->alpha_max);
@@ -509,6 +529,7 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     a.amax = p->alpha_max;
     a.eta = (p->eta_unsat == 0.0f) ? 1.10f : p->eta_unsat;
     a.inv_m = 1.0f / (float)code->m;
+    a.dcmax = code->dc_max;
     a.max_iter = p->max_iter;
     a.flags = p->flags;
     a.shots = shots;
@@ -520,6 +541,7 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     // Kernel: the plan's choice where the code and parameters allow it, else the fastest
     // that does (two-group, two-slot, one-shot-per-CTA).
     const bool msfam_fast = !bp && !(p->flags & SAGMS_FLAG_GENERIC_KERNEL);
+    const bool auto_ceiling = (p->flags & SAGMS_FLAG_AUTO_CEILING) != 0;
     const bool use_qc = msfam_fast && code->qc_variant >= 0 && !per_qubit && (plan.kernel == 0 || plan.kernel == 4);
     const bool use_groups = !use_qc && msfam_fast && code->groups && !per_qubit &&
                             (plan.kernel == 0 || plan.kernel >= 3);
@@ -537,7 +559,7 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     long long units;
     if (use_qc) {
         const int DVq = kQcDV[code->qc_variant];
-        fn = reinterpret_cast<const void*>(qc_kernel_for(code->qc_variant));
+        fn = reinterpret_cast<const void*>(qc_kernel_for(code->qc_variant, auto_ceiling));
         smem = qc_smem_bytes(DVq);
         threads = 2048 / kQcK;
         units = (shots + 1) / 2;   // two shots in flight per CTA
@@ -609,7 +631,7 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
         const long long g = std::min(grid, (cnt + 1) / 2);
         c.chunk_lg = plan.chunk_lg > 0 ? plan.chunk_lg : chunk_lg_for(cnt, g);
         if (use_qc)
-            qc_kernel_for(code->qc_variant)<<<(unsigned)g, threads, smem, stream>>>(c, code->d_colQ);
+            qc_kernel_for(code->qc_variant, auto_ceiling)<<<(unsigned)g, threads, smem, stream>>>(c, code->d_colQ);
         else if (use_groups)
             group_kernel_fn()<<<(unsigned)g, threads, smem, stream>>>(c, glay);
         else
