@@ -205,3 +205,22 @@ def test_run_needs_logicals(dev):
     dc = S.DeviceCode.from_code(c)
     with pytest.raises(_native.SagmsError, match="logical"):
         S.mc_run(dc, S.Params(), 1, 0.01, max_shots=10)
+
+
+@gpu
+def test_sms_alpha_sweep_rows_are_independent_runs(dev):
+    """The sweep is one Monte Carlo run per alpha on the same frames: each row equals a
+    direct run, the best alpha has the lowest FER, and alpha* is Eq. 9 for the prior."""
+    from paper_2605_10433_gb300.sweep import sms_alpha_sweep
+    import oracle
+    c = I.gb_code(63, 3)
+    dc = S.DeviceCode.from_code(c)
+    dc.set_logicals(S.x_logicals(c))
+    alphas = [0.5, 0.7, 0.9, 1.0]
+    sw = sms_alpha_sweep(dc, alphas, 0.05, seed=9, target_failures=10**9, max_shots=4000, max_iter=30, batch=1000)
+    for row, a in zip(sw["rows"], alphas):
+        r = S.mc_run(dc, S.Params(mode="sms", alpha=a, max_iter=30), 9, 0.05, target_failures=10**9,
+                     max_shots=4000, batch=4000)
+        assert (row["failures"], row["shots"], row["logical"]) == (r["failures"], r["shots"], r["logical"])
+    assert sw["best_alpha"] == min(sw["rows"], key=lambda x: (x["fer"], x["alpha"]))["alpha"]
+    assert sw["alpha_star"] == pytest.approx(oracle.alpha_star(np.log(0.95 / 0.05), 6), rel=1e-12)
