@@ -5,23 +5,25 @@
 // structure (slot j < w is term j of a(x) and qubit c < l meets it as its j-th edge; slot
 // w + k is term k of b(x)), with DC = 2w and DV = w.
 //
-// A CTA holds two independent groups of T = 1024 / K threads; each group decodes one shot at
-// a time and refills as shots finish (as in decode_groups.cuh), synchronised by its own named
-// barriers, so one group's arithmetic-bound check-node phase overlaps the other's
-// shared-memory-bound phases.  Thread tg of a group owns the K checks tg + kT and the K qubit
-// pairs (2tg + 2hT, 2tg + 2hT + 1), h < K.  The byte offsets of its checks' columns stay in
-// registers for the whole launch (K * DC of them: with K = 4 the 512-thread CTA has 128
-// registers per thread).
+// A 512-thread CTA holds NG = 512 / T independent groups of T threads; each group decodes one
+// shot at a time and refills as shots finish (as in decode_groups.cuh), synchronised by its
+// own named barrier (a warp barrier when T = 32), so one group's arithmetic-bound check-node
+// phase overlaps another's shared-memory-bound phases.  Thread tg of a group owns the K checks
+// tg + kT and the qubit pairs (2tg + 2hT, 2tg + 2hT + 1), h < NP / 2T.  The byte offsets of
+// its checks' columns stay in registers for the whole launch, biased by its group's
+// shared-memory base, so every access of the loop is a register plus an immediate and one
+// code body serves all groups (K * DC offsets: with K = 4 a thread has 128 registers).
 //
-// Shared memory per group g (byte offsets are compile-time for each group):
-//   P_g[2048 + 4]          posteriors; P_g[2048] = +inf is the column padded check slots read
-//   C_g[q][2048 + 4]       negated message D = -L_{i->c} of qubit c's q-th edge at [q][c];
-//                          column 2048 is scratch for padded check slots
-// A check thread reaches P_g[col] and C_g[j mod DV][col] from the same offset register, and a
-// qubit thread reads its messages at fixed offsets: no index loads at all.  A freshly loaded
-// shot's first round has every check send the same message on all of its edges (all inputs
-// are the prior), so that round stores one closed-form value per check instead of running
-// the check-node minimum search.
+// Shared memory per group g:
+//   P_g[NP + 4]            posteriors; P_g[NP] = +inf is the column padded check slots read
+//   C_g[q][NP + 4]         negated message D = -L_{i->c} of qubit c's q-th edge at [q][c];
+//                          column NP is scratch for padded check slots
+// then the groups' bookkeeping and the first-check flip words.  A check thread reaches
+// P_g[col] and C_g[j mod DV][col] from the same offset register, and a qubit thread reads its
+// messages at fixed offsets: no index loads at all.  A freshly loaded shot's first round has
+// every check send the same message on all of its edges (all inputs are the prior), so that
+// round stores one closed-form value per check instead of running the check-node minimum
+// search.
 //
 // The arithmetic of every check and qubit is, operation for operation, that of
 // decode_kernel.cuh: results are bitwise identical to the other kernels.
@@ -31,61 +33,80 @@
 
 namespace sagms {
 
-constexpr int kQcRowBytes = (kGrpQubits + 4) * 4;    // one qubit-indexed row plus padding column
-constexpr uint32_t kQcPadOff = (uint32_t)kGrpQubits * 4;
-constexpr int kQcMisc = 320;                          // per-group bookkeeping bytes
+constexpr int kQcMisc = 320;     // per-group bookkeeping bytes
+constexpr int kQcThreads = 512;  // threads per CTA
 
-__host__ __device__ constexpr size_t qc_group_bytes(int DV) { return (size_t)(1 + DV) * kQcRowBytes; }
-__host__ __device__ constexpr size_t qc_P_off(int DV, int g) { return (size_t)g * qc_group_bytes(DV); }
-__host__ __device__ constexpr size_t qc_C_off(int DV, int g, int q) {
-    return qc_P_off(DV, g) + (size_t)(1 + q) * kQcRowBytes;
+// One kernel shape: DC x DV slot degrees, K checks per thread, T threads per group, NP qubit
+// columns.  Byte layout of the CTA's shared memory (see the file comment).
+template <int DC_, int DV_, int K_, int T_, int NP_>
+struct QcShape {
+    static constexpr int DC = DC_, DV = DV_, K = K_, T = T_, NP = NP_;
+    static constexpr int NG = kQcThreads / T;               // groups per CTA
+    static constexpr int MC = K * T;                        // checks a group covers
+    static constexpr size_t ROW = (size_t)(NP + 4) * 4;     // one qubit-indexed row + padding
+    static constexpr uint32_t PAD = (uint32_t)NP * 4;       // byte offset of the padding column
+    static constexpr size_t GROUP = (size_t)(1 + DV) * ROW;
+    static constexpr size_t MISC = (size_t)NG * GROUP;
+    static constexpr size_t SMEM = MISC + (size_t)NG * kQcMisc + 32 * 4;
+    static_assert(DC == 2 * DV && (K == 2 || K == 4) && NG * T == kQcThreads, "shape");
+    static_assert(NP % (2 * T) == 0 && MC <= 1024 && (T == 32 || NG <= 15), "layout");
+};
+
+// Group barrier: a warp barrier for warp-sized groups, else named barrier 1 + g (an
+// immediate when the group index is known at compile time, GC >= 0).
+template <int T, int GC>
+__device__ __forceinline__ void qc_sync(int g) {
+    if constexpr (T == 32) __syncwarp();
+    else if constexpr (GC >= 0) asm volatile("bar.sync %0, %1;" ::"n"(1 + GC), "n"(T) : "memory");
+    else asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "n"(T) : "memory");
 }
-__host__ __device__ constexpr size_t qc_misc_off(int DV) { return 2 * qc_group_bytes(DV); }
-__host__ __device__ constexpr size_t qc_smem_bytes(int DV) { return qc_misc_off(DV) + 2 * kQcMisc + 32 * 4; }
 
 // Bits of a per-check field for check k of a thread (K <= 4 checks, 8 bits each).
 __device__ __forceinline__ uint32_t qc_byte(uint32_t x, int k) { return (x >> (8 * k)) & 0xffu; }
 
-template <int DC, int DV, int K, int G, bool AUTO>
-__device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* smem, const int tg,
-                                         const uint32_t (&off)[K][DC], const uint32_t degs) {
-    constexpr int T = 1024 / K;               // threads per group
-    constexpr int NP = kGrpQubits;
-    constexpr size_t PO = qc_P_off(DV, G);
+// GC: the group index when it is fixed at compile time (one copy of the loop per group, every
+// group address an immediate), or -1 (one copy for all groups, g at run time).
+template <class S, bool AUTO, int GC>
+__device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* smem, const int tg, const int g_rt,
+                                         const uint32_t (&off)[S::K][S::DC], const uint32_t degs) {
+    constexpr int DC = S::DC, DV = S::DV, K = S::K, T = S::T, NP = S::NP;
+    const int g = GC >= 0 ? GC : g_rt;
+    const size_t PO = (size_t)g * S::GROUP;
     const bool early = (a.flags & kFlagNoEarlyStop) == 0;
     const int lane = tg & 31;
     const int n = a.n, m = a.m;
     const int mw = (m + 31) >> 5, nw = (n + 31) >> 5;
     const float inf = __uint_as_float(0x7f800000u);
     float* P = reinterpret_cast<float*>(smem + PO);
-    unsigned char* misc = smem + qc_misc_off(DV);
-    int* cnt = reinterpret_cast<int*>(misc + G * kQcMisc);   // [2 parity]
+    unsigned char* misc = smem + S::MISC;
+    int* cnt = reinterpret_cast<int*>(misc + g * kQcMisc);   // [2 parity]
     int* claim = cnt + 2;
     int* pfidx = cnt + 4;
     int* shotsm = cnt + 6;
     float* pfl0 = reinterpret_cast<float*>(cnt + 8);
     float* amaxsh = reinterpret_cast<float*>(cnt + 10);   // alpha_max of the group's shot (Eq. 7)
     uint32_t* pfsyn = reinterpret_cast<uint32_t*>(cnt + 16);
-    const uint32_t* flipw = reinterpret_cast<const uint32_t*>(misc + 2 * kQcMisc);
-    auto Pat = [&](uint32_t o) -> float& { return *reinterpret_cast<float*>(smem + PO + o); };
+    const uint32_t* flipw = reinterpret_cast<const uint32_t*>(misc + S::NG * kQcMisc);
+    // o: the column's byte offset biased by the group's base
+    auto Pat = [&](uint32_t o) -> float& { return *reinterpret_cast<float*>(smem + o); };
     auto Cat = [&](int j, uint32_t o) -> float& {
-        return *reinterpret_cast<float*>(smem + qc_C_off(DV, G, j % DV) + o);
+        return *reinterpret_cast<float*>(smem + o + (size_t)(1 + j % DV) * S::ROW);
     };
 
     const int nshots = (int)a.shots;
     const int clg = a.chunk_lg;
     const int cmask = (1 << clg) - 1;
     const bool dynamic = a.work != nullptr;
-    const int gid = 2 * (int)blockIdx.x + G;
-    const int gstride = 2 * (int)gridDim.x;
+    const int gid = S::NG * (int)blockIdx.x + g;
+    const int gstride = S::NG * (int)gridDim.x;
     if (tg == 0) {
         claim[0] = dynamic ? atomicAdd(a.work, 1) : gid;
         claim[1] = dynamic ? atomicAdd(a.work, 1) : gid + gstride;
     }
-    asm volatile("bar.sync %0, %1;" ::"n"(1 + G), "n"(T) : "memory");
+    qc_sync<T, GC>(g);
     // Shots: chunks of 2^chunk_lg consecutive shots, claimed dynamically through the work
     // counter (one atomic per chunk, a chunk ahead of its use, via the two-entry ring
-    // `claim`), or statically: group b = 2 * CTA + g takes chunks b, b + 2G, ...
+    // `claim`), or statically: group b = NG * CTA + g takes chunks b, b + NG * grid, ...
     int seqp = 0;
     auto assign = [&]() -> int {
         const int p = seqp++;
@@ -138,7 +159,7 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
         const int part = __reduce_add_sync(0xffffffffu, __popc(xb));
         if (lane == 0) atomicAdd(&cnt[ph], part);
         if (tg < 32) cp_async_wait_all();
-        asm volatile("bar.sync %0, %1;" ::"n"(1 + G), "n"(T) : "memory");
+        qc_sync<T, GC>(g);
         int gcnt = cnt[ph];
         uint32_t stb = xb;   // bit k: residual bit of check k this round
         if (tg == 0) cnt[ph ^ 1] = 0;
@@ -294,7 +315,7 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
                 }
             }
         }
-        asm volatile("bar.sync %0, %1;" ::"n"(1 + G), "n"(T) : "memory");
+        qc_sync<T, GC>(g);
 
         // Claim and prefetch the group's next shot (warp 0 of the group).
         if (consumed >= 0 && tg < 32) {
@@ -306,31 +327,32 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
         if (!idle) {
             // A4 variable-node update: qubit pairs (2tg + 2hT, 2tg + 2hT + 1)
             const float2 npr = make_float2(-prior, -prior);
+            unsigned char* vbase = smem + PO + (size_t)tg * 8;
 #pragma unroll
-            for (int h = 0; h < K; ++h) {
-                const int c = h * 2 * T + 2 * tg;
+            for (int h = 0; h < NP / (2 * T); ++h) {
                 float2 acc = npr;
 #pragma unroll
                 for (int q = 0; q < DV; ++q)
-                    acc = add2(acc, *reinterpret_cast<const float2*>(smem + qc_C_off(DV, G, q) + (size_t)c * 4));
-                *reinterpret_cast<float2*>(smem + PO + (size_t)c * 4) =
+                    acc = add2(acc, *reinterpret_cast<const float2*>(vbase + (size_t)(1 + q) * S::ROW + (size_t)h * 8 * T));
+                *reinterpret_cast<float2*>(vbase + (size_t)h * 8 * T) =
                     __ffma2_rn(acc, make_float2(-1.0f, -1.0f), make_float2(0.0f, 0.0f));
             }
         }
-        asm volatile("bar.sync %0, %1;" ::"n"(1 + G), "n"(T) : "memory");
+        qc_sync<T, GC>(g);
         ph ^= 1;
     }
 }
 
-// colQ: [K][DC][T] u32, byte offset 4 * col of check tg + kT in slot j (kQcPadOff for a
-// padded slot or a check past m).  AUTO: the gain ceiling of each shot comes from its prior
+// colQ: [K][DC][T] u32, byte offset 4 * col of check tg + kT in slot j (S::PAD for a padded
+// slot or a check past m).  AUTO: the gain ceiling of each shot comes from its prior
 // (SAGMS_FLAG_AUTO_CEILING), a separate instantiation so the default one carries no trace of it.
-template <int DC, int DV, int K, bool AUTO>
-__global__ void __launch_bounds__(2048 / K, 1) qc_kernel(const DecodeArgs a, const uint32_t* __restrict__ colQ) {
-    static_assert(DC == 2 * DV && DC % 2 == 0 && (K == 2 || K == 4), "shape");
-    constexpr int T = 1024 / K;
+template <class S, bool AUTO>
+__global__ void __launch_bounds__(kQcThreads, S::K * S::DC <= 16 ? 2 : 1)
+qc_kernel(const DecodeArgs a, const uint32_t* __restrict__ colQ) {
+    constexpr int DC = S::DC, K = S::K, T = S::T;
     extern __shared__ __align__(16) unsigned char smem[];
     const int t = threadIdx.x;
+    const int g = t / T;
     const int tg = t % T;
     const float inf = __uint_as_float(0x7f800000u);
     uint32_t off[K][DC];
@@ -340,23 +362,24 @@ __global__ void __launch_bounds__(2048 / K, 1) qc_kernel(const DecodeArgs a, con
         uint32_t d = 0;
 #pragma unroll
         for (int j = 0; j < DC; ++j) {
-            off[k][j] = __ldg(colQ + (k * DC + j) * T + tg);
-            d += (off[k][j] != kQcPadOff) ? 1u : 0u;
+            const uint32_t o = __ldg(colQ + (k * DC + j) * T + tg);
+            d += (o != S::PAD) ? 1u : 0u;
+            off[k][j] = o + (uint32_t)(g * S::GROUP);   // into this group's arrays
         }
         degs |= d << (8 * k);
     }
-    // Posteriors, messages and bookkeeping of both groups start at zero; the padding columns
+    // Posteriors, messages and bookkeeping of every group start at zero; the padding columns
     // of the posteriors hold +inf.
     {
         float* z = reinterpret_cast<float*>(smem);
-        for (int k = t; k < (int)(2 * qc_group_bytes(DV) / 4); k += 2 * T) z[k] = 0.0f;
-        int* misc = reinterpret_cast<int*>(smem + qc_misc_off(DV));
-        for (int k = t; k < 2 * kQcMisc / 4; k += 2 * T) misc[k] = 0;
+        for (int k = t; k < (int)(S::MISC / 4); k += kQcThreads) z[k] = 0.0f;
+        int* misc = reinterpret_cast<int*>(smem + S::MISC);
+        for (int k = t; k < S::NG * kQcMisc / 4; k += kQcThreads) misc[k] = 0;
     }
     __syncthreads();
-    if (t < 2) *reinterpret_cast<float*>(smem + qc_P_off(DV, t) + kQcPadOff) = inf;
+    if (t < S::NG) *reinterpret_cast<float*>(smem + (size_t)t * S::GROUP + S::PAD) = inf;
     // First residual bits under a negative prior: a check's degree parity.
-    uint32_t* flipw = reinterpret_cast<uint32_t*>(smem + qc_misc_off(DV) + 2 * kQcMisc);
+    uint32_t* flipw = reinterpret_cast<uint32_t*>(smem + S::MISC + S::NG * kQcMisc);
     if (t < T) {
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -365,10 +388,12 @@ __global__ void __launch_bounds__(2048 / K, 1) qc_kernel(const DecodeArgs a, con
         }
     }
     __syncthreads();
-    if (t < T)
-        qc_group<DC, DV, K, 0, AUTO>(a, smem, tg, off, degs);
-    else
-        qc_group<DC, DV, K, 1, AUTO>(a, smem, tg, off, degs);
+    if constexpr (S::NG == 2) {
+        if (g == 0) qc_group<S, AUTO, 0>(a, smem, tg, g, off, degs);
+        else qc_group<S, AUTO, 1>(a, smem, tg, g, off, degs);
+    } else {
+        qc_group<S, AUTO, -1>(a, smem, tg, g, off, degs);
+    }
 }
 
 }  // namespace sagms

@@ -77,31 +77,40 @@ constexpr int kGroupDC = 10, kGroupDV = 5;
 using GroupFn = void (*)(const DecodeArgs, const GroupLayout);
 GroupFn group_kernel_fn() { return group_kernel<kGroupDC, kGroupDV>; }
 
-// Column-indexed two-group kernels (decode_qc.cuh): (DC, DV) with DC = 2 DV, four checks per
-// thread (with two checks per thread, 1024-thread CTAs, it measured 5-15% slower).
-constexpr int kQcDV[] = {3, 4, 5};
-constexpr int kNumQc = sizeof(kQcDV) / sizeof(kQcDV[0]);
-constexpr int kQcK = 4;
+// Column-indexed group kernels (decode_qc.cuh): one entry per compiled shape, listed by
+// increasing size; a code takes the first whose slot degrees cover it (DC = 2 DV), whose
+// checks and qubits it fills at least halfway, and whose slot structure it has.  Four checks
+// per thread where the offsets and inputs fit in 128 registers (two checks per thread in
+// 1024-thread CTAs measured 5-15% slower at n = 2046).
 using QcFn = void (*)(const DecodeArgs, const uint32_t*);
-QcFn qc_kernel_for(int v, bool auto_ceiling) {
-    switch (v * 2 + (auto_ceiling ? 1 : 0)) {
-        case 0: return qc_kernel<6, 3, kQcK, false>;
-        case 1: return qc_kernel<6, 3, kQcK, true>;
-        case 2: return qc_kernel<8, 4, kQcK, false>;
-        case 3: return qc_kernel<8, 4, kQcK, true>;
-        case 4: return qc_kernel<10, 5, kQcK, false>;
-        default: return qc_kernel<10, 5, kQcK, true>;
+struct QcVariant {
+    int dc, dv, k, t, np;
+    QcFn fn[2];    // [auto ceiling]
+    size_t smem;
+};
+#define SAGMS_QC(DC, DV, K, T, NP)                                                               \
+    QcVariant {                                                                                   \
+        DC, DV, K, T, NP, {qc_kernel<QcShape<DC, DV, K, T, NP>, false>, qc_kernel<QcShape<DC, DV, K, T, NP>, true>}, \
+            QcShape<DC, DV, K, T, NP>::SMEM                                                       \
     }
-}
+const QcVariant kQcVariants[] = {
+    SAGMS_QC(6, 3, 2, 32, 128),                                                       // n <= 128
+    SAGMS_QC(8, 4, 4, 32, 256),                                                       // n <= 256
+    SAGMS_QC(6, 3, 4, 64, 512),  SAGMS_QC(8, 4, 4, 64, 512),  SAGMS_QC(10, 5, 4, 64, 512),
+    SAGMS_QC(12, 6, 4, 64, 512), SAGMS_QC(16, 8, 2, 128, 512),                        // n <= 512
+    SAGMS_QC(8, 4, 4, 128, 1024), SAGMS_QC(10, 5, 4, 128, 1024),                      // n <= 1024
+    SAGMS_QC(6, 3, 4, 256, 2048), SAGMS_QC(8, 4, 4, 256, 2048), SAGMS_QC(10, 5, 4, 256, 2048),
+};
+#undef SAGMS_QC
+constexpr int kNumQc = sizeof(kQcVariants) / sizeof(kQcVariants[0]);
 
-// colQ layout of the column-indexed kernel: [K][DC][1024 / K], byte offset 4 * col of check
-// tg + k * (1024 / K) in slot j (kQcPadOff for padding).
-std::vector<uint32_t> qc_layout(int m, const int32_t* row_ptr, const int32_t* col_idx, int DC) {
-    constexpr int K = kQcK, T = 1024 / kQcK;
-    std::vector<uint32_t> out((size_t)K * DC * T, kQcPadOff);
+// colQ layout of a column-indexed shape: [K][DC][T], byte offset 4 * col of check
+// tg + k * T in slot j (4 * NP, the padding column, for padding).
+std::vector<uint32_t> qc_layout(int m, const int32_t* row_ptr, const int32_t* col_idx, const QcVariant& V) {
+    std::vector<uint32_t> out((size_t)V.k * V.dc * V.t, (uint32_t)V.np * 4u);
     for (int i = 0; i < m; ++i)
         for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
-            out[((size_t)(i / T) * DC + (e - row_ptr[i])) * T + (i % T)] = (uint32_t)col_idx[e] * 4u;
+            out[((size_t)(i / V.t) * V.dc + (e - row_ptr[i])) * V.t + (i % V.t)] = (uint32_t)col_idx[e] * 4u;
     return out;
 }
 
@@ -383,13 +392,14 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
     }
 
     // Column-indexed layout, when every edge in check slot j is its qubit's edge number
-    // j mod DV and a qubit's edges in increasing slot have increasing numbers (the smallest
-    // compiled DV that covers the degrees and has that structure).
+    // j mod DV and a qubit's edges in increasing slot have increasing numbers.
     int qv = -1;
-    if (m > 512 && m <= kGrpChecks && n <= kGrpQubits) {
+    {
         for (int v = 0; v < kNumQc && qv < 0; ++v) {
-            const int DVq = kQcDV[v];
-            if (dc_max > 2 * DVq || dv_max > DVq) continue;
+            const QcVariant& V = kQcVariants[v];
+            const int DVq = V.dv;
+            if (dc_max > V.dc || dv_max > V.dv) continue;
+            if (m > V.k * V.t || 2 * m <= V.k * V.t || n > V.np || 2 * n <= V.np) continue;
             bool ok = true;
             for (int c = 0; c < n && ok; ++c) {
                 const auto& ve = vedges[c];   // sorted by slot
@@ -400,7 +410,7 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
         }
     }
     std::vector<uint32_t> colQ;
-    if (qv >= 0) colQ = qc_layout(m, row_ptr, col_idx, 2 * kQcDV[qv]);
+    if (qv >= 0) colQ = qc_layout(m, row_ptr, col_idx, kQcVariants[qv]);
 
     // Checks of each qubit, for syndrome formation in the Monte Carlo sampler.
     std::vector<uint16_t> qchk((size_t)dv_max * n, (uint16_t)0xFFFFu);
@@ -556,29 +566,29 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     const void* fn;
     size_t smem;
     int threads;
-    long long units;
+    int shots_per_cta;   // shots one CTA decodes at a time
     if (use_qc) {
-        const int DVq = kQcDV[code->qc_variant];
-        fn = reinterpret_cast<const void*>(qc_kernel_for(code->qc_variant, auto_ceiling));
-        smem = qc_smem_bytes(DVq);
-        threads = 2048 / kQcK;
-        units = (shots + 1) / 2;   // two shots in flight per CTA
+        const QcVariant& V = kQcVariants[code->qc_variant];
+        fn = reinterpret_cast<const void*>(V.fn[auto_ceiling ? 1 : 0]);
+        smem = V.smem;
+        threads = kQcThreads;
+        shots_per_cta = kQcThreads / V.t;   // one shot in flight per group
     } else if (use_groups) {
         fn = reinterpret_cast<const void*>(group_kernel_fn());
         smem = grp_smem_bytes(kGroupDC, kGroupDV);
         threads = 2 * kGrpThreads;
-        units = (shots + 1) / 2;   // two shots in flight per CTA
+        shots_per_cta = 2;   // two shots in flight per CTA
     } else if (use_slots) {
         const SlotVariant& S = kSlotVariants[code->slot_variant];
         fn = reinterpret_cast<const void*>(slot_kernel_for(code->slot_variant));
         smem = slot_smem_bytes(S.dc, S.dv, S.mp, S.np, per_qubit);
         threads = S.mp;
-        units = (shots + 1) / 2;
+        shots_per_cta = 2;
     } else {
         fn = reinterpret_cast<const void*>(kernel_for(code->variant, bp));
         smem = smem_bytes(code->DC, code->DV, code->Mp, code->Np, per_qubit);
         threads = code->Mp;
-        units = shots;
+        shots_per_cta = 1;
     }
     if (smem > (size_t)smem_optin)
         return fail(SAGMS_ERR_SIZE, "code needs %zu B of shared memory per CTA (limit %d)", smem, smem_optin);
@@ -589,6 +599,7 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     if (ce != cudaSuccess) return cuda_fail(ce, "occupancy query");
     if (per_sm < 1) return fail(SAGMS_ERR_SIZE, "kernel does not fit on an SM");
     if (plan.ctas_per_sm > 0) per_sm = std::min(per_sm, plan.ctas_per_sm);
+    const long long units = (shots + shots_per_cta - 1) / shots_per_cta;
     long long grid = std::min<long long>(units, (long long)per_sm * sms);
     if (plan.max_grid > 0) grid = std::min(grid, plan.max_grid);
     if (!use_qc && !use_groups && !use_slots) {
@@ -628,10 +639,10 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
         c.iters = a.iters + s0;
         c.trace = a.trace ? a.trace + s0 * (long long)(a.max_iter + 1) * code->n : nullptr;
         c.work = d_work + ci;
-        const long long g = std::min(grid, (cnt + 1) / 2);
+        const long long g = std::min(grid, (cnt + shots_per_cta - 1) / shots_per_cta);
         c.chunk_lg = plan.chunk_lg > 0 ? plan.chunk_lg : chunk_lg_for(cnt, g);
         if (use_qc)
-            qc_kernel_for(code->qc_variant, auto_ceiling)<<<(unsigned)g, threads, smem, stream>>>(c, code->d_colQ);
+            kQcVariants[code->qc_variant].fn[auto_ceiling ? 1 : 0]<<<(unsigned)g, threads, smem, stream>>>(c, code->d_colQ);
         else if (use_groups)
             group_kernel_fn()<<<(unsigned)g, threads, smem, stream>>>(c, glay);
         else

@@ -30,6 +30,12 @@ def _with(p, **kw):
 
 
 @pytest.fixture(scope="module")
+def dev_check():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.fixture(scope="module")
 def group_codes():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -157,3 +163,34 @@ def test_set_plan_rejects_unknown_bits(group_codes):
         with pytest.raises(_native.SagmsError):
             _native.sagms_set_plan(dc.handle, bad)
     _native.sagms_set_plan(dc.handle, KERNEL_QC | (1 << 16))
+
+
+@pytest.mark.parametrize("lw", [(63, 3), (127, 4), (255, 3), (255, 4), (255, 5), (255, 6), (255, 8), (511, 5)])
+def test_column_indexed_shapes_for_smaller_codes(dev_check, lw):
+    """Every compiled column-indexed shape (n from 126 to 1022, warp-sized groups up to four
+    256-thread groups) against the one-shot-per-CTA kernel, bit for bit, on mixed noise with
+    zero syndromes, negative priors and an odd shot count."""
+    c = I.gb_code(*lw)
+    _, syn, L0, _ = I.workload(c, [0.005, 0.02, 0.06], 2501, seed=lw[0] + lw[1])
+    syn = syn.copy()
+    L0 = L0.copy()
+    syn[::9] = 0
+    L0[4::13] = -L0[4::13]
+    for mode in ("ms", "sagms"):
+        p = PARAMS[mode]
+        assert _same(_decode_with_kernel(c, KERNEL_QC, syn, L0, p), _decode_with_kernel(c, KERNEL_GENERIC, syn, L0, p))
+    tr = _decode_with_kernel(c, KERNEL_GENERIC, syn[:16], L0[:16], PARAMS["sagms"], trace=True)["trace"]
+    tq = _decode_with_kernel(c, KERNEL_QC, syn[:16], L0[:16], PARAMS["sagms"], trace=True)["trace"]
+    assert np.array_equal(np.nan_to_num(tr, nan=7.0), np.nan_to_num(tq, nan=7.0))
+
+
+def test_small_truncated_code_oracle_parity(dev_check):
+    """A truncated GB(255, 5) (check degrees 10, 9, 1, 0) on the n <= 512 shape against the
+    FP64 oracle."""
+    c = _truncated_gb(255, 5)
+    dc = S.DeviceCode.from_code(c)
+    _native.sagms_set_plan(dc.handle, KERNEL_QC)
+    _, syn, L0, _ = I.workload(c, [0.01, 0.03], 600, seed=89)
+    G.compare(c, dc, syn, L0, PARAMS["sagms"])
+    assert _same(G.gpu_decode(dc, syn, L0, PARAMS["sagms"]),
+                 _decode_with_kernel(c, KERNEL_GENERIC, syn, L0, PARAMS["sagms"]))
