@@ -13,7 +13,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libsagms.so")
-SOURCES = [os.path.join(HERE, "csrc", f) for f in ("sagms.cu", "server.cu", "mc.cu")]
+SOURCES = [os.path.join(HERE, "csrc", f)
+           for f in ("kernels_qc.cu", "kernels_slots.cu", "kernels_generic.cu", "sagms.cu", "server.cu", "mc.cu")]
 DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in os.listdir(os.path.join(HERE, "csrc"))] + \
     [os.path.join(ROOT, "include", "sagms.h")]
 
@@ -35,16 +36,39 @@ def stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
+    """Compile every translation unit to an object in parallel, then link the library."""
     if not force and not stale():
         return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-I", os.path.join(ROOT, "include"), *extra, *SOURCES, "-o", tmp]
+    from concurrent.futures import ThreadPoolExecutor
+    tag = f".tmp{os.getpid()}"
+    flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
+             *extra]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-        print(" ".join(cmd), file=sys.stderr)
-    subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
+        flags.insert(0, "-Xptxas=-v")
+    objs = [os.path.join(HERE, "csrc", os.path.basename(src) + tag + ".o") for src in SOURCES]
+
+    def compile_one(args):
+        src, obj = args
+        cmd = [nvcc(), *flags, "-c", src, "-o", obj]
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        return subprocess.run(cmd, capture_output=True, text=True)
+
+    try:
+        with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+            results = list(ex.map(compile_one, zip(SOURCES, objs)))
+        for r in results:
+            sys.stderr.write(r.stdout + r.stderr)
+        failed = [src for src, r in zip(SOURCES, results) if r.returncode != 0]
+        if failed:
+            raise RuntimeError(f"nvcc failed for {', '.join(os.path.basename(f) for f in failed)}")
+        tmp = LIB + tag
+        subprocess.check_call([nvcc(), *ARCH, "-shared", *objs, "-o", tmp])
+        os.replace(tmp, LIB)
+    finally:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
     return LIB
 
 

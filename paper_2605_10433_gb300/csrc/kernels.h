@@ -1,0 +1,47 @@
+// The library's compiled decoder kernels and their shapes.  Each table is defined, with the
+// kernel instantiations it names, in a translation unit of its own (kernels_*.cu), so the
+// kernels compile in parallel; sagms.cu selects and launches them through these tables.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "decode_qc.cuh"
+
+namespace sagms_kernels {
+
+using sagms::DecodeArgs;
+
+// One shot per CTA (decode_kernel.cuh), for every mode: (padded check degree, padded qubit
+// degree), the first variant that covers a code's largest degrees.
+struct Variant { int dc, dv; };
+extern const Variant kVariants[];
+extern const int kNumVariants;
+using KernelFn = void (*)(const DecodeArgs);
+KernelFn generic_kernel(int variant, bool bp);
+
+// Two shot slots per CTA (decode_slots.cuh), MS family: (DC, DV, MP threads, NP qubit slots).
+using SlotFn = void (*)(const DecodeArgs, const sagms::SlotLayout);
+struct SlotVariant { int dc, dv, mp, np; SlotFn fn; };
+extern const SlotVariant kSlotVariants[];
+extern const int kNumSlotVariants;
+
+// Two 512-thread groups per CTA (decode_groups.cuh), MS family: one compiled shape, for codes
+// with more than 512 and at most 1024 checks, at most 2048 qubits and degrees up to (10, 5).
+constexpr int kGroupDC = 10, kGroupDV = 5;
+using GroupFn = void (*)(const DecodeArgs, const sagms::GroupLayout);
+GroupFn group_kernel_fn();
+
+// Column-indexed groups (decode_qc.cuh): one entry per compiled shape, listed by increasing
+// size; a code takes the first whose slot degrees cover it (DC = 2 DV), whose checks and
+// qubits it fills at least halfway, and whose slot structure it has.
+using QcFn = void (*)(const DecodeArgs, const uint32_t*);
+struct QcVariant {
+    int dc, dv, k, t, np;
+    QcFn fn[2];    // [auto ceiling]
+    size_t smem;
+};
+extern const QcVariant kQcVariants[];
+extern const int kNumQc;
+
+}  // namespace sagms_kernels

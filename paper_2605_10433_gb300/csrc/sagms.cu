@@ -18,13 +18,11 @@
 #include <vector>
 
 #include "../../include/sagms.h"
-#include "decode_kernel.cuh"
-#include "decode_slots.cuh"
-#include "decode_groups.cuh"
-#include "decode_qc.cuh"
 #include "internal.h"
+#include "kernels.h"
 
 using namespace sagms;
+using namespace sagms_kernels;
 
 namespace {
 
@@ -46,63 +44,9 @@ int cuda_fail(cudaError_t e, const char* what) {
                 cudaGetErrorString(e));
 }
 
-// Kernel variants: (padded check degree, padded qubit degree).  A code uses the first
-// variant whose degrees cover its largest check and qubit degree.
-struct Variant { int dc, dv; };
-constexpr Variant kVariants[] = {{4, 2}, {6, 3}, {8, 4}, {10, 5}, {12, 6}, {16, 8}, {32, 16}};
-constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
-
-using KernelFn = void (*)(const DecodeArgs);
-
-template <int DC, int DV>
-KernelFn pick(bool bp) { return bp ? decode_kernel<DC, DV, true> : decode_kernel<DC, DV, false>; }
-
-KernelFn kernel_for(int variant, bool bp) {
-    switch (variant) {
-        case 0: return pick<4, 2>(bp);
-        case 1: return pick<6, 3>(bp);
-        case 2: return pick<8, 4>(bp);
-        case 3: return pick<10, 5>(bp);
-        case 4: return pick<12, 6>(bp);
-        case 5: return pick<16, 8>(bp);
-        default: return pick<32, 16>(bp);
-    }
-}
-
 int round_up(int x, int k) { return (x + k - 1) / k * k; }
 
-// Two-group kernel (decode_groups.cuh): one compiled shape, for MS-family codes with more
-// than 512 and at most 1024 checks, at most 2048 qubits and degrees up to (10, 5).
-constexpr int kGroupDC = 10, kGroupDV = 5;
-using GroupFn = void (*)(const DecodeArgs, const GroupLayout);
-GroupFn group_kernel_fn() { return group_kernel<kGroupDC, kGroupDV>; }
 
-// Column-indexed group kernels (decode_qc.cuh): one entry per compiled shape, listed by
-// increasing size; a code takes the first whose slot degrees cover it (DC = 2 DV), whose
-// checks and qubits it fills at least halfway, and whose slot structure it has.  Four checks
-// per thread where the offsets and inputs fit in 128 registers (two checks per thread in
-// 1024-thread CTAs measured 5-15% slower at n = 2046).
-using QcFn = void (*)(const DecodeArgs, const uint32_t*);
-struct QcVariant {
-    int dc, dv, k, t, np;
-    QcFn fn[2];    // [auto ceiling]
-    size_t smem;
-};
-#define SAGMS_QC(DC, DV, K, T, NP)                                                               \
-    QcVariant {                                                                                   \
-        DC, DV, K, T, NP, {qc_kernel<QcShape<DC, DV, K, T, NP>, false>, qc_kernel<QcShape<DC, DV, K, T, NP>, true>}, \
-            QcShape<DC, DV, K, T, NP>::SMEM                                                       \
-    }
-const QcVariant kQcVariants[] = {
-    SAGMS_QC(6, 3, 2, 32, 128),                                                       // n <= 128
-    SAGMS_QC(8, 4, 4, 32, 256),                                                       // n <= 256
-    SAGMS_QC(6, 3, 4, 64, 512),  SAGMS_QC(8, 4, 4, 64, 512),  SAGMS_QC(10, 5, 4, 64, 512),
-    SAGMS_QC(12, 6, 4, 64, 512), SAGMS_QC(16, 8, 2, 128, 512),                        // n <= 512
-    SAGMS_QC(8, 4, 4, 128, 1024), SAGMS_QC(10, 5, 4, 128, 1024),                      // n <= 1024
-    SAGMS_QC(6, 3, 4, 256, 2048), SAGMS_QC(8, 4, 4, 256, 2048), SAGMS_QC(10, 5, 4, 256, 2048),
-};
-#undef SAGMS_QC
-constexpr int kNumQc = sizeof(kQcVariants) / sizeof(kQcVariants[0]);
 
 // colQ layout of a column-indexed shape: [K][DC][T], byte offset 4 * col of check
 // tg + k * T in slot j (4 * NP, the padding column, for padding).
@@ -169,28 +113,6 @@ int chunk_lg_for(long long shots, long long grid) {
     return lg;
 }
 
-// Two-slot MS-family kernels with compile-time layout: (DC, DV, MP threads, NP qubit slots).
-struct SlotVariant { int dc, dv, mp, np; };
-constexpr SlotVariant kSlotVariants[] = {
-    {6, 3, 64, 128},   {8, 4, 128, 256},  {6, 3, 256, 512},   {8, 4, 256, 512},  {10, 5, 256, 512},
-    {12, 6, 256, 512}, {16, 8, 256, 512}, {10, 5, 512, 1024}, {10, 5, 1024, 2048}};
-constexpr int kNumSlotVariants = sizeof(kSlotVariants) / sizeof(kSlotVariants[0]);
-
-using SlotFn = void (*)(const DecodeArgs, const SlotLayout);
-
-SlotFn slot_kernel_for(int v) {
-    switch (v) {
-        case 0: return slot_kernel<6, 3, 64, 128>;
-        case 1: return slot_kernel<8, 4, 128, 256>;
-        case 2: return slot_kernel<6, 3, 256, 512>;
-        case 3: return slot_kernel<8, 4, 256, 512>;
-        case 4: return slot_kernel<10, 5, 256, 512>;
-        case 5: return slot_kernel<12, 6, 256, 512>;
-        case 6: return slot_kernel<16, 8, 256, 512>;
-        case 7: return slot_kernel<10, 5, 512, 1024>;
-        default: return slot_kernel<10, 5, 1024, 2048>;
-    }
-}
 
 }  // namespace
 
@@ -580,12 +502,12 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
         shots_per_cta = 2;   // two shots in flight per CTA
     } else if (use_slots) {
         const SlotVariant& S = kSlotVariants[code->slot_variant];
-        fn = reinterpret_cast<const void*>(slot_kernel_for(code->slot_variant));
+        fn = reinterpret_cast<const void*>(kSlotVariants[code->slot_variant].fn);
         smem = slot_smem_bytes(S.dc, S.dv, S.mp, S.np, per_qubit);
         threads = S.mp;
         shots_per_cta = 2;
     } else {
-        fn = reinterpret_cast<const void*>(kernel_for(code->variant, bp));
+        fn = reinterpret_cast<const void*>(generic_kernel(code->variant, bp));
         smem = smem_bytes(code->DC, code->DV, code->Mp, code->Np, per_qubit);
         threads = code->Mp;
         shots_per_cta = 1;
@@ -603,7 +525,7 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     long long grid = std::min<long long>(units, (long long)per_sm * sms);
     if (plan.max_grid > 0) grid = std::min(grid, plan.max_grid);
     if (!use_qc && !use_groups && !use_slots) {
-        kernel_for(code->variant, bp)<<<(unsigned)grid, threads, smem, stream>>>(a);
+        generic_kernel(code->variant, bp)<<<(unsigned)grid, threads, smem, stream>>>(a);
         ce = cudaGetLastError();
         if (ce != cudaSuccess) return cuda_fail(ce, "decode launch");
         return SAGMS_OK;
@@ -646,7 +568,7 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
         else if (use_groups)
             group_kernel_fn()<<<(unsigned)g, threads, smem, stream>>>(c, glay);
         else
-            slot_kernel_for(code->slot_variant)<<<(unsigned)g, threads, smem, stream>>>(c, slay);
+            kSlotVariants[code->slot_variant].fn<<<(unsigned)g, threads, smem, stream>>>(c, slay);
     }
     ce = cudaGetLastError();
     if (own_work) cudaFreeAsync(d_work, stream);
