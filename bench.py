@@ -425,7 +425,8 @@ def main():
     if not args.no_extras:
         modes = {}
         for name, p in (("sms", S.Params(mode="sms", alpha=SMS_ALPHA, max_iter=MAX_ITER)),
-                        ("ms", S.Params(mode="ms", max_iter=MAX_ITER))):
+                        ("ms", S.Params(mode="ms", max_iter=MAX_ITER)),
+                        ("bp", S.Params(mode="bp", max_iter=MAX_ITER))):
             m_ms, _ = timed(p, 1, args.mode_steps)
             cv = conv.cpu().numpy()
             modes[name] = {"shots_per_s": shots * world * args.mode_steps / (m_ms / 1e3),
