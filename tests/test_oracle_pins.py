@@ -265,3 +265,33 @@ def test_non_finite_prior_marks_shot_invalid():
     assert list(r["iters"][[0, 2]]) == [-1, -1] and not r["conv"][[0, 2]].any()
     assert not r["err"][[0, 2]].any()
     assert r["iters"][1] >= 0
+
+
+@pytest.mark.parametrize("mode,alpha", [(oracle.MS, 1.0), (oracle.SMS, 0.5)])
+def test_exact_modes_are_invariant_under_relabelling(mode, alpha):
+    """Algorithm 1 does not depend on how checks, qubits or the edges within a check are
+    numbered.  MS in normalised units and SMS with a dyadic scale are exact in FP64, so a
+    relabelled code (rows and columns permuted, each row's edges in a new order) must give the
+    same decisions, convergence flags and iteration counts, mapped back: a mis-indexed edge,
+    a transposed operand or a row/column mix-up anywhere in the oracle breaks this."""
+    c = I.gb_code(127, 4)
+    err, syn, L0, _ = I.workload(c, [0.06], 300, seed=61, want_err=True)
+    r0 = oracle.decode_code(c, syn, L0.astype(np.float64), mode=mode, alpha=alpha, max_iter=30)
+    rng = np.random.default_rng(62)
+    rows = rng.permutation(c.m)        # old row i becomes row rows[i]
+    cols = rng.permutation(c.n)        # old column j becomes column cols[j]
+    new_rows = [None] * c.m
+    for i in range(c.m):
+        edges = cols[c.col_idx[c.row_ptr[i]:c.row_ptr[i + 1]]]
+        new_rows[rows[i]] = list(rng.permutation(edges))
+    rp = np.concatenate([[0], np.cumsum([len(r) for r in new_rows])]).astype(np.int32)
+    ci = np.concatenate([np.asarray(r, dtype=np.int32) for r in new_rows])
+    c2 = I.Code(m=c.m, n=c.n, row_ptr=rp, col_idx=ci, name="relabelled")
+    s = I.unpack_bits(syn, c.m)
+    s2 = np.zeros_like(s)
+    s2[:, rows] = s
+    r1 = oracle.decode_code(c2, I.pack_bits(s2), L0.astype(np.float64), mode=mode, alpha=alpha, max_iter=30)
+    e1 = I.unpack_bits(r1["err"], c.n)[:, cols]
+    assert np.array_equal(e1, I.unpack_bits(r0["err"], c.n))
+    assert np.array_equal(r1["conv"], r0["conv"]) and np.array_equal(r1["iters"], r0["iters"])
+    assert 0 < r0["conv"].sum() < 300          # both outcomes occur
