@@ -51,8 +51,8 @@ struct DecodeArgs {
     uint8_t* conv;
     int32_t* iters;
     float* trace;
-    int* work;     // two-slot kernel: zero-initialised chunk counter (dynamic scheduling), or null
-    int chunk_lg;  // two-slot kernel: log2 of the shots per claimed chunk
+    int* work;     // continuous-batching kernels: zero-initialised chunk counter, or null (static)
+    int chunk_lg;  // continuous-batching kernels: log2 of the shots per claimed chunk
 };
 
 enum { kModeMS = 0, kModeSMS = 1, kModeSAGMS = 2, kModeBP = 3 };

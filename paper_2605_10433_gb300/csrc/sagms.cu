@@ -98,14 +98,14 @@ uint32_t pack_plan(const Plan& p) {
     return (uint32_t)(p.kernel & 7) | ((uint32_t)(p.ctas_per_sm & 0xff) << 8) | ((uint32_t)(p.chunk_lg & 0xf) << 16);
 }
 
-// Largest launch of the two-slot kernel: its per-shot indexing (shot * words per pattern)
+// Largest launch of a continuous-batching kernel: its per-shot indexing (shot * words per pattern)
 // stays within 32-bit integers.
 long long max_slot_chunk(int m, int n) {
     const long long words = std::max((m + 31) / 32, (n + 31) / 32);
     return 0x7fffffffLL / std::max(1LL, words);
 }
 
-// Shots per claimed chunk of the two-slot kernel (log2): about eight chunks per CTA, at
+// Shots per claimed chunk of the continuous-batching kernels (log2): about eight chunks per CTA, at
 // least 2 shots (the claim ring needs a chunk of slack per refill round) and at most 16.
 int chunk_lg_for(long long shots, long long grid) {
     int lg = 1;

@@ -8,7 +8,7 @@
 // in, decode, copy out, completion event.  In continuous mode several requests are on the
 // GPU at once and each decode's grid is capped at about one CTA per `shots_per_cta` shots,
 // so its CTAs retire as they finish and the CTAs of newer requests take the freed SMs
-// (inside a CTA the two-slot kernel refills its slots shot by shot).  Plain mode is the
+// (inside a CTA the continuous-batching kernels refill their slots or groups shot by shot).  Plain mode is the
 // baseline the loop is measured against: one request at a time on one stream, each decode
 // with the full persistent grid.
 #include <cuda_runtime.h>
