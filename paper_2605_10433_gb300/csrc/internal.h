@@ -2,12 +2,22 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 
 #include "../../include/sagms.h"
 
 namespace sagms_internal {
+
+// NVTX range over a host-side step (decode launch, serving request, Monte Carlo batch): shows
+// up in Nsight timelines; costs a function-pointer test when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // How a decode is launched.  kernel: 0 automatic, 1 one shot per CTA, 2 two-slot, 3 two-group,
 // 4 two-group with column-indexed messages;

@@ -420,6 +420,7 @@ int sagms_mc_run(const sagms_code* code, const sagms_params* params, uint64_t se
     rc = ce == cudaSuccess ? SAGMS_OK : sagms_internal::cuda_error(ce, "Monte Carlo buffers");
     while (rc == SAGMS_OK && counts->failures < target_failures && counts->shots < max_shots) {
         const int64_t b = std::min(B, max_shots - counts->shots);
+        const sagms_internal::NvtxRange nvtx("sagms_mc_batch");
         sagms_mc_counts h = {0, 0, 0, 0, 0};
         ce = cudaMemsetAsync(d_counts, 0, sizeof(sagms_mc_counts), st);
         if (ce != cudaSuccess) { rc = sagms_internal::cuda_error(ce, "counter reset"); break; }

@@ -443,6 +443,7 @@ namespace {
 int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, const uint32_t* d_syn,
                   const float* d_L0, uint32_t* d_err, uint8_t* d_conv, int32_t* d_iters, float* d_trace,
                   cudaStream_t stream, const Plan* plan_override = nullptr) {
+    const sagms_internal::NvtxRange nvtx("sagms_decode");
     if (!code) return fail(SAGMS_ERR_ARG, "code is NULL");
     int rc = sagms_check_params(p);
     if (rc != SAGMS_OK) return rc;
@@ -630,6 +631,7 @@ int sagms_decode_trace(const sagms_code* code, const sagms_params* params, int64
 
 int sagms_decode_host(const sagms_code* code, const sagms_params* params, int64_t shots, const uint32_t* h_syn,
                       const float* h_L0, uint32_t* h_err, uint8_t* h_conv, int32_t* h_iters) {
+    const sagms_internal::NvtxRange nvtx("sagms_decode_host");
     if (!code) return fail(SAGMS_ERR_ARG, "code is NULL");
     int rc = sagms_check_params(params);
     if (rc != SAGMS_OK) return rc;

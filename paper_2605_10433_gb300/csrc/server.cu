@@ -141,6 +141,7 @@ size_t request_bytes(const CodeEntry& c, int64_t shots, bool per_qubit) {
 }  // namespace
 
 void sagms_server::launch_request(Request& r, int slot) {
+    const sagms_internal::NvtxRange nvtx("sagms_server_request");
     const CodeEntry& c = codes[r.code_id];
     const bool per_qubit = (c.params.flags & SAGMS_FLAG_L0_PER_QUBIT) != 0;
     const size_t mw = (c.m + 31) / 32, nw = (c.n + 31) / 32;
