@@ -30,3 +30,40 @@ def sms_alpha_sweep(code, alphas, q, seed=1, target_failures=500, max_shots=20_0
     d = code.dc_max if dc is None else dc
     return {"q": q, "L0": prior, "rows": rows, "best_alpha": best["alpha"],
             "alpha_star": _native.sagms_alpha_star(abs(prior), d)}
+
+
+def _key(code_name, params, q, L0, seed):
+    return {"code": code_name, "mode": params.mode, "alpha": params.alpha, "alpha_min": params.alpha_min,
+            "alpha_max": params.alpha_max, "eta_unsat": params.eta_unsat, "max_iter": params.max_iter,
+            "flags": params.flags, "q": float(q), "L0": float(L0), "seed": int(seed)}
+
+
+def mc_run_checkpointed(code, code_name, params, seed, q, checkpoint, L0=None, target_failures=500,
+                        max_shots=20_000_000, batch=1 << 22):
+    """The Monte Carlo protocol of one noise level with an append-only JSONL checkpoint: after
+    every batch one line records the run's identity (code name, parameters, q, L0, seed) and
+    its cumulative counts.  Calling again with the same identity resumes from the last line:
+    frames are indexed by a counter-based generator, so the continued run is the same frame
+    sequence an uninterrupted one would draw.  Returns the counts."""
+    import json
+    import os
+    from . import llr, mc_run
+    prior = llr(q) if L0 is None else float(L0)
+    key = _key(code_name, params, q, prior, seed)
+    counts = None
+    if os.path.exists(checkpoint):
+        with open(checkpoint) as f:
+            for line in f:
+                line = line.strip()
+                if not line:
+                    continue
+                rec = json.loads(line)
+                if all(rec.get(k) == v for k, v in key.items()):
+                    counts = {k: rec[k] for k in ("shots", "failures", "not_converged", "logical", "iters_sum")}
+    counts = counts or {"shots": 0, "failures": 0, "not_converged": 0, "logical": 0, "iters_sum": 0}
+    while counts["failures"] < target_failures and counts["shots"] < max_shots:
+        counts = mc_run(code, params, seed, q, L0=prior, target_failures=target_failures,
+                        max_shots=min(counts["shots"] + batch, max_shots), batch=batch, counts=counts)
+        with open(checkpoint, "a") as f:
+            f.write(json.dumps({**key, **counts}) + "\n")
+    return counts

@@ -224,3 +224,51 @@ def test_sms_alpha_sweep_rows_are_independent_runs(dev):
         assert (row["failures"], row["shots"], row["logical"]) == (r["failures"], r["shots"], r["logical"])
     assert sw["best_alpha"] == min(sw["rows"], key=lambda x: (x["fer"], x["alpha"]))["alpha"]
     assert sw["alpha_star"] == pytest.approx(oracle.alpha_star(np.log(0.95 / 0.05), 6), rel=1e-12)
+
+
+def test_checkpointed_run_resumes_from_the_last_record(tmp_path, monkeypatch):
+    """Host logic of the JSONL checkpoint (CPU, with a stand-in for the GPU run that draws
+    a fixed number of failures per frame index): an interrupted run resumes at the last
+    recorded frame and ends with the counts of an uninterrupted one; records of other runs
+    in the same file are ignored."""
+    import json
+    import paper_2605_10433_gb300 as pkg
+    from paper_2605_10433_gb300 import sweep
+
+    def fake_run(code, params, seed, q, L0=None, target_failures=0, max_shots=0, batch=0, counts=None):
+        c = dict(counts)
+        while c["failures"] < target_failures and c["shots"] < max_shots:
+            b = min(batch, max_shots - c["shots"])
+            c["failures"] += sum(1 for t in range(c["shots"], c["shots"] + b) if (t * 7 + seed) % 97 == 0)
+            c["shots"] += b
+            c["iters_sum"] += 2 * b
+        return c
+
+    monkeypatch.setattr(pkg, "mc_run", fake_run)
+    p = S.Params(mode="sagms")
+    ck = str(tmp_path / "ck.jsonl")
+    with open(ck, "w") as f:   # a record of another run (different seed) in the same file
+        f.write(json.dumps({**sweep._key("GB(63,3)", p, 0.01, S.llr(0.01), 99), "shots": 5, "failures": 5,
+                            "not_converged": 5, "logical": 0, "iters_sum": 1}) + "\n")
+    part = sweep.mc_run_checkpointed(None, "GB(63,3)", p, 3, 0.01, ck, target_failures=10**9, max_shots=3000, batch=1000)
+    assert part["shots"] == 3000
+    full = sweep.mc_run_checkpointed(None, "GB(63,3)", p, 3, 0.01, ck, target_failures=10**9, max_shots=10000, batch=1000)
+    ref = fake_run(None, p, 3, 0.01, target_failures=10**9, max_shots=10000, batch=1000,
+                   counts={"shots": 0, "failures": 0, "not_converged": 0, "logical": 0, "iters_sum": 0})
+    assert full == ref
+    lines = [json.loads(x) for x in open(ck)]
+    assert len(lines) == 1 + 10 and lines[-1]["shots"] == 10000 and lines[0]["seed"] == 99
+
+
+@gpu
+def test_checkpointed_run_on_the_gpu_equals_one_run(dev, tmp_path):
+    from paper_2605_10433_gb300 import sweep
+    c = I.gb_code(127, 4)
+    dc = S.DeviceCode.from_code(c)
+    dc.set_logicals(S.x_logicals(c))
+    p = S.Params(mode="sagms", max_iter=40)
+    ck = str(tmp_path / "ck.jsonl")
+    sweep.mc_run_checkpointed(dc, "GB(127,4)", p, 5, 0.04, ck, target_failures=10**9, max_shots=4096, batch=2048)
+    got = sweep.mc_run_checkpointed(dc, "GB(127,4)", p, 5, 0.04, ck, target_failures=10**9, max_shots=10240,
+                                    batch=2048)
+    assert got == S.mc_run(dc, p, 5, 0.04, target_failures=10**9, max_shots=10240, batch=10240)
