@@ -48,6 +48,10 @@ struct QcShape {
     static constexpr size_t GROUP = (size_t)(1 + DV) * ROW;
     static constexpr size_t MISC = (size_t)NG * GROUP;
     static constexpr size_t SMEM = MISC + (size_t)NG * kQcMisc + 32 * 4;
+    // per-qubit priors (shared by the groups) and their negativity bits, after the rest
+    static constexpr size_t PQS = SMEM;
+    static constexpr size_t NEGW = PQS + (size_t)(NP + 4) * 4;
+    static constexpr size_t SMEM_PQ = NEGW + (size_t)(NP / 32) * 4;
     static_assert(DC == 2 * DV && (K == 2 || K == 4) && NG * T == kQcThreads, "shape");
     static_assert(NP % (2 * T) == 0 && MC <= 1024 && (T == 32 || NG <= 15), "layout");
 };
@@ -65,10 +69,11 @@ __device__ __forceinline__ void qc_sync(int g) {
 __device__ __forceinline__ uint32_t qc_byte(uint32_t x, int k) { return (x >> (8 * k)) & 0xffu; }
 
 // GC: the group index when it is fixed at compile time (one copy of the loop per group, every
-// group address an immediate), or -1 (one copy for all groups, g at run time).
-template <class S, bool AUTO, int GC>
+// group address an immediate), or -1 (one copy for all groups, g at run time).  PQ: one prior
+// per qubit shared by all shots (SAGMS_FLAG_L0_PER_QUBIT; LLR units), pq_ok = all finite.
+template <class S, bool AUTO, bool PQ, int GC>
 __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* smem, const int tg, const int g_rt,
-                                         const uint32_t (&off)[S::K][S::DC], const uint32_t degs) {
+                                         const uint32_t (&off)[S::K][S::DC], const uint32_t degs, const bool pq_ok) {
     constexpr int DC = S::DC, DV = S::DV, K = S::K, T = S::T, NP = S::NP;
     const int g = GC >= 0 ? GC : g_rt;
     const size_t PO = (size_t)g * S::GROUP;
@@ -89,6 +94,10 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
     const uint32_t* flipw = reinterpret_cast<const uint32_t*>(misc + S::NG * kQcMisc);
     // o: the column's byte offset biased by the group's base
     auto Pat = [&](uint32_t o) -> float& { return *reinterpret_cast<float*>(smem + o); };
+    // per-qubit prior of a column, from the same biased offset
+    auto PQat = [&](uint32_t o) -> float { return *reinterpret_cast<const float*>(smem + S::PQS + o - PO); };
+    const float* PQs = reinterpret_cast<const float*>(smem + S::PQS);
+    const uint32_t* negw = reinterpret_cast<const uint32_t*>(smem + S::NEGW);
     auto Cat = [&](int j, uint32_t o) -> float& {
         return *reinterpret_cast<float*>(smem + o + (size_t)(1 + j % DV) * S::ROW);
     };
@@ -121,7 +130,7 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
     auto prefetch = [&](int b, int s) {
         if (tg < 32 && s < nshots) {
             if (lane < mw) cp_async4(pfsyn + b * 32 + lane, a.syn + s * mw + lane);
-            if (lane == 0) cp_async4(pfl0 + b, a.L0 + s);
+            if (lane == 0 && !PQ) cp_async4(pfl0 + b, a.L0 + s);
             cp_async_commit();
         }
     };
@@ -196,25 +205,26 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
                 pbuf ^= 1;
                 consumed = b;
                 const uint32_t* row = pfsyn + b * 32;
-                const float l0 = pfl0[b];
+                const float l0 = PQ ? 0.0f : pfl0[b];
                 const uint32_t word = (lane < mw) ? row[lane] : 0u;
-                if (!isfinite(l0)) {
+                if (!(PQ ? pq_ok : isfinite(l0))) {
                     for (int w = tg; w < nw; w += T) a.err[s * nw + w] = 0u;
                     if (tg == 0) { a.conv[s] = 0; a.iters[s] = -1; }
                 } else {
-                    const float pi = (l0 > 0.0f) ? 1.0f : ((l0 < 0.0f) ? -1.0f : 0.0f);
-                    const bool flipped = pi < 0.0f;
+                    const float pi = PQ ? 0.0f : ((l0 > 0.0f) ? 1.0f : ((l0 < 0.0f) ? -1.0f : 0.0f));
+                    const bool flipped = PQ || pi < 0.0f;
                     // First check (l = 0), Eqs. 1 and 6: popcount of s XOR flip.
                     const uint32_t flip_lane = (flipped && lane < mw) ? flipw[lane] : 0u;
                     const int c0 = __reduce_add_sync(0xffffffffu, (int)__popc(word ^ flip_lane));
                     if (tracing) {
                         float* tr = a.trace + (size_t)s * (size_t)(a.max_iter + 1) * (size_t)n;
-                        for (int c = tg; c < n; c += T) tr[c] = pi;
+                        for (int c = tg; c < n; c += T) tr[c] = PQ ? PQs[c] : pi;
                     }
                     if ((c0 == 0 && early) || a.max_iter == 0) {
                         for (int w = tg; w < nw; w += T)
                             a.err[s * nw + w] =
-                                (pi < 0.0f) ? ((w == nw - 1 && (n & 31)) ? ((1u << (n & 31)) - 1u) : 0xffffffffu) : 0u;
+                                PQ ? negw[w]
+                                   : ((pi < 0.0f) ? ((w == nw - 1 && (n & 31)) ? ((1u << (n & 31)) - 1u) : 0xffffffffu) : 0u);
                         if (tg == 0) { a.conv[s] = (c0 == 0) ? 1 : 0; a.iters[s] = 0; }
                     } else {
                         // Round 1 runs now on the priors themselves (Eq. 2 at l = 1).
@@ -234,7 +244,8 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
                             const int i = tg + k * T;
                             const uint32_t bit = (i < m) ? ((row[i >> 5] >> (i & 31)) & 1u) : 0u;
                             sbits |= bit << k;
-                            stb |= (bit ^ (flipped ? (qc_byte(degs, k) & 1u) : 0u)) << k;
+                            const uint32_t flip = PQ ? ((flipw[i >> 5] >> (i & 31)) & 1u) : (qc_byte(degs, k) & 1u);
+                            stb |= (bit ^ (flipped ? flip : 0u)) << k;
                         }
                     }
                 }
@@ -254,7 +265,7 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
 #pragma unroll
                 for (int k = 0; k < K; ++k) g[k] = (a.mode == kModeSMS) ? a.alpha : 1.0f;
             }
-            if (fresh) {
+            if (fresh && !PQ) {
                 // A3 on round-1 inputs: every real edge carries the prior s, padded slots +inf.
                 // The minimum and second minimum of |v| are |s| (a check with one edge has no
                 // second: +inf), the parity is the syndrome bit XOR the sign of s once per
@@ -272,13 +283,22 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
                     for (int j = 0; j < DC; ++j) Cat(j, off[k][j]) = d;
                 }
             } else {
+                if (PQ && fresh) {
+                    // round-1 inputs are the qubits' own priors (+inf on padded slots)
+#pragma unroll
+                    for (int p = 0; p < K / 2; ++p)
+#pragma unroll
+                        for (int j = 0; j < DC; ++j) v[p][j] = make_float2(PQat(off[2 * p][j]), PQat(off[2 * p + 1][j]));
+                }
 #pragma unroll
                 for (int p = 0; p < K / 2; ++p) {
                     // A3 check-node update for checks 2p and 2p + 1 (C holds negated
-                    // messages: P - L = P + D)
+                    // messages: P - L = P + D; a fresh shot has no old messages)
+                    if (!(PQ && fresh)) {
 #pragma unroll
-                    for (int j = 0; j < DC; ++j)
-                        v[p][j] = add2(v[p][j], make_float2(Cat(j, off[2 * p][j]), Cat(j, off[2 * p + 1][j])));
+                        for (int j = 0; j < DC; ++j)
+                            v[p][j] = add2(v[p][j], make_float2(Cat(j, off[2 * p][j]), Cat(j, off[2 * p + 1][j])));
+                    }
                     uint32_t par0 = ((sbits >> (2 * p)) & 1u) << 31, par1 = ((sbits >> (2 * p + 1)) & 1u) << 31;
 #pragma unroll
                     for (int j = 0; j < DC; j += 2) {
@@ -331,6 +351,10 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
 #pragma unroll
             for (int h = 0; h < NP / (2 * T); ++h) {
                 float2 acc = npr;
+                if (PQ) {
+                    const float2 pq = *reinterpret_cast<const float2*>(smem + S::PQS + (size_t)tg * 8 + (size_t)h * 8 * T);
+                    acc = make_float2(-pq.x, -pq.y);
+                }
 #pragma unroll
                 for (int q = 0; q < DV; ++q)
                     acc = add2(acc, *reinterpret_cast<const float2*>(vbase + (size_t)(1 + q) * S::ROW + (size_t)h * 8 * T));
@@ -346,7 +370,7 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
 // colQ: [K][DC][T] u32, byte offset 4 * col of check tg + kT in slot j (S::PAD for a padded
 // slot or a check past m).  AUTO: the gain ceiling of each shot comes from its prior
 // (SAGMS_FLAG_AUTO_CEILING), a separate instantiation so the default one carries no trace of it.
-template <class S, bool AUTO>
+template <class S, bool AUTO, bool PQ>
 __global__ void __launch_bounds__(kQcThreads, S::K * S::DC <= 16 ? 2 : 1)
 qc_kernel(const DecodeArgs a, const uint32_t* __restrict__ colQ) {
     constexpr int DC = S::DC, K = S::K, T = S::T;
@@ -376,23 +400,50 @@ qc_kernel(const DecodeArgs a, const uint32_t* __restrict__ colQ) {
         int* misc = reinterpret_cast<int*>(smem + S::MISC);
         for (int k = t; k < S::NG * kQcMisc / 4; k += kQcThreads) misc[k] = 0;
     }
+    int pq_ok = 1;
+    if constexpr (PQ) {
+        // per-qubit priors (LLR units), +inf past n; all finite or every shot is invalid
+        float* pqs = reinterpret_cast<float*>(smem + S::PQS);
+        for (int c = t; c < S::NP + 4; c += kQcThreads) {
+            const float v = (c < a.n) ? __ldg(a.L0 + c) : inf;
+            pqs[c] = v;
+            if (c < a.n) pq_ok &= isfinite(v) ? 1 : 0;
+        }
+    }
     __syncthreads();
     if (t < S::NG) *reinterpret_cast<float*>(smem + (size_t)t * S::GROUP + S::PAD) = inf;
-    // First residual bits under a negative prior: a check's degree parity.
+    // First residual bits under the priors' signs: a check's degree parity under a negative
+    // per-shot prior, the parity of its negative priors with per-qubit priors.
     uint32_t* flipw = reinterpret_cast<uint32_t*>(smem + S::MISC + S::NG * kQcMisc);
     if (t < T) {
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const uint32_t w = __ballot_sync(0xffffffffu, qc_byte(degs, k) & 1u);
+            uint32_t f = qc_byte(degs, k) & 1u;
+            if constexpr (PQ) {
+                f = 0u;
+#pragma unroll
+                for (int j = 0; j < DC; ++j)   // group 0: offsets are the plain column offsets
+                    f ^= __float_as_uint(*reinterpret_cast<const float*>(smem + S::PQS + off[k][j])) >> 31;
+            }
+            const uint32_t w = __ballot_sync(0xffffffffu, f);
             if ((t & 31) == 0) flipw[(t + k * T) >> 5] = w;
         }
     }
-    __syncthreads();
+    if constexpr (PQ) {
+        // [L0_c < 0]: the decision of a shot stopped at its first check
+        uint32_t* negw = reinterpret_cast<uint32_t*>(smem + S::NEGW);
+        const float* pqs = reinterpret_cast<const float*>(smem + S::PQS);
+        for (int c = t; c < S::NP; c += kQcThreads) {
+            const uint32_t w = __ballot_sync(0xffffffffu, (c < a.n) && (__float_as_uint(pqs[c]) >> 31));
+            if ((t & 31) == 0) negw[c >> 5] = w;
+        }
+    }
+    pq_ok = __syncthreads_and(pq_ok);
     if constexpr (S::NG == 2) {
-        if (g == 0) qc_group<S, AUTO, 0>(a, smem, tg, g, off, degs);
-        else qc_group<S, AUTO, 1>(a, smem, tg, g, off, degs);
+        if (g == 0) qc_group<S, AUTO, PQ, 0>(a, smem, tg, g, off, degs, pq_ok != 0);
+        else qc_group<S, AUTO, PQ, 1>(a, smem, tg, g, off, degs, pq_ok != 0);
     } else {
-        qc_group<S, AUTO, -1>(a, smem, tg, g, off, degs);
+        qc_group<S, AUTO, PQ, -1>(a, smem, tg, g, off, degs, pq_ok != 0);
     }
 }
 

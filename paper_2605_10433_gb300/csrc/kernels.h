@@ -38,8 +38,8 @@ GroupFn group_kernel_fn();
 using QcFn = void (*)(const DecodeArgs, const uint32_t*);
 struct QcVariant {
     int dc, dv, k, t, np;
-    QcFn fn[2];    // [auto ceiling]
-    size_t smem;
+    QcFn fn[3];      // per-shot priors, per-shot priors with the automatic ceiling, per-qubit priors
+    size_t smem[3];  // shared memory of each
 };
 extern const QcVariant kQcVariants[];
 extern const int kNumQc;

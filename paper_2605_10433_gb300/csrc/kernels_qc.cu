@@ -1,5 +1,5 @@
-// Instantiations of the column-indexed group kernels (decode_qc.cuh), one per shape, each with
-// and without the automatic gain ceiling.  Four checks per thread where the offsets and inputs
+// Instantiations of the column-indexed group kernels (decode_qc.cuh), three per shape: per-shot
+// priors, per-shot priors with the automatic gain ceiling, and per-qubit priors.  Four checks per thread where the offsets and inputs
 // fit in 128 registers (two checks per thread in 1024-thread CTAs measured 5-15% slower at
 // n = 2046).
 #include "kernels.h"
@@ -9,9 +9,11 @@ namespace sagms_kernels {
 #define SAGMS_QC(DC, DV, K, T, NP)                                                                     \
     QcVariant {                                                                                         \
         DC, DV, K, T, NP,                                                                               \
-            {sagms::qc_kernel<sagms::QcShape<DC, DV, K, T, NP>, false>,                                 \
-             sagms::qc_kernel<sagms::QcShape<DC, DV, K, T, NP>, true>},                                 \
-            sagms::QcShape<DC, DV, K, T, NP>::SMEM                                                      \
+            {sagms::qc_kernel<sagms::QcShape<DC, DV, K, T, NP>, false, false>,                          \
+             sagms::qc_kernel<sagms::QcShape<DC, DV, K, T, NP>, true, false>,                           \
+             sagms::qc_kernel<sagms::QcShape<DC, DV, K, T, NP>, false, true>},                          \
+            {sagms::QcShape<DC, DV, K, T, NP>::SMEM, sagms::QcShape<DC, DV, K, T, NP>::SMEM,            \
+             sagms::QcShape<DC, DV, K, T, NP>::SMEM_PQ}                                                 \
     }
 const QcVariant kQcVariants[] = {
     SAGMS_QC(6, 3, 2, 32, 128),                                                       // n <= 128

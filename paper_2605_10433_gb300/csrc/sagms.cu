@@ -475,7 +475,8 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     // that does (two-group, two-slot, one-shot-per-CTA).
     const bool msfam_fast = !bp && !(p->flags & SAGMS_FLAG_GENERIC_KERNEL);
     const bool auto_ceiling = (p->flags & SAGMS_FLAG_AUTO_CEILING) != 0;
-    const bool use_qc = msfam_fast && code->qc_variant >= 0 && !per_qubit && (plan.kernel == 0 || plan.kernel == 4);
+    const bool use_qc = msfam_fast && code->qc_variant >= 0 && (plan.kernel == 0 || plan.kernel == 4);
+    const int qc_form = per_qubit ? 2 : (auto_ceiling ? 1 : 0);   // which instantiation
     const bool use_groups = !use_qc && msfam_fast && code->groups && !per_qubit &&
                             (plan.kernel == 0 || plan.kernel >= 3);
     const bool use_slots = !use_qc && !use_groups && msfam_fast && code->slot_variant >= 0 && plan.kernel != 1;
@@ -492,8 +493,8 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     int shots_per_cta;   // shots one CTA decodes at a time
     if (use_qc) {
         const QcVariant& V = kQcVariants[code->qc_variant];
-        fn = reinterpret_cast<const void*>(V.fn[auto_ceiling ? 1 : 0]);
-        smem = V.smem;
+        fn = reinterpret_cast<const void*>(V.fn[qc_form]);
+        smem = V.smem[qc_form];
         threads = kQcThreads;
         shots_per_cta = kQcThreads / V.t;   // one shot in flight per group
     } else if (use_groups) {
@@ -565,7 +566,7 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
         const long long g = std::min(grid, (cnt + shots_per_cta - 1) / shots_per_cta);
         c.chunk_lg = plan.chunk_lg > 0 ? plan.chunk_lg : chunk_lg_for(cnt, g);
         if (use_qc)
-            kQcVariants[code->qc_variant].fn[auto_ceiling ? 1 : 0]<<<(unsigned)g, threads, smem, stream>>>(c, code->d_colQ);
+            kQcVariants[code->qc_variant].fn[qc_form]<<<(unsigned)g, threads, smem, stream>>>(c, code->d_colQ);
         else if (use_groups)
             group_kernel_fn()<<<(unsigned)g, threads, smem, stream>>>(c, glay);
         else
@@ -767,7 +768,7 @@ int sagms_autotune(const sagms_code* code, const sagms_params* params, int64_t s
     std::vector<Plan> cands;
     const bool slots_ok = params->mode != SAGMS_BP && code->slot_variant >= 0;
     const bool groups_ok = params->mode != SAGMS_BP && code->groups && !(params->flags & SAGMS_FLAG_L0_PER_QUBIT);
-    const bool qc_ok = params->mode != SAGMS_BP && code->qc_variant >= 0 && !(params->flags & SAGMS_FLAG_L0_PER_QUBIT);
+    const bool qc_ok = params->mode != SAGMS_BP && code->qc_variant >= 0;
     for (int kernel : {4, 3, 2, 1}) {
         if (kernel == 2 && !slots_ok) continue;
         if (kernel == 3 && !groups_ok) continue;

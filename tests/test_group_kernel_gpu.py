@@ -146,8 +146,8 @@ def test_group_kernel_oracle_parity(group_codes, key, kernel):
 
 
 def test_group_kernel_falls_back_for_per_qubit_priors(group_codes):
-    """Per-qubit priors are not a two-group shape: a two-group plan falls back to the
-    two-slot kernel, with identical results."""
+    """Per-qubit priors on GB(1023, 5): the column-indexed kernel runs them itself; the
+    two-group kernel's plan falls back to the two-slot kernel.  Identical results."""
     c = group_codes[(1023, 5)]
     _, syn = I.sample(c, 0.02, 500, seed=8)
     L0q = I.llr_prior(np.random.default_rng(3).uniform(0.005, 0.05, size=c.n)).astype(np.float32)
@@ -155,6 +155,40 @@ def test_group_kernel_falls_back_for_per_qubit_priors(group_codes):
     for kernel in (KERNEL_GROUPS, KERNEL_QC):
         assert _same(_decode_with_kernel(c, kernel, syn, L0q, p),
                      _decode_with_kernel(c, KERNEL_GENERIC, syn, L0q, p))
+
+
+@pytest.mark.parametrize("lw", [(63, 3), (127, 4), (255, 5), (255, 8), (511, 5), (1023, 5)])
+def test_column_indexed_per_qubit_priors(dev_check, lw):
+    """Per-qubit priors (LLR units, some negative) on every column-indexed shape: bitwise
+    equal to the one-shot-per-CTA kernel, including zero syndromes (decision [L0 < 0]) and
+    traces; a non-finite prior invalidates every shot."""
+    c = I.gb_code(*lw)
+    rng = np.random.default_rng(lw[0])
+    _, syn = I.sample(c, 0.03, 1201, seed=lw[0] + 1)
+    syn = syn.copy()
+    syn[::11] = 0
+    L0q = I.llr_prior(rng.uniform(0.005, 0.08, size=c.n)).astype(np.float32)
+    L0q[rng.choice(c.n, size=max(1, c.n // 50), replace=False)] *= -1.0
+    for mode in ("ms", "sagms"):
+        p = _with(PARAMS[mode], flags=S.FLAG_L0_PER_QUBIT)
+        assert _same(_decode_with_kernel(c, KERNEL_QC, syn, L0q, p), _decode_with_kernel(c, KERNEL_GENERIC, syn, L0q, p))
+    p = _with(PARAMS["sagms"], flags=S.FLAG_L0_PER_QUBIT)
+    tr = _decode_with_kernel(c, KERNEL_GENERIC, syn[:12], L0q, p, trace=True)["trace"]
+    tq = _decode_with_kernel(c, KERNEL_QC, syn[:12], L0q, p, trace=True)["trace"]
+    assert np.array_equal(np.nan_to_num(tr, nan=7.0), np.nan_to_num(tq, nan=7.0))
+    bad = L0q.copy()
+    bad[c.n // 2] = np.nan
+    g = _decode_with_kernel(c, KERNEL_QC, syn[:40], bad, p)
+    assert (g["iters"] == -1).all() and (g["conv"] == 0).all() and not g["err"].any()
+
+
+def test_column_indexed_per_qubit_oracle_parity(dev_check):
+    c = I.gb_code(255, 5)
+    dc = S.DeviceCode.from_code(c)
+    _native.sagms_set_plan(dc.handle, KERNEL_QC)
+    _, syn = I.sample(c, 0.02, 500, seed=19)
+    L0q = I.llr_prior(np.random.default_rng(19).uniform(0.005, 0.05, size=c.n)).astype(np.float32)
+    G.compare(c, dc, syn, L0q, _with(PARAMS["sagms"], flags=S.FLAG_L0_PER_QUBIT))
 
 
 def test_set_plan_rejects_unknown_bits(group_codes):
