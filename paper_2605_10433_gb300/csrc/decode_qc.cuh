@@ -371,7 +371,7 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
 // slot or a check past m).  AUTO: the gain ceiling of each shot comes from its prior
 // (SAGMS_FLAG_AUTO_CEILING), a separate instantiation so the default one carries no trace of it.
 template <class S, bool AUTO, bool PQ>
-__global__ void __launch_bounds__(kQcThreads, S::K * S::DC <= 16 ? 2 : 1)
+__global__ void __launch_bounds__(kQcThreads, S::K * S::DC <= 12 ? 2 : 1)
 qc_kernel(const DecodeArgs a, const uint32_t* __restrict__ colQ) {
     constexpr int DC = S::DC, K = S::K, T = S::T;
     extern __shared__ __align__(16) unsigned char smem[];

@@ -41,7 +41,15 @@ struct QcVariant {
     QcFn fn[3];      // per-shot priors, per-shot priors with the automatic ceiling, per-qubit priors
     size_t smem[3];  // shared memory of each
 };
-extern const QcVariant kQcVariants[];
-extern const int kNumQc;
+// Two tables (kernels_qc_small.cu: n <= 512; kernels_qc_large.cu: n > 512), compiled in
+// parallel and read as one list, smallest shapes first.
+extern const QcVariant kQcVariantsSmall[];
+extern const int kNumQcSmall;
+extern const QcVariant kQcVariantsLarge[];
+extern const int kNumQcLarge;
+inline int num_qc_variants() { return kNumQcSmall + kNumQcLarge; }
+inline const QcVariant& qc_variant(int v) {
+    return v < kNumQcSmall ? kQcVariantsSmall[v] : kQcVariantsLarge[v - kNumQcSmall];
+}
 
 }  // namespace sagms_kernels

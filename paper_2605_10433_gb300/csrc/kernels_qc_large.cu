@@ -1,7 +1,9 @@
 // Instantiations of the column-indexed group kernels (decode_qc.cuh), three per shape: per-shot
-// priors, per-shot priors with the automatic gain ceiling, and per-qubit priors.  Four checks per thread where the offsets and inputs
-// fit in 128 registers (two checks per thread in 1024-thread CTAs measured 5-15% slower at
-// n = 2046).
+// priors, per-shot priors with the automatic gain ceiling, and per-qubit priors.  Shapes for
+// slot degrees (6, 3), (8, 4) and (10, 5) -- GB codes of weight w = 3, 4, 5 and other codes
+// with that slot structure -- at every size class, four checks per thread where the offsets
+// and inputs fit in 128 registers (two checks per thread in 1024-thread CTAs measured 5-15%
+// slower at n = 2046).
 #include "kernels.h"
 
 namespace sagms_kernels {
@@ -15,15 +17,13 @@ namespace sagms_kernels {
             {sagms::QcShape<DC, DV, K, T, NP>::SMEM, sagms::QcShape<DC, DV, K, T, NP>::SMEM,            \
              sagms::QcShape<DC, DV, K, T, NP>::SMEM_PQ}                                                 \
     }
-const QcVariant kQcVariants[] = {
-    SAGMS_QC(6, 3, 2, 32, 128),                                                       // n <= 128
-    SAGMS_QC(8, 4, 4, 32, 256),                                                       // n <= 256
-    SAGMS_QC(6, 3, 4, 64, 512),  SAGMS_QC(8, 4, 4, 64, 512),  SAGMS_QC(10, 5, 4, 64, 512),
-    SAGMS_QC(12, 6, 4, 64, 512), SAGMS_QC(16, 8, 2, 128, 512),                        // n <= 512
-    SAGMS_QC(8, 4, 4, 128, 1024), SAGMS_QC(10, 5, 4, 128, 1024),                      // n <= 1024
+const QcVariant kQcVariantsLarge[] = {
+    // n <= 1024: 128-thread groups (up to 512 checks)
+    SAGMS_QC(6, 3, 4, 128, 1024), SAGMS_QC(8, 4, 4, 128, 1024), SAGMS_QC(10, 5, 4, 128, 1024),
+    // n <= 2048: 256-thread groups (up to 1024 checks)
     SAGMS_QC(6, 3, 4, 256, 2048), SAGMS_QC(8, 4, 4, 256, 2048), SAGMS_QC(10, 5, 4, 256, 2048),
 };
 #undef SAGMS_QC
-const int kNumQc = sizeof(kQcVariants) / sizeof(kQcVariants[0]);
+const int kNumQcLarge = sizeof(kQcVariantsLarge) / sizeof(kQcVariantsLarge[0]);
 
 }  // namespace sagms_kernels

@@ -317,8 +317,8 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
     // j mod DV and a qubit's edges in increasing slot have increasing numbers.
     int qv = -1;
     {
-        for (int v = 0; v < kNumQc && qv < 0; ++v) {
-            const QcVariant& V = kQcVariants[v];
+        for (int v = 0; v < num_qc_variants() && qv < 0; ++v) {
+            const QcVariant& V = qc_variant(v);
             const int DVq = V.dv;
             if (dc_max > V.dc || dv_max > V.dv) continue;
             if (m > V.k * V.t || 2 * m <= V.k * V.t || n > V.np || 2 * n <= V.np) continue;
@@ -332,7 +332,7 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
         }
     }
     std::vector<uint32_t> colQ;
-    if (qv >= 0) colQ = qc_layout(m, row_ptr, col_idx, kQcVariants[qv]);
+    if (qv >= 0) colQ = qc_layout(m, row_ptr, col_idx, qc_variant(qv));
 
     // Checks of each qubit, for syndrome formation in the Monte Carlo sampler.
     std::vector<uint16_t> qchk((size_t)dv_max * n, (uint16_t)0xFFFFu);
@@ -492,7 +492,7 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     int threads;
     int shots_per_cta;   // shots one CTA decodes at a time
     if (use_qc) {
-        const QcVariant& V = kQcVariants[code->qc_variant];
+        const QcVariant& V = qc_variant(code->qc_variant);
         fn = reinterpret_cast<const void*>(V.fn[qc_form]);
         smem = V.smem[qc_form];
         threads = kQcThreads;
@@ -566,7 +566,7 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
         const long long g = std::min(grid, (cnt + shots_per_cta - 1) / shots_per_cta);
         c.chunk_lg = plan.chunk_lg > 0 ? plan.chunk_lg : chunk_lg_for(cnt, g);
         if (use_qc)
-            kQcVariants[code->qc_variant].fn[qc_form]<<<(unsigned)g, threads, smem, stream>>>(c, code->d_colQ);
+            qc_variant(code->qc_variant).fn[qc_form]<<<(unsigned)g, threads, smem, stream>>>(c, code->d_colQ);
         else if (use_groups)
             group_kernel_fn()<<<(unsigned)g, threads, smem, stream>>>(c, glay);
         else

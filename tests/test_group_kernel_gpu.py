@@ -199,7 +199,8 @@ def test_set_plan_rejects_unknown_bits(group_codes):
     _native.sagms_set_plan(dc.handle, KERNEL_QC | (1 << 16))
 
 
-@pytest.mark.parametrize("lw", [(63, 3), (127, 4), (255, 3), (255, 4), (255, 5), (255, 6), (255, 8), (511, 5)])
+@pytest.mark.parametrize("lw", [(63, 3), (63, 4), (63, 5), (127, 3), (127, 4), (127, 5), (255, 3), (255, 4),
+                                (255, 5), (255, 6), (255, 8), (511, 3), (511, 4), (511, 5), (1023, 3)])
 def test_column_indexed_shapes_for_smaller_codes(dev_check, lw):
     """Every compiled column-indexed shape (n from 126 to 1022, warp-sized groups up to four
     256-thread groups) against the one-shot-per-CTA kernel, bit for bit, on mixed noise with
@@ -228,3 +229,14 @@ def test_small_truncated_code_oracle_parity(dev_check):
     G.compare(c, dc, syn, L0, PARAMS["sagms"])
     assert _same(G.gpu_decode(dc, syn, L0, PARAMS["sagms"]),
                  _decode_with_kernel(c, KERNEL_GENERIC, syn, L0, PARAMS["sagms"]))
+
+
+def test_bivariate_bicycle_code_on_the_column_indexed_kernel(dev_check):
+    """A code of another family with the slot structure: the bivariate-bicycle [[144,12,12]]
+    code runs on the column-indexed kernel, bit for bit as on the one-shot-per-CTA kernel."""
+    from tests.test_mc import bb_code
+    c = bb_code(12, 6, [("x", 3), ("y", 1), ("y", 2)], [("y", 3), ("x", 1), ("x", 2)])
+    _, syn, L0, _ = I.workload(c, [0.01, 0.03, 0.05], 3000, seed=144)
+    for mode in ("ms", "sagms"):
+        assert _same(_decode_with_kernel(c, KERNEL_QC, syn, L0, PARAMS[mode]),
+                     _decode_with_kernel(c, KERNEL_GENERIC, syn, L0, PARAMS[mode]))

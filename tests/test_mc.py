@@ -82,6 +82,37 @@ def test_logicals_reject_non_css_and_bad_csr():
         _native.sagms_x_logicals(3, bad, np.array([0, 5], dtype=np.int32), rz, cz)
 
 
+def bb_code(l, m, a_terms, b_terms):
+    """Bivariate-bicycle code H_X = [A | B], H_Z = [B^T | A^T] over the group Z_l x Z_m, with
+    A and B sums of monomials x^p or y^p; rows list A's terms, then B's, in the given order."""
+    N = l * m
+
+    def mono(term, r, sign=1):
+        i, j = divmod(r, m)
+        return ((i + sign * term[1]) % l) * m + j if term[0] == "x" else i * m + (j + sign * term[1]) % m
+
+    rows = [[mono(t, r) for t in a_terms] + [N + mono(t, r) for t in b_terms] for r in range(N)]
+    rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    hz = []
+    for r in range(N):
+        x = 0
+        for t in b_terms:
+            x |= 1 << mono(t, r, -1)
+        for t in a_terms:
+            x |= 1 << (N + mono(t, r, -1))
+        hz.append(x)
+    return I.Code(m=N, n=2 * N, row_ptr=rp, col_idx=np.concatenate(rows).astype(np.int32), name=f"BB({l},{m})",
+                  hz_rows=hz)
+
+
+def test_bivariate_bicycle_144_has_twelve_logicals():
+    """[[144,12,12]] (A = x^3 + y + y^2, B = y^3 + x + x^2 over Z_12 x Z_6): the construction
+    encodes k = 12 logical qubits, so the basis has 12 X-logicals."""
+    c = bb_code(12, 6, [("x", 3), ("y", 1), ("y", 2)], [("y", 3), ("x", 1), ("x", 2)])
+    L = S.x_logicals(c)
+    assert L.shape == (12, (144 + 31) // 32)
+
+
 # ----------------------------------------------------------------------------- GPU
 gpu = pytest.mark.gpu
 
