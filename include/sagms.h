@@ -104,8 +104,9 @@ typedef struct {
 
 /*
  * Load a parity-check matrix (Tanner graph sets M(i), N(j) of Sec. II) onto the current
- * CUDA device.  row_ptr[m+1] and col_idx[nnz] are host arrays in CSR form; the order of
- * columns inside a row is kept as the edge order of that check (no sorting needed).
+ * CUDA device.  row_ptr[m+1] and col_idx[nnz] are host arrays in CSR form, columns in any
+ * order within a row: the library fixes the edge order (sagms_column_slots), which decides
+ * only the order in which a qubit's incoming messages are summed in Eq. 2, i.e. rounding.
  * Requires 1 <= m <= SAGMS_MAX_M, n >= 1, check degrees <= SAGMS_MAX_DC and qubit
  * degrees <= SAGMS_MAX_DV.  On success *out owns device memory until sagms_free_code.
  * Errors: ERR_ARG, ERR_CSR, ERR_DEGREE, ERR_SIZE, ERR_OOM, ERR_CUDA.
@@ -118,6 +119,29 @@ void sagms_free_code(sagms_code* code);
 
 /* Shape of a loaded code: any output pointer may be NULL. */
 int sagms_code_info(const sagms_code* code, int32_t* m, int32_t* n, int32_t* dc_max, int32_t* dv_max);
+
+/* Kernels that can decode a loaded code in the MS family (SAGMS, SMS, MS), in the numbering of
+ * a launch plan (sagms_autotune): bit k of *mask set when kernel k has a layout for the code
+ * (bit 1, one shot per CTA, always; 2 two-slot; 3 two-group; 4 two-group with column-indexed
+ * messages).  Parameters can still rule a kernel out (per-qubit priors: no two-group kernel;
+ * BP: one shot per CTA only).  Host only.  Errors: ERR_ARG. */
+int sagms_code_kernels(const sagms_code* code, uint32_t* mask);
+
+/*
+ * Edge order of the column-indexed kernels (the Sec. II Tanner graph laid out so that a check's
+ * edge in slot j keeps its message at row j mod D of its qubit's column).  For every edge e
+ * (CSR order) slots[e] in [0, 2D) such that slots are distinct within each check and
+ * slots[e] mod D are distinct among each qubit's edges.  The CSR order itself when it has this
+ * property (e.g. generalized-bicycle rows listed by polynomial term), else a proper D-edge-
+ * colouring of the graph of qubits and check halves (Koenig's theorem: it exists whenever every
+ * qubit degree is <= D and every check degree <= 2D), preferring colours that keep cyclic-shift
+ * structure.  sagms_load_code uses it with D = the message rows of the kernel shape it picks.
+ *   slots  [nnz] host, out.
+ * Host only (no CUDA call).  Errors: ERR_ARG (NULL pointers, D outside [1, 32]), ERR_CSR,
+ * ERR_DEGREE (a qubit degree above D or a check degree above 2D).
+ */
+int sagms_column_slots(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr,
+                       const int32_t* col_idx, int32_t D, int32_t* slots);
 
 /* Validate a parameter block without decoding.  Returns SAGMS_OK or SAGMS_ERR_PARAM /
  * SAGMS_ERR_ARG.  Runs on the host only (no CUDA call). */

@@ -56,6 +56,12 @@ class DeviceCode:
     def nw(self):
         return (self.n + 31) // 32
 
+    @property
+    def kernels(self):
+        """Names of the kernels with a layout for this code (decode_plan's names)."""
+        mask = self._native.sagms_code_kernels(self.handle)
+        return [KERNEL_NAMES[k] for k in range(1, 5) if mask >> k & 1]
+
     def set_logicals(self, logicals):
         """Attach logical operators (uint32 [k][ceil(n/32)]) for the Monte Carlo check."""
         self._native.sagms_mc_set_logicals(self.handle, logicals)
@@ -137,10 +143,12 @@ def decode_host(code: DeviceCode, syn, L0, params: Params | None = None, out=Non
     return err, conv, iters
 
 
+KERNEL_NAMES = {0: "auto", 1: "one-shot-per-CTA", 2: "two-slot", 3: "two-group", 4: "two-group-qc"}
+
+
 def decode_plan(plan: int) -> dict:
     """Unpack a launch plan returned by sagms_autotune."""
-    return {"kernel": {0: "auto", 1: "one-shot-per-CTA", 2: "two-slot", 3: "two-group",
-                       4: "two-group-qc"}[plan & 7],
+    return {"kernel": KERNEL_NAMES[plan & 7],
             "ctas_per_sm": (plan >> 8) & 0xff, "chunk_lg": (plan >> 16) & 0xf}
 
 

@@ -61,6 +61,8 @@ def _load_library():
         "sagms_load_code": (ctypes.c_int, [i32, i32, i64, P(i32), P(i32), P(vp)]),
         "sagms_free_code": (None, [vp]),
         "sagms_code_info": (ctypes.c_int, [vp, P(i32), P(i32), P(i32), P(i32)]),
+        "sagms_code_kernels": (ctypes.c_int, [vp, P(ctypes.c_uint32)]),
+        "sagms_column_slots": (ctypes.c_int, [i32, i32, i64, P(i32), P(i32), i32, P(i32)]),
         "sagms_check_params": (ctypes.c_int, [P(sagms_params)]),
         "sagms_decode": (ctypes.c_int, [vp, P(sagms_params), i64, vp, vp, vp, vp, vp, vp]),
         "sagms_decode_trace": (ctypes.c_int, [vp, P(sagms_params), i64, vp, vp, vp, vp, vp, vp, vp]),
@@ -134,6 +136,26 @@ def sagms_code_info(handle):
     v = [ctypes.c_int32() for _ in range(4)]
     _check(_lib.sagms_code_info(handle, *[ctypes.byref(x) for x in v]))
     return tuple(x.value for x in v)
+
+
+def sagms_code_kernels(handle):
+    """Bit mask of the plan kernels (1-4) that have a layout for the code."""
+    v = ctypes.c_uint32()
+    _check(_lib.sagms_code_kernels(handle, ctypes.byref(v)))
+    return v.value
+
+
+def sagms_column_slots(m, n, row_ptr, col_idx, D):
+    """Column-indexed slot of every edge (int32 numpy array, CSR order) for D message rows."""
+    import numpy as np
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    out = np.zeros(len(ci), dtype=np.int32)
+    _check(_lib.sagms_column_slots(int(m), int(n), int(rp[-1]) if len(rp) else 0,
+                                   rp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   ci.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(D),
+                                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    return out
 
 
 def sagms_check_params(params: sagms_params) -> int:

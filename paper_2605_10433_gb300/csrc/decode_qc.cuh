@@ -1,9 +1,10 @@
-// Two-group decoder kernel with column-indexed message storage, for the MS family on codes
-// whose edges line up slot by slot: every edge in check slot j is, at its qubit, the edge
-// numbered q = j mod DV, and a qubit's edges in increasing check slot have increasing q.
-// Generalized-bicycle codes H = [A | B] with rows listed in polynomial-term order have this
-// structure (slot j < w is term j of a(x) and qubit c < l meets it as its j-th edge; slot
-// w + k is term k of b(x)), with DC = 2w and DV = w.
+// Two-group decoder kernel with column-indexed message storage, for the MS family.  Every
+// edge has a check slot j (distinct within its check) such that the j mod DV are distinct
+// among each qubit's edges; the edge's message lives at row j mod DV of its qubit's column.
+// Generalized-bicycle codes H = [A | B] with rows listed in polynomial-term order have such
+// slots as listed (slot j < w is term j of a(x), slot w + k term k of b(x); DC = 2w, DV = w);
+// for any other code with qubit degrees <= DV and check degrees <= DC the host assigns them
+// by edge colouring (sagms_column_slots).
 //
 // A 512-thread CTA holds NG = 512 / T independent groups of T threads; each group decodes one
 // shot at a time and refills as shots finish (as in decode_groups.cuh), synchronised by its

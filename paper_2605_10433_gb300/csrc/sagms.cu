@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cstdlib>
 #include <cmath>
@@ -49,13 +50,146 @@ int round_up(int x, int k) { return (x + k - 1) / k * k; }
 
 
 // colQ layout of a column-indexed shape: [K][DC][T], byte offset 4 * col of check
-// tg + k * T in slot j (4 * NP, the padding column, for padding).
-std::vector<uint32_t> qc_layout(int m, const int32_t* row_ptr, const int32_t* col_idx, const QcVariant& V) {
+// tg + k * T in slot qslot[e] (4 * NP, the padding column, for padding).
+std::vector<uint32_t> qc_layout(int m, const int32_t* row_ptr, const int32_t* col_idx, const std::vector<int>& qslot,
+                                const QcVariant& V) {
     std::vector<uint32_t> out((size_t)V.k * V.dc * V.t, (uint32_t)V.np * 4u);
     for (int i = 0; i < m; ++i)
         for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
-            out[((size_t)(i / V.t) * V.dc + (e - row_ptr[i])) * V.t + (i % V.t)] = (uint32_t)col_idx[e] * 4u;
+            out[((size_t)(i / V.t) * V.dc + qslot[e]) * V.t + (i % V.t)] = (uint32_t)col_idx[e] * 4u;
     return out;
+}
+
+// True when slot[e] mod D differs between the edges of every qubit (the column-indexed
+// kernel keeps qubit c's edge in slot j at message row j mod D of column c).
+bool column_slots_ok(int m, int n, const int32_t* row_ptr, const int32_t* col_idx, const std::vector<int>& slot,
+                     int D) {
+    std::vector<uint32_t> used(n, 0u);
+    for (int i = 0; i < m; ++i)
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            const uint32_t bit = 1u << (slot[e] % D);
+            if (used[col_idx[e]] & bit) return false;
+            used[col_idx[e]] |= bit;
+        }
+    return true;
+}
+
+// Column-indexed slots for any code whose degrees fit the shape (dv <= D, dc <= 2D), by edge
+// colouring.  Each check's edges split, in CSR order, into two halves of at most D edges; the
+// bipartite graph of qubits and check halves then has maximum degree D, so by Koenig's
+// edge-colouring theorem it has a proper colouring with D colours, found here by the
+// alternating-path method: give an edge a colour free at both ends, or else take a colour a
+// free at its qubit and b free at its half, swap a and b along the a/b path leaving the half
+// (the path cannot reach the qubit, the graph being bipartite) and give the edge a.  An edge of
+// colour q in half h takes slot q + D h: distinct slots within a check, distinct q at a qubit.
+// Preferred colours keep shift structure where the code has it (quasi-cyclic codes listed with
+// sorted columns): first the colour of the edge one check and one column back in the same
+// half, then the edge's rank in its half, then any colour free at both ends.  Returns an empty vector if no colouring is found
+// (it always is when the degrees fit).
+std::vector<int> colour_slots(int m, int n, const int32_t* row_ptr, const int32_t* col_idx, int D) {
+    const int nnz = row_ptr[m];
+    std::vector<int> colour(nnz, -1), half(nnz), rank(nnz);
+    std::vector<int> at_q((size_t)n * D, -1), at_h((size_t)2 * m * D, -1);
+    for (int i = 0; i < m; ++i) {
+        const int d = row_ptr[i + 1] - row_ptr[i], h0 = (d + 1) / 2;
+        if (h0 > D || d - h0 > D) return {};
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            const int r = e - row_ptr[i];
+            half[e] = 2 * i + (r < h0 ? 0 : 1);
+            rank[e] = r < h0 ? r : r - h0;
+        }
+    }
+    auto free_at = [&](int e, int c) {
+        return at_q[(size_t)col_idx[e] * D + c] < 0 && at_h[(size_t)half[e] * D + c] < 0;
+    };
+    auto set = [&](int e, int c) {
+        colour[e] = c;
+        at_q[(size_t)col_idx[e] * D + c] = e;
+        at_h[(size_t)half[e] * D + c] = e;
+    };
+    std::vector<int> path;
+    for (int i = 0; i < m; ++i) {
+        for (int e = row_ptr[i]; i > 0 && e < row_ptr[i + 1]; ++e) {   // the shifted predecessor's colour
+            for (int f = row_ptr[i - 1]; f < row_ptr[i]; ++f)
+                if (col_idx[f] == col_idx[e] - 1 && (half[f] & 1) == (half[e] & 1) && colour[f] >= 0 &&
+                    free_at(e, colour[f])) {
+                    set(e, colour[f]);
+                    break;
+                }
+        }
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            if (colour[e] >= 0) continue;
+            if (free_at(e, rank[e])) { set(e, rank[e]); continue; }
+            int c = 0;
+            while (c < D && !free_at(e, c)) ++c;
+            if (c < D) { set(e, c); continue; }
+            int a = 0, b = 0;
+            while (a < D && at_q[(size_t)col_idx[e] * D + a] >= 0) ++a;
+            while (b < D && at_h[(size_t)half[e] * D + b] >= 0) ++b;
+            if (a == D || b == D) return {};
+            if (at_h[(size_t)half[e] * D + a] >= 0) {
+                // alternating a/b path from the half: half -a-> qubit -b-> half -a-> ...
+                path.clear();
+                int x = half[e], cur = a;
+                bool at_half = true;
+                while ((int)path.size() <= nnz) {
+                    const int f = at_half ? at_h[(size_t)x * D + cur] : at_q[(size_t)x * D + cur];
+                    if (f < 0) break;
+                    path.push_back(f);
+                    x = at_half ? col_idx[f] : half[f];
+                    at_half = !at_half;
+                    cur = (cur == a) ? b : a;
+                }
+                for (int f : path) {
+                    at_q[(size_t)col_idx[f] * D + colour[f]] = -1;
+                    at_h[(size_t)half[f] * D + colour[f]] = -1;
+                }
+                for (int f : path) set(f, colour[f] == a ? b : a);
+            }
+            if (!free_at(e, a)) return {};
+            set(e, a);
+        }
+    }
+    std::vector<int> slot(nnz);
+    for (int e = 0; e < nnz; ++e) slot[e] = colour[e] + D * (half[e] & 1);
+    if (!column_slots_ok(m, n, row_ptr, col_idx, slot, D)) return {};
+    return slot;
+}
+
+// CSR checks shared by the entry points that take a matrix: row_ptr monotone from 0 to nnz,
+// columns in range, no repeated column in a row.  Reports the largest check and qubit degrees.
+int check_csr(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx, int* dc_max,
+              int* dv_max) {
+    if (!row_ptr || (nnz > 0 && !col_idx)) return fail(SAGMS_ERR_ARG, "row_ptr/col_idx is NULL");
+    if (m < 1 || n < 1 || nnz < 0) return fail(SAGMS_ERR_ARG, "need m >= 1, n >= 1, nnz >= 0");
+    if (row_ptr[0] != 0 || row_ptr[m] != nnz) return fail(SAGMS_ERR_CSR, "row_ptr[0] must be 0 and row_ptr[m] == nnz");
+    int dc = 0;
+    std::vector<int> deg_v(n, 0);
+    std::vector<int> seen(n, -1);
+    for (int i = 0; i < m; ++i) {
+        if (row_ptr[i + 1] < row_ptr[i]) return fail(SAGMS_ERR_CSR, "row_ptr not monotone at row %d", i);
+        dc = std::max(dc, row_ptr[i + 1] - row_ptr[i]);
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            const int j = col_idx[e];
+            if (j < 0 || j >= n) return fail(SAGMS_ERR_CSR, "column %d out of range in row %d", j, i);
+            if (seen[j] == i) return fail(SAGMS_ERR_CSR, "duplicate column %d in row %d", j, i);
+            seen[j] = i;
+            deg_v[j]++;
+        }
+    }
+    *dc_max = dc;
+    *dv_max = *std::max_element(deg_v.begin(), deg_v.end());
+    return SAGMS_OK;
+}
+
+// Column-indexed slots of a code for D message rows: the CSR order when it already gives every
+// qubit distinct slots mod D, else an edge colouring (empty if neither).
+std::vector<int> column_slots(int m, int n, const int32_t* row_ptr, const int32_t* col_idx, int D) {
+    std::vector<int> slot(row_ptr[m]);
+    for (int i = 0; i < m; ++i)
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) slot[e] = e - row_ptr[i];
+    if (column_slots_ok(m, n, row_ptr, col_idx, slot, D)) return slot;
+    return colour_slots(m, n, row_ptr, col_idx, D);
 }
 
 constexpr int kMaxDevices = 64;
@@ -212,64 +346,104 @@ int sagms_check_params(const sagms_params* p) {
     }
 }
 
+int sagms_column_slots(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+                       int32_t D, int32_t* slots) {
+    if (!slots && nnz > 0) return fail(SAGMS_ERR_ARG, "slots is NULL");
+    int dc_max = 0, dv_max = 0;
+    const int rc = check_csr(m, n, nnz, row_ptr, col_idx, &dc_max, &dv_max);
+    if (rc != SAGMS_OK) return rc;
+    if (D < 1 || D > 32) return fail(SAGMS_ERR_ARG, "D = %d outside [1, 32]", D);
+    if (dv_max > D || dc_max > 2 * D)
+        return fail(SAGMS_ERR_DEGREE, "degrees dc=%d dv=%d need more than %d message rows", dc_max, dv_max, D);
+    const std::vector<int> s = column_slots(m, n, row_ptr, col_idx, D);
+    if (s.empty()) return fail(SAGMS_ERR_DEGREE, "no column-indexed slot assignment found");
+    std::copy(s.begin(), s.end(), slots);
+    return SAGMS_OK;
+}
+
 int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
                     sagms_code** out) {
     if (!out) return fail(SAGMS_ERR_ARG, "out is NULL");
     *out = nullptr;
-    if (!row_ptr || (nnz > 0 && !col_idx)) return fail(SAGMS_ERR_ARG, "row_ptr/col_idx is NULL");
-    if (m < 1 || n < 1 || nnz < 0) return fail(SAGMS_ERR_ARG, "need m >= 1, n >= 1, nnz >= 0");
+    int dc_max = 0, dv_max = 0;
+    const int rc = check_csr(m, n, nnz, row_ptr, col_idx, &dc_max, &dv_max);
+    if (rc != SAGMS_OK) return rc;
     if (m > SAGMS_MAX_M) return fail(SAGMS_ERR_SIZE, "m = %d exceeds %d checks", m, SAGMS_MAX_M);
     if (n > 60000) return fail(SAGMS_ERR_SIZE, "n = %d too large", n);
-    if (row_ptr[0] != 0 || row_ptr[m] != nnz) return fail(SAGMS_ERR_CSR, "row_ptr[0] must be 0 and row_ptr[m] == nnz");
-    int dc_max = 0;
-    std::vector<int> deg_v(n, 0);
-    std::vector<int> seen(n, -1);
-    for (int i = 0; i < m; ++i) {
-        if (row_ptr[i + 1] < row_ptr[i]) return fail(SAGMS_ERR_CSR, "row_ptr not monotone at row %d", i);
-        const int d = row_ptr[i + 1] - row_ptr[i];
-        dc_max = std::max(dc_max, d);
-        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-            const int j = col_idx[e];
-            if (j < 0 || j >= n) return fail(SAGMS_ERR_CSR, "column %d out of range in row %d", j, i);
-            if (seen[j] == i) return fail(SAGMS_ERR_CSR, "duplicate column %d in row %d", j, i);
-            seen[j] = i;
-            deg_v[j]++;
-        }
-    }
-    const int dv_max = *std::max_element(deg_v.begin(), deg_v.end());
     if (dc_max > SAGMS_MAX_DC || dv_max > SAGMS_MAX_DV)
         return fail(SAGMS_ERR_DEGREE, "degrees dc=%d dv=%d exceed limits %d/%d", dc_max, dv_max, SAGMS_MAX_DC,
                     SAGMS_MAX_DV);
+    // Column-indexed shape: the first compiled one whose degrees and size class fit.
+    int qv = -1;
+    for (int v = 0; v < num_qc_variants() && qv < 0; ++v) {
+        const QcVariant& V = qc_variant(v);
+        if (dc_max > V.dc || dv_max > V.dv) continue;
+        if (m > V.k * V.t || 2 * m <= V.k * V.t || n > V.np || 2 * n <= V.np) continue;
+        qv = v;
+    }
+    // Edge order shared by every layout, so that all kernels add each qubit's messages in the
+    // same order (bitwise-identical results): cslot[e] = the check slot of edge e in the
+    // slot-major layouts, vrow[e] = its row in the qubit's variable-node sum.  With a
+    // column-indexed shape, qslot[e] = its slot there (the CSR order when that already gives
+    // every qubit distinct slots mod DV, else an edge colouring), cslot its rank in the check
+    // by qslot and vrow = qslot mod DV; otherwise cslot is the CSR order and vrow the rank among
+    // the qubit's edges by (cslot, check).
+    std::vector<int> cslot(nnz), qslot, vrow(nnz);
+    for (int i = 0; i < m; ++i)
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) cslot[e] = e - row_ptr[i];
+    int DVr = dv_max;   // message rows every variable-node layout needs
+    if (qv >= 0) {
+        const int DVq = qc_variant(qv).dv;
+        qslot = column_slots(m, n, row_ptr, col_idx, DVq);
+        if (qslot.empty()) {
+            qv = -1;
+        } else {
+            DVr = DVq;
+            for (int i = 0; i < m; ++i) {
+                std::vector<std::pair<int, int>> r;
+                for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) r.push_back({qslot[e], e});
+                std::sort(r.begin(), r.end());
+                for (size_t k = 0; k < r.size(); ++k) cslot[r[k].second] = (int)k;
+            }
+            for (int64_t e = 0; e < nnz; ++e) vrow[e] = qslot[e] % DVq;
+        }
+    }
+    // vedges[c] = (vrow, check, cslot) of qubit c's edges
+    std::vector<std::vector<std::array<int, 3>>> vedges(n);
+    for (int i = 0; i < m; ++i)
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) vedges[col_idx[e]].push_back({cslot[e], i, e});
+    for (int c = 0; c < n; ++c) {
+        auto& ve = vedges[c];
+        std::sort(ve.begin(), ve.end());   // by (cslot, check): consecutive qubits of a circulant, consecutive positions
+        for (size_t q = 0; q < ve.size(); ++q) {
+            const int e = ve[q][2];
+            ve[q] = {qv >= 0 ? vrow[e] : (int)q, ve[q][1], cslot[e]};
+        }
+    }
+
     int variant = kNumVariants - 1;
     for (int v = 0; v < kNumVariants; ++v)
-        if (kVariants[v].dc >= dc_max && kVariants[v].dv >= dv_max) { variant = v; break; }
+        if (kVariants[v].dc >= dc_max && kVariants[v].dv >= DVr) { variant = v; break; }
     const int DC = kVariants[variant].dc, DV = kVariants[variant].dv;
     const int Mp = round_up(m, 32);
     const int Np = round_up(n + 1, 32);
     if ((long long)DC * Mp + 1 > 65535) return fail(SAGMS_ERR_SIZE, "edge slots exceed 16-bit indexing");
 
-    // Slot-major layouts.  colT[j*Mp + i] = column of the j-th edge of check i (n = padding).
+    // Slot-major layouts.  colT[j*Mp + i] = column of the edge of check i in slot j (n = padding).
     std::vector<uint16_t> colT((size_t)DC * Mp, (uint16_t)n);
     for (int i = 0; i < m; ++i)
         for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
-            colT[(size_t)(e - row_ptr[i]) * Mp + i] = (uint16_t)col_idx[e];
-    // vneT[q*Np + c] = slot position of the q-th edge of qubit c, edges ordered by slot index j
-    // (for circulant codes consecutive qubits then touch consecutive positions).
-    std::vector<std::vector<std::pair<int, int>>> vedges(n);
-    for (int i = 0; i < m; ++i)
-        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) vedges[col_idx[e]].push_back({e - row_ptr[i], i});
+            colT[(size_t)cslot[e] * Mp + i] = (uint16_t)col_idx[e];
+    // vneT[q*Np + c] = slot position of qubit c's edge in message row q
     std::vector<uint16_t> vneT((size_t)DV * Np, (uint16_t)(DC * Mp));
-    for (int c = 0; c < n; ++c) {
-        auto& ve = vedges[c];
-        std::sort(ve.begin(), ve.end());
-        for (size_t q = 0; q < ve.size(); ++q) vneT[q * Np + c] = (uint16_t)(ve[q].first * Mp + ve[q].second);
-    }
+    for (int c = 0; c < n; ++c)
+        for (const auto& x : vedges[c]) vneT[(size_t)x[0] * Np + c] = (uint16_t)(x[2] * Mp + x[1]);
 
     // Two-slot layout, when a compiled shape covers the code.
     int sv = -1;
     for (int v = 0; v < kNumSlotVariants; ++v) {
         const SlotVariant& S = kSlotVariants[v];
-        if (dc_max <= S.dc && dv_max <= S.dv && m <= S.mp && S.mp <= 2 * round_up(m, 32) &&
+        if (dc_max <= S.dc && DVr <= S.dv && m <= S.mp && S.mp <= 2 * round_up(m, 32) &&
             n <= S.np && S.np * 8 < 65536) { sv = v; break; }
     }
     std::vector<uint16_t> colB;
@@ -279,18 +453,15 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
         colB.assign((size_t)S.dc * S.mp, (uint16_t)(S.np * 8));   // padding -> sentinel qubit NP
         for (int i = 0; i < m; ++i)
             for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
-                colB[(size_t)(e - row_ptr[i]) * S.mp + i] = (uint16_t)(col_idx[e] * 8);
+                colB[(size_t)cslot[e] * S.mp + i] = (uint16_t)(col_idx[e] * 8);
         vneB.assign((size_t)S.dv * S.np, (uint32_t)(S.dc * S.mp * 8));
-        for (int c = 0; c < n; ++c) {
-            const auto& ve = vedges[c];
-            for (size_t q = 0; q < ve.size(); ++q)
-                vneB[q * S.np + c] = (uint32_t)((ve[q].first * S.mp + ve[q].second) * 8);
-        }
+        for (int c = 0; c < n; ++c)
+            for (const auto& x : vedges[c]) vneB[(size_t)x[0] * S.np + c] = (uint32_t)((x[2] * S.mp + x[1]) * 8);
     }
 
     // Two-group layout: the same graph once per group, as byte offsets from the start of
     // shared memory into that group's posterior and message arrays.
-    const bool groups = dc_max <= kGroupDC && dv_max <= kGroupDV && m > 512 && m <= kGrpChecks && n <= kGrpQubits;
+    const bool groups = dc_max <= kGroupDC && DVr <= kGroupDV && m > 512 && m <= kGrpChecks && n <= kGrpQubits;
     std::vector<uint16_t> colG;
     std::vector<uint32_t> vneG;
     if (groups) {
@@ -303,41 +474,21 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
             std::fill(cg, cg + kGroupDC * kGrpChecks, (uint16_t)(pb + (size_t)kGrpQubits * 4));
             for (int i = 0; i < m; ++i)
                 for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
-                    cg[(size_t)(e - row_ptr[i]) * kGrpChecks + i] = (uint16_t)(pb + (size_t)col_idx[e] * 4);
+                    cg[(size_t)cslot[e] * kGrpChecks + i] = (uint16_t)(pb + (size_t)col_idx[e] * 4);
             std::fill(vg, vg + kGroupDV * kGrpQubits, (uint32_t)(cb + (size_t)kGroupDC * kGrpChecks * 4));
-            for (int c = 0; c < n; ++c) {
-                const auto& ve = vedges[c];
-                for (size_t q = 0; q < ve.size(); ++q)
-                    vg[q * kGrpQubits + c] = (uint32_t)(cb + ((size_t)ve[q].first * kGrpChecks + ve[q].second) * 4);
-            }
+            for (int c = 0; c < n; ++c)
+                for (const auto& x : vedges[c])
+                    vg[(size_t)x[0] * kGrpQubits + c] = (uint32_t)(cb + ((size_t)x[2] * kGrpChecks + x[1]) * 4);
         }
     }
 
-    // Column-indexed layout, when every edge in check slot j is its qubit's edge number
-    // j mod DV and a qubit's edges in increasing slot have increasing numbers.
-    int qv = -1;
-    {
-        for (int v = 0; v < num_qc_variants() && qv < 0; ++v) {
-            const QcVariant& V = qc_variant(v);
-            const int DVq = V.dv;
-            if (dc_max > V.dc || dv_max > V.dv) continue;
-            if (m > V.k * V.t || 2 * m <= V.k * V.t || n > V.np || 2 * n <= V.np) continue;
-            bool ok = true;
-            for (int c = 0; c < n && ok; ++c) {
-                const auto& ve = vedges[c];   // sorted by slot
-                for (size_t q = 1; q < ve.size() && ok; ++q)
-                    ok = (ve[q].first % DVq) > (ve[q - 1].first % DVq);
-            }
-            if (ok) qv = v;
-        }
-    }
     std::vector<uint32_t> colQ;
-    if (qv >= 0) colQ = qc_layout(m, row_ptr, col_idx, qc_variant(qv));
+    if (qv >= 0) colQ = qc_layout(m, row_ptr, col_idx, qslot, qc_variant(qv));
 
     // Checks of each qubit, for syndrome formation in the Monte Carlo sampler.
     std::vector<uint16_t> qchk((size_t)dv_max * n, (uint16_t)0xFFFFu);
     for (int c = 0; c < n; ++c)
-        for (size_t q = 0; q < vedges[c].size(); ++q) qchk[q * n + c] = (uint16_t)vedges[c][q].second;
+        for (size_t q = 0; q < vedges[c].size(); ++q) qchk[q * n + c] = (uint16_t)vedges[c][q][1];
 
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
@@ -433,6 +584,13 @@ int sagms_code_info(const sagms_code* code, int32_t* m, int32_t* n, int32_t* dc_
     if (n) *n = code->n;
     if (dc_max) *dc_max = code->dc_max;
     if (dv_max) *dv_max = code->dv_max;
+    return SAGMS_OK;
+}
+
+int sagms_code_kernels(const sagms_code* code, uint32_t* mask) {
+    if (!code || !mask) return fail(SAGMS_ERR_ARG, "code or mask is NULL");
+    *mask = (1u << 1) | (code->slot_variant >= 0 ? 1u << 2 : 0u) | (code->groups ? 1u << 3 : 0u) |
+            (code->qc_variant >= 0 ? 1u << 4 : 0u);
     return SAGMS_OK;
 }
 

@@ -132,7 +132,8 @@ class Code:
     """A binary parity-check matrix H (m x n) in CSR form plus its CSC lists.
 
     ``col_idx`` keeps the order in which the rows were built (for GB codes: the terms of
-    a(x), then those of b(x)), which the decoder keeps as each check's edge order."""
+    a(x), then those of b(x)); the decoder library keeps that order as each check's edge
+    order where it suits its column-indexed layout, and picks its own otherwise."""
     m: int
     n: int
     row_ptr: np.ndarray
