@@ -10,6 +10,10 @@ Parity status per function:
 * ``decode`` (MS, SMS, SAGMS, BP): pinned by the tests in ``tests/test_oracle_pins.py``
   (tree-code brute force, closed forms at the first iteration, reductions between modes,
   the single-check ratio of Eq. 9, the zero-syndrome case).
+* ``decode`` with FLAG_LAYERED (the layered schedule, not used by the paper): pinned by
+  ``tests/test_layered_oracle.py`` (tree-code brute force, a hand-worked example, the
+  first-fit layering on a hand-drawn graph, single-layer codes, information speed on
+  a chain).
 * ``alpha_star`` / ``alpha_star_approx``: pinned to the values the paper prints (Sec. V).
 """
 from __future__ import annotations
@@ -26,6 +30,7 @@ FLAG_L0_PER_QUBIT = 1
 FLAG_NO_EARLY_STOP = 2
 FLAG_NATURAL_UNITS = 8
 FLAG_AUTO_CEILING = 16
+FLAG_LAYERED = 32
 
 MSFAM_CLIP = 1.0e6
 BP_CLIP = 23.718998

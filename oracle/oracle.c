@@ -51,6 +51,19 @@
  *   - ORACLE_FLAG_AUTO_CEILING (SAGMS, per-shot prior): the gain ceiling of
  *     Corollary 1, alpha_max = alpha*(|L0|, d_c) of Eq. 9 per shot with d_c the
  *     largest check degree, clamped to [alpha_min, 1/eta]; L0 = 0 gives alpha_min.
+ *
+ * ORACLE_FLAG_LAYERED: a layered (serial-check) schedule, which the paper does not
+ * use; it replaces (iv) and (v) of each round, everything else staying as above:
+ *   - layers: check i goes to the smallest layer number used by no check k < i that
+ *     shares a qubit with it (first-fit colouring of the checks in index order), so
+ *     the checks of one layer share no qubit;
+ *   - a round visits the layers in increasing order and, in each, every check i
+ *     (index order; checks of a layer commute): first its inputs
+ *     q(j,i) = L0_j + sum_{k in N(j)\i} r(k,j) from the CN messages as they stand
+ *     (Eq. 2, including those already replaced earlier in the round), then its
+ *     outputs r(i,j) by the rule of (iv) with the round's gain g_i;
+ *   - the gains of a round come from the residual at its start, (i)-(iii), as in
+ *     the flooding schedule.
  */
 #include <math.h>
 #include <stdint.h>
@@ -66,6 +79,7 @@
 #define ORACLE_FLAG_NO_EARLY_STOP 2u
 #define ORACLE_FLAG_NATURAL_UNITS 8u  /* oracle only: keep the MS family in LLR units */
 #define ORACLE_FLAG_AUTO_CEILING 16u
+#define ORACLE_FLAG_LAYERED 32u
 
 double oracle_alpha_star(double L0, int dc);
 
@@ -73,6 +87,31 @@ static const double MSFAM_CLIP = 1.0e6;
 static const double BP_CLIP = 23.718998;
 
 static int bit_of(const uint32_t* w, int k) { return (int)((w[k >> 5] >> (k & 31)) & 1u); }
+
+/* (iv) for one check i: every outgoing message r(i,j) from the incoming q over M(i)\j,
+ * leave-one-out written out directly (Eqs. 3, 4, 8). */
+static void cn_update(int i, const int32_t* row_ptr, int s_i, int msfam, double g, const double* q, double* r) {
+    for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+        int neg = s_i;
+        double mn = INFINITY, prod = 1.0;
+        for (int f = row_ptr[i]; f < row_ptr[i + 1]; ++f) {
+            if (f == e) continue;
+            if (q[f] < 0.0) neg ^= 1;
+            const double a = fabs(q[f]);
+            if (msfam) { if (a < mn) mn = a; }
+            else prod *= tanh(0.5 * a);
+        }
+        double mag;
+        if (msfam) {
+            mag = g * mn;
+            if (mag > MSFAM_CLIP) mag = MSFAM_CLIP;
+        } else {
+            mag = (prod >= 1.0) ? INFINITY : 2.0 * atanh(prod);
+            if (mag > BP_CLIP) mag = BP_CLIP;
+        }
+        r[e] = neg ? -mag : mag;
+    }
+}
 
 /*
  * Decode `shots` syndromes.
@@ -108,8 +147,12 @@ int oracle_decode(int m, int n, const int32_t* row_ptr, const int32_t* col_idx,
     int* ehat = (int*)malloc(sizeof(int) * (size_t)n);
     int* sres = (int*)malloc(sizeof(int) * (size_t)(m > 0 ? m : 1));
     int* fill = (int*)calloc((size_t)n + 1, sizeof(int));
+    int* layer = (int*)malloc(sizeof(int) * (size_t)(m > 0 ? m : 1));
+    int* order = (int*)malloc(sizeof(int) * (size_t)(m > 0 ? m : 1));
+    int* stamp = (int*)malloc(sizeof(int) * (size_t)m + sizeof(int));
     int rc = 0;
-    if (!vn_ptr || !vn_edges || !edge_row || !q || !r || !P || !prior || !gain || !ehat || !sres || !fill) {
+    if (!vn_ptr || !vn_edges || !edge_row || !q || !r || !P || !prior || !gain || !ehat || !sres || !fill ||
+        !layer || !order || !stamp) {
         rc = -1;
         goto done;
     }
@@ -135,6 +178,29 @@ int oracle_decode(int m, int n, const int32_t* row_ptr, const int32_t* col_idx,
         if (row_ptr[i + 1] - row_ptr[i] > dc_max) dc_max = row_ptr[i + 1] - row_ptr[i];
     const int normalise = msfam && !per_qubit && !(flags & ORACLE_FLAG_NATURAL_UNITS);
     const int early_stop = !(flags & ORACLE_FLAG_NO_EARLY_STOP);
+    const int layered = (flags & ORACLE_FLAG_LAYERED) != 0;
+    if (layered) {
+        /* first-fit layer of every check in index order, then the checks by (layer, index) */
+        int nlayers = 0;
+        for (int i = 0; i < m; ++i) {
+            for (int k = 0; k <= m; ++k) stamp[k] = 0;
+            for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+                const int j = col_idx[e];
+                for (int u = vn_ptr[j]; u < vn_ptr[j + 1]; ++u) {
+                    const int k = edge_row[vn_edges[u]];
+                    if (k < i) stamp[layer[k]] = 1;
+                }
+            }
+            int l = 0;
+            while (stamp[l]) ++l;
+            layer[i] = l;
+            if (l + 1 > nlayers) nlayers = l + 1;
+        }
+        int o = 0;
+        for (int l = 0; l < nlayers; ++l)
+            for (int i = 0; i < m; ++i)
+                if (layer[i] == l) order[o++] = i;
+    }
 
     for (int64_t s = 0; s < shots; ++s) {
         const uint32_t* sy = syn + (size_t)s * mw;
@@ -200,37 +266,32 @@ int oracle_decode(int m, int n, const int32_t* row_ptr, const int32_t* col_idx,
                 else gain[i] = 1.0;
             }
 
-            /* (iv) CN update, leave-one-out over M(i)\j (Eqs. 3, 4, 8) */
-            for (int i = 0; i < m; ++i) {
-                for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-                    int neg = bit_of(sy, i);
-                    double mn = INFINITY, prod = 1.0;
-                    for (int f = row_ptr[i]; f < row_ptr[i + 1]; ++f) {
-                        if (f == e) continue;
-                        if (q[f] < 0.0) neg ^= 1;
-                        const double a = fabs(q[f]);
-                        if (msfam) { if (a < mn) mn = a; }
-                        else prod *= tanh(0.5 * a);
+            if (!layered) {
+                /* (iv) CN update of every check (Eqs. 3, 4, 8) */
+                for (int i = 0; i < m; ++i) cn_update(i, row_ptr, bit_of(sy, i), msfam, gain[i], q, r);
+                /* (v) VN update, leave-one-out over N(j)\i (Eq. 2) */
+                for (int j = 0; j < n; ++j) {
+                    for (int t = vn_ptr[j]; t < vn_ptr[j + 1]; ++t) {
+                        const int e = vn_edges[t];
+                        double acc = prior[j];
+                        for (int u = vn_ptr[j]; u < vn_ptr[j + 1]; ++u)
+                            if (u != t) acc += r[vn_edges[u]];
+                        q[e] = acc;
                     }
-                    double mag;
-                    if (msfam) {
-                        mag = gain[i] * mn;
-                        if (mag > MSFAM_CLIP) mag = MSFAM_CLIP;
-                    } else {
-                        mag = (prod >= 1.0) ? INFINITY : 2.0 * atanh(prod);
-                        if (mag > BP_CLIP) mag = BP_CLIP;
-                    }
-                    r[e] = neg ? -mag : mag;
                 }
-            }
-            /* (v) VN update, leave-one-out over N(j)\i (Eq. 2) */
-            for (int j = 0; j < n; ++j) {
-                for (int t = vn_ptr[j]; t < vn_ptr[j + 1]; ++t) {
-                    const int e = vn_edges[t];
-                    double acc = prior[j];
-                    for (int u = vn_ptr[j]; u < vn_ptr[j + 1]; ++u)
-                        if (u != t) acc += r[vn_edges[u]];
-                    q[e] = acc;
+            } else {
+                /* layered round: each check in layer order takes its inputs from the CN
+                 * messages as they stand (Eq. 2), then updates its outputs */
+                for (int o = 0; o < m; ++o) {
+                    const int i = order[o];
+                    for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+                        const int j = col_idx[e];
+                        double acc = prior[j];
+                        for (int u = vn_ptr[j]; u < vn_ptr[j + 1]; ++u)
+                            if (vn_edges[u] != e) acc += r[vn_edges[u]];
+                        q[e] = acc;
+                    }
+                    cn_update(i, row_ptr, bit_of(sy, i), msfam, gain[i], q, r);
                 }
             }
             ++l;
@@ -242,7 +303,7 @@ int oracle_decode(int m, int n, const int32_t* row_ptr, const int32_t* col_idx,
 
 done:
     free(vn_ptr); free(vn_edges); free(edge_row); free(q); free(r); free(P); free(prior);
-    free(gain); free(ehat); free(sres); free(fill);
+    free(gain); free(ehat); free(sres); free(fill); free(layer); free(order); free(stamp);
     return rc;
 }
 

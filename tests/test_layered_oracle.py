@@ -1,0 +1,108 @@
+"""Pins of the oracle's layered schedule (FLAG_LAYERED) against things other than itself.
+CPU only.  The paper decodes with the flooding schedule; the layered one is an option of
+this library, read as: first-fit layers of the checks in index order, layers visited in
+increasing order, each check taking its inputs from the messages as they stand, gains from
+the residual at the start of the round.
+
+* cycle-free Tanner graphs: any schedule run to convergence gives BP's exact marginals and
+  MS's min-marginals, so brute force over all error patterns pins both rules;
+* a hand-worked three-check chain whose first-fit order (c0, c2, c1) differs from the index
+  order and from flooding (tests/golden/hand_layered_ms_chain.json);
+* codes whose checks share no qubit form a single layer, where the layered round is the
+  flooding round: bitwise identical to the flooding oracle in every mode.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_10433_gb300 import inputs as I
+from tests import brute
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+LAYERED = oracle.FLAG_LAYERED
+
+
+def _tree_case(seed, mode):
+    rng = np.random.default_rng(2000 + seed)
+    c = I.tree_code(int(rng.integers(6, 13)), seed, max_deg=4)
+    H = c.dense()
+    L0 = rng.uniform(0.4, 3.0, size=c.n)
+    e = (rng.random(c.n) < 0.3).astype(np.uint8)
+    s = (H.astype(np.int64) @ e) % 2
+    syn = I.pack_bits(s[None, :].astype(np.uint8))
+    it = 2 * (c.n + c.m)
+    r = oracle.decode_code(c, syn, L0, mode=mode, max_iter=it,
+                           flags=oracle.FLAG_L0_PER_QUBIT | oracle.FLAG_NO_EARLY_STOP | LAYERED, trace=True)
+    return c, H, s, L0, r["trace"][0, it], r
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_layered_bp_on_trees_equals_exact_marginals(seed):
+    c, H, s, L0, post, _ = _tree_case(seed, oracle.BP)
+    assert np.max(np.abs(post)) < oracle.BP_CLIP
+    np.testing.assert_allclose(post, brute.exact_llr(H, s, L0), rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_layered_ms_on_trees_equals_min_marginals(seed):
+    c, H, s, L0, post, r = _tree_case(seed, oracle.MS)
+    np.testing.assert_allclose(post, brute.min_marginal_diff(H, s, L0), rtol=0, atol=1e-9)
+    best, unique = brute.ml_pattern(H, s, L0)
+    if unique:
+        assert np.array_equal(I.unpack_bits(r["err"], c.n)[0], best)
+
+
+def _chain():
+    g = json.load(open(os.path.join(GOLDEN, "hand_layered_ms_chain.json")))
+    H = np.zeros((len(g["rows"]), g["n"]), dtype=np.uint8)
+    for i, row in enumerate(g["rows"]):
+        H[i, row] = 1
+    return g, I.code_from_dense(H), I.pack_bits(np.array([g["syndrome"]], dtype=np.uint8))
+
+
+def test_hand_worked_layered_chain():
+    g, c, syn = _chain()
+    L0 = np.array(g["L0"])
+    f = oracle.FLAG_L0_PER_QUBIT | LAYERED
+    r = oracle.decode_code(c, syn, L0, mode=oracle.MS, max_iter=5, flags=f, trace=True)
+    np.testing.assert_allclose(r["trace"][0, :2], np.array(g["trace_early_stop"]), rtol=0, atol=1e-12)
+    assert list(I.unpack_bits(r["err"], c.n)[0]) == g["err_bits"]
+    assert r["conv"][0] == g["conv"] and r["iters"][0] == g["iters"]
+    r2 = oracle.decode_code(c, syn, L0, mode=oracle.MS, max_iter=2, flags=f | oracle.FLAG_NO_EARLY_STOP, trace=True)
+    np.testing.assert_allclose(r2["trace"][0], np.array(g["trace_two_rounds"]), rtol=0, atol=1e-12)
+    fl = oracle.decode_code(c, syn, L0, mode=oracle.MS, max_iter=1,
+                            flags=oracle.FLAG_L0_PER_QUBIT | oracle.FLAG_NO_EARLY_STOP, trace=True)
+    np.testing.assert_allclose(fl["trace"][0, 1], np.array(g["flooding_round_one"]), rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("mode", [oracle.MS, oracle.SMS, oracle.SAGMS, oracle.BP])
+def test_single_layer_codes_match_flooding_bitwise(mode):
+    """Checks with pairwise disjoint supports (every qubit in at most one check)."""
+    rng = np.random.default_rng(mode)
+    n = 60
+    perm = rng.permutation(n)
+    cuts = np.sort(rng.choice(np.arange(1, n), size=11, replace=False))
+    rows = [r for r in np.split(perm, cuts) if len(r)][:10]   # the last block's qubits stay unchecked
+    H = np.zeros((len(rows), n), dtype=np.uint8)
+    for i, row in enumerate(rows):
+        H[i, row] = 1
+    c = I.code_from_dense(H)
+    _, syn, L0, _ = I.workload(c, [0.05, 0.2], 40, seed=3)
+    kw = dict(mode=mode, alpha=0.8, max_iter=6, trace=True)
+    a = oracle.decode_code(c, syn, L0, flags=oracle.FLAG_NO_EARLY_STOP, **kw)
+    b = oracle.decode_code(c, syn, L0, flags=oracle.FLAG_NO_EARLY_STOP | LAYERED, **kw)
+    assert np.array_equal(a["trace"], b["trace"]) and np.array_equal(a["err"], b["err"])
+
+
+def test_layered_differs_from_flooding_on_a_loopy_code():
+    """Sanity of the flag itself: on a GB code the layered posteriors after one round differ
+    from the flooding ones (a later layer sees messages replaced earlier in the round)."""
+    c = I.gb_code(63, 3)
+    _, syn, L0, _ = I.workload(c, [0.05], 8, seed=4)
+    kw = dict(mode=oracle.SAGMS, max_iter=1, trace=True)
+    a = oracle.decode_code(c, syn, L0, flags=oracle.FLAG_NO_EARLY_STOP, **kw)["trace"][:, 1]
+    b = oracle.decode_code(c, syn, L0, flags=oracle.FLAG_NO_EARLY_STOP | LAYERED, **kw)["trace"][:, 1]
+    assert not np.array_equal(a, b)
