@@ -56,7 +56,16 @@ enum {
      * check degree d_c (alpha* decreases in d_c, Prop. 1, so on an irregular code this is
      * the most conservative ceiling), clamped to [alpha_min, 1/eta_unsat]; a zero prior gets
      * alpha_min.  params.alpha_max is then ignored. */
-    SAGMS_FLAG_AUTO_CEILING = 16u
+    SAGMS_FLAG_AUTO_CEILING = 16u,
+    /* MS family only (SAGMS, SMS, MS), check degrees <= 24: a layered (serial-check)
+     * schedule in place of Algorithm 1's flooding one -- a different decoder, with its own
+     * results.  The checks form layers that share no qubit (check i joins the smallest
+     * layer used by no earlier check sharing a qubit with it); a round visits the layers in
+     * increasing order, and each check computes its Eq. 2 inputs from the messages as they
+     * stand, including those replaced earlier in the same round.  The gains of Eq. 7 come
+     * from the residual at the start of each round, the stopping rule and outputs are those
+     * of Algorithm 1, and d_iters counts rounds.  The plan's kernel choice does not apply. */
+    SAGMS_FLAG_LAYERED = 32u
 };
 
 /* Status codes. */

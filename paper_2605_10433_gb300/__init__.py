@@ -14,6 +14,7 @@ FLAG_L0_PER_QUBIT = 1
 FLAG_NO_EARLY_STOP = 2
 FLAG_GENERIC_KERNEL = 4
 FLAG_AUTO_CEILING = 16
+FLAG_LAYERED = 32
 
 
 @dataclass

@@ -1,0 +1,217 @@
+// Layered (serial-check) schedule for the MS family (SAGMS_FLAG_LAYERED).
+//
+// The checks are split into layers whose checks share no qubit: check i joins the smallest
+// layer used by no earlier check sharing a qubit with it (first-fit in index order, computed
+// at load time).  A round visits the layers in order; every check of a layer takes its
+// inputs from the posteriors as they stand, so a later layer already sees the messages an
+// earlier one replaced in the same round.  With P_j = L0_j + sum of the current CN->VN
+// messages of qubit j, the check update of Eqs. 2, 4 and 8 becomes, per edge:
+//   v_j = P_j - c_old(i, j)        (Eq. 2's extrinsic input)
+//   c_new(i, j) from the v of the check, as in the flooding kernels
+//   P_j = v_j + c_new(i, j)
+// Checks of one layer touch disjoint qubits, so one thread per check updates P in place.
+// The gains of a round come from the residual syndrome at its start (Eqs. 1, 6, 7).
+//
+// One CTA of T threads decodes one shot at a time (static stride over shots).  Shared
+// memory holds, per shot:
+//   P[Np]          posteriors (column n and up: +inf, the target of padded check slots)
+//   PQ[Np]         per-qubit priors (SAGMS_FLAG_L0_PER_QUBIT only)
+//   O1[Mp], O2[Mp] magnitudes min(g*min1, clip), min(g*min2, clip) of each check's last output
+//   meta[Mp]       bit j: sign of the output on slot j; bits 24..28: slot of the first minimum
+//   sbits, rbits   input syndrome (check order) and residual bits (layer order)
+// A check's outputs take two magnitudes only, so (O1, O2, meta) rebuilds every old message
+// exactly: slot j carries O2 if it holds the first minimum, else O1 (two slots tying at the
+// minimum have O1 == O2).  The check records (columns and check index, layer order) stay in
+// global memory, read through the read-only cache.
+#pragma once
+
+#include "decode_kernel.cuh"
+
+namespace sagms {
+
+// Record of one check in layer order: its DC columns (n = padding) and then its index, as
+// u16, padded to whole 16-byte vectors.
+template <int DC>
+struct LayeredRec {
+    static constexpr int R = (DC + 1 + 7) / 8 * 8;
+};
+
+struct LayeredLayout {
+    const uint16_t* rec;  // [m][R]
+    const int* lay_ptr;   // [L + 1] first position of each layer
+    int L;
+};
+
+__host__ __device__ inline size_t layered_smem_bytes(int Mp, int Np, bool per_qubit) {
+    return (size_t)Np * 4 * (per_qubit ? 2 : 1) + (size_t)Mp * 12 + (size_t)(Mp / 32) * 8 + 16;
+}
+
+template <int DC, int T>
+__global__ void __launch_bounds__(T) layered_kernel(const DecodeArgs a, const LayeredLayout lay) {
+    constexpr int R = LayeredRec<DC>::R;
+    static_assert(DC <= 24 && T % 32 == 0, "layout");
+    extern __shared__ __align__(16) unsigned char smem[];
+    const bool per_qubit = (a.flags & kFlagPerQubit) != 0;
+    const bool early = (a.flags & kFlagNoEarlyStop) == 0;
+    const int t = threadIdx.x;
+    const int lane = t & 31;
+    const int n = a.n, m = a.m, Np = a.Np, Mp = a.Mp;
+    const int mw = (m + 31) >> 5, nw = (n + 31) >> 5;
+    float* P = reinterpret_cast<float*>(smem);
+    float* PQ = P + Np;
+    float* O1 = PQ + (per_qubit ? Np : 0);
+    float* O2 = O1 + Mp;
+    uint32_t* meta = reinterpret_cast<uint32_t*>(O2 + Mp);
+    uint32_t* sbits = meta + Mp;
+    uint32_t* rbits = sbits + Mp / 32;
+    int* cnt_sh = reinterpret_cast<int*>(rbits + Mp / 32);
+    const uint4* rec = reinterpret_cast<const uint4*>(lay.rec);
+    const float inf = __uint_as_float(0x7f800000u);
+
+    auto sync = [] {
+        if constexpr (T == 32) __syncwarp();
+        else __syncthreads();
+    };
+    // columns and check index of the check at layer position p
+    auto load_rec = [&](int p, int (&col)[DC]) {
+        uint32_t w[R / 2];
+#pragma unroll
+        for (int k = 0; k < R / 8; ++k) {
+            const uint4 u = __ldg(rec + (size_t)p * (R / 8) + k);
+            w[4 * k] = u.x; w[4 * k + 1] = u.y; w[4 * k + 2] = u.z; w[4 * k + 3] = u.w;
+        }
+#pragma unroll
+        for (int j = 0; j < DC; ++j) col[j] = (int)((w[j >> 1] >> (16 * (j & 1))) & 0xffffu);
+        return (int)((w[DC >> 1] >> (16 * (DC & 1))) & 0xffffu);
+    };
+
+    for (int c = n + t; c < Np; c += T) P[c] = inf;
+    int pq_ok = 1;
+    if (per_qubit) {
+        for (int c = t; c < n; c += T) {
+            const float v = __ldg(a.L0 + c) + 0.0f;   // -0 -> +0: the sign bit is the decision
+            PQ[c] = v;
+            pq_ok &= isfinite(v) ? 1 : 0;
+        }
+    }
+    if constexpr (T == 32) pq_ok = __all_sync(0xffffffffu, pq_ok);
+    else pq_ok = __syncthreads_and(pq_ok);
+
+    for (long long shot = blockIdx.x; shot < a.shots; shot += gridDim.x) {
+        float prior = 0.0f;
+        float amax = a.amax;
+        bool valid;
+        if (per_qubit) {
+            valid = pq_ok != 0;
+        } else {
+            const float l0 = __ldg(a.L0 + shot);
+            valid = isfinite(l0);
+            prior = (l0 > 0.0f) ? 1.0f : ((l0 < 0.0f) ? -1.0f : 0.0f);
+            if (valid) amax = shot_alpha_max(a, l0);
+        }
+        if (!valid) {
+            for (int w = t; w < nw; w += T) a.err[shot * nw + w] = 0u;
+            if (t == 0) { a.conv[shot] = 0; a.iters[shot] = -1; }
+            continue;
+        }
+        // A0: P = L0, every message zero, load s
+        for (int c = t; c < n; c += T) P[c] = per_qubit ? PQ[c] : prior;
+        for (int p = t; p < Mp; p += T) { O1[p] = 0.0f; O2[p] = 0.0f; meta[p] = 0u; }
+        for (int w = t; w < mw; w += T) sbits[w] = __ldg(a.syn + shot * mw + w);
+        if (t == 0) { cnt_sh[0] = 0; cnt_sh[1] = 0; }
+        sync();
+
+        int it = 0, cnt = 0;
+        for (;; ++it) {
+            // A5: hard decision and residual bit of every check (Eq. 1), count (Eq. 6)
+            for (int base = 0; base < Mp; base += T) {
+                const int p = base + t;
+                uint32_t x = 0u;
+                if (p < m) {
+                    int col[DC];
+                    const int i = load_rec(p, col);
+                    x = (sbits[i >> 5] >> (i & 31)) & 1u;
+#pragma unroll
+                    for (int j = 0; j < DC; ++j) x ^= __float_as_uint(P[col[j]]) >> 31;
+                }
+                const uint32_t b = __ballot_sync(0xffffffffu, x);
+                if (lane == 0 && p < Mp) {
+                    rbits[p >> 5] = b;
+                    if (b) atomicAdd(&cnt_sh[it & 1], __popc(b));
+                }
+            }
+            sync();
+            cnt = cnt_sh[it & 1];
+            if (a.trace) {
+                float* tr = a.trace + ((size_t)shot * (size_t)(a.max_iter + 1) + (size_t)it) * (size_t)n;
+                for (int c = t; c < n; c += T) tr[c] = P[c];
+            }
+            // A6
+            if ((cnt == 0 && early) || it == a.max_iter) break;
+            if (t == 0) cnt_sh[(it + 1) & 1] = 0;
+            // A2: the round's gain (Eq. 7), boosted on unsatisfied checks
+            const float g0 = (a.mode == kModeSAGMS) ? amax - (amax - a.amin) * ((float)cnt * a.inv_m)
+                                                    : ((a.mode == kModeSMS) ? a.alpha : 1.0f);
+            // A3 + A4, layer by layer
+            for (int l = 0; l < lay.L; ++l) {
+                const int p1 = __ldg(lay.lay_ptr + l + 1);
+                for (int p = __ldg(lay.lay_ptr + l) + t; p < p1; p += T) {
+                    int col[DC];
+                    const int i = load_rec(p, col);
+                    const uint32_t s_i = (sbits[i >> 5] >> (i & 31)) & 1u;
+                    const float g = (a.mode == kModeSAGMS && ((rbits[p >> 5] >> (p & 31)) & 1u)) ? g0 * a.eta : g0;
+                    const uint32_t mt = meta[p];
+                    const float q1 = O1[p], q2 = O2[p];
+                    const int am = (int)(mt >> 24);
+                    float v[DC];
+                    uint32_t par = s_i << 31;
+#pragma unroll
+                    for (int j = 0; j < DC; ++j) {
+                        const float mag = (j == am) ? q2 : q1;
+                        const float c_old = __uint_as_float(__float_as_uint(mag) | (((mt >> j) & 1u) << 31));
+                        v[j] = P[col[j]] - c_old;
+                        par ^= __float_as_uint(v[j]);
+                    }
+                    par &= kSign;
+                    float m1 = inf, m2 = inf;
+                    int amn = 0;
+#pragma unroll
+                    for (int j = 0; j < DC; ++j) {
+                        const float av = fabsf(v[j]);
+                        m2 = fminf(m2, fmaxf(m1, av));
+                        amn = (av < m1) ? j : amn;
+                        m1 = fminf(m1, av);
+                    }
+                    const float o1 = fminf(g * m1, kMsFamClip), o2 = fminf(g * m2, kMsFamClip);
+                    uint32_t nm = (uint32_t)amn << 24;
+#pragma unroll
+                    for (int j = 0; j < DC; ++j) {
+                        const uint32_t sg = (par ^ __float_as_uint(v[j])) & kSign;
+                        const float mag = (fabsf(v[j]) == m1) ? o2 : o1;
+                        P[col[j]] = v[j] + __uint_as_float(__float_as_uint(mag) | sg);
+                        nm |= (sg >> 31) << j;
+                    }
+                    O1[p] = o1;
+                    O2[p] = o2;
+                    meta[p] = nm;
+                }
+                sync();
+            }
+        }
+
+        // A7: write-out
+        for (int base = 0; base < n; base += T) {
+            const int c = base + t;
+            const bool b = (c < n) && (__float_as_uint(P[c]) >> 31);
+            const uint32_t word = __ballot_sync(0xffffffffu, b);
+            if (lane == 0 && c < n) a.err[shot * nw + (c >> 5)] = word;
+        }
+        if (t == 0) {
+            a.conv[shot] = (cnt == 0) ? 1 : 0;
+            a.iters[shot] = it;
+        }
+        sync();
+    }
+}
+
+}  // namespace sagms

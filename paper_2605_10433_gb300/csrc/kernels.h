@@ -6,6 +6,7 @@
 #include <cstddef>
 #include <cstdint>
 
+#include "decode_layered.cuh"
 #include "decode_qc.cuh"
 
 namespace sagms_kernels {
@@ -51,5 +52,13 @@ inline int num_qc_variants() { return kNumQcSmall + kNumQcLarge; }
 inline const QcVariant& qc_variant(int v) {
     return v < kNumQcSmall ? kQcVariantsSmall[v] : kQcVariantsLarge[v - kNumQcSmall];
 }
+
+// Layered schedule (decode_layered.cuh), MS family: (padded check degree, threads per CTA).
+// A code takes the first check degree that covers it, with 32 threads when no layer holds
+// more than 64 checks and 128 otherwise.
+using LayeredFn = void (*)(const DecodeArgs, const sagms::LayeredLayout);
+struct LayeredVariant { int dc, t; LayeredFn fn; };
+extern const LayeredVariant kLayeredVariants[];
+extern const int kNumLayeredVariants;
 
 }  // namespace sagms_kernels

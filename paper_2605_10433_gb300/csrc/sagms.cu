@@ -182,6 +182,38 @@ int check_csr(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, const i
     return SAGMS_OK;
 }
 
+// First-fit layers of the checks in index order: check i joins the smallest layer that no
+// earlier check sharing a qubit with it uses, so the checks of a layer share no qubit.
+// order: the checks by (layer, index); lay_ptr[l]: position of layer l's first check.
+void first_fit_layers(int m, int n, const int32_t* row_ptr, const int32_t* col_idx, std::vector<int>& order,
+                      std::vector<int>& lay_ptr) {
+    std::vector<int> cptr(n + 1, 0), cchk(row_ptr[m]);
+    for (int e = 0; e < row_ptr[m]; ++e) cptr[col_idx[e] + 1]++;
+    for (int j = 0; j < n; ++j) cptr[j + 1] += cptr[j];
+    {
+        std::vector<int> fill(cptr.begin(), cptr.end() - 1);
+        for (int i = 0; i < m; ++i)
+            for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) cchk[fill[col_idx[e]]++] = i;
+    }
+    std::vector<int> layer(m, 0), seen(m + 1, -1);
+    int L = 0;
+    for (int i = 0; i < m; ++i) {
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+            for (int u = cptr[col_idx[e]]; u < cptr[col_idx[e] + 1]; ++u)
+                if (cchk[u] < i) seen[layer[cchk[u]]] = i;
+        int l = 0;
+        while (seen[l] == i) ++l;
+        layer[i] = l;
+        L = std::max(L, l + 1);
+    }
+    lay_ptr.assign(L + 1, 0);
+    for (int i = 0; i < m; ++i) lay_ptr[layer[i] + 1]++;
+    for (int l = 0; l < L; ++l) lay_ptr[l + 1] += lay_ptr[l];
+    order.assign(m, 0);
+    std::vector<int> fill(lay_ptr.begin(), lay_ptr.end() - 1);
+    for (int i = 0; i < m; ++i) order[fill[layer[i]]++] = i;
+}
+
 // Column-indexed slots of a code for D message rows: the CSR order when it already gives every
 // qubit distinct slots mod D, else an edge colouring (empty if neither).
 std::vector<int> column_slots(int m, int n, const int32_t* row_ptr, const int32_t* col_idx, int D) {
@@ -267,6 +299,11 @@ struct sagms_code {
     int qc_variant;        // -1: no column-indexed kernel for this code
     uint32_t* d_colQ;      // qc_layout
     uint16_t* d_qchk;      // [dv_max][n] checks of each qubit, 0xFFFF padding (Monte Carlo sampler)
+    int lay_variant;       // -1: no layered-schedule kernel for this code (check degree above 24)
+    int lay_L;             // layers of the first-fit partition
+    int lay_max;           // checks in the largest layer
+    uint16_t* d_lrec;      // [m][R] check records in layer order (LayeredRec)
+    int* d_lptr;           // [lay_L + 1] first position of each layer
     int k_logicals;        // logical operators attached for the Monte Carlo check (-1: none)
     uint32_t* d_logicals;  // [k][ceil(n/32)]
     // Launch plan chosen by sagms_autotune (0 = defaults), packed so decodes on other
@@ -301,8 +338,10 @@ double sagms_alpha_star(double L0, int32_t dc) {
 int sagms_check_params(const sagms_params* p) {
     if (!p) return fail(SAGMS_ERR_ARG, "params is NULL");
     if (p->flags & ~(uint32_t)(SAGMS_FLAG_L0_PER_QUBIT | SAGMS_FLAG_NO_EARLY_STOP | SAGMS_FLAG_GENERIC_KERNEL |
-                               SAGMS_FLAG_AUTO_CEILING))
+                               SAGMS_FLAG_AUTO_CEILING | SAGMS_FLAG_LAYERED))
         return fail(SAGMS_ERR_ARG, "unknown flag bits 0x%x", p->flags);
+    if ((p->flags & SAGMS_FLAG_LAYERED) && p->mode == SAGMS_BP)
+        return fail(SAGMS_ERR_PARAM, "SAGMS_FLAG_LAYERED applies to the MS family only");
     const bool auto_ceiling = (p->flags & SAGMS_FLAG_AUTO_CEILING) != 0;
     if (auto_ceiling && p->mode != SAGMS_SAGMS)
         return fail(SAGMS_ERR_PARAM, "SAGMS_FLAG_AUTO_CEILING applies to the SAGMS mode only");
@@ -485,6 +524,29 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
     std::vector<uint32_t> colQ;
     if (qv >= 0) colQ = qc_layout(m, row_ptr, col_idx, qslot, qc_variant(qv));
 
+    // Layered schedule: first-fit layers and, in layer order, each check's record (columns,
+    // padding n, then the check index).
+    int lv = -1, lay_max = 0;
+    std::vector<int> lorder, lptr;
+    std::vector<uint16_t> lrec;
+    first_fit_layers(m, n, row_ptr, col_idx, lorder, lptr);
+    for (size_t l = 0; l + 1 < lptr.size(); ++l) lay_max = std::max(lay_max, lptr[l + 1] - lptr[l]);
+    for (int v = 0; v < kNumLayeredVariants && lv < 0; ++v) {
+        const LayeredVariant& V = kLayeredVariants[v];
+        if (dc_max <= V.dc && V.t == (lay_max <= 64 ? 32 : 128)) lv = v;
+    }
+    if (lv >= 0) {
+        const int DCl = kLayeredVariants[lv].dc, R = (DCl + 1 + 7) / 8 * 8;
+        lrec.assign((size_t)m * R, (uint16_t)0);
+        for (int p = 0; p < m; ++p) {
+            const int i = lorder[p];
+            uint16_t* r = lrec.data() + (size_t)p * R;
+            for (int j = 0; j < DCl; ++j) r[j] = (uint16_t)n;
+            for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) r[e - row_ptr[i]] = (uint16_t)col_idx[e];
+            r[DCl] = (uint16_t)i;
+        }
+    }
+
     // Checks of each qubit, for syndrome formation in the Monte Carlo sampler.
     std::vector<uint16_t> qchk((size_t)dv_max * n, (uint16_t)0xFFFFu);
     for (int c = 0; c < n; ++c)
@@ -495,6 +557,11 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
     sagms_code* code = new sagms_code();
     code->qc_variant = qv;
+    code->lay_variant = lv;
+    code->lay_L = (int)lptr.size() - 1;
+    code->lay_max = lay_max;
+    code->d_lrec = nullptr;
+    code->d_lptr = nullptr;
     code->d_qchk = nullptr;
     code->k_logicals = -1;
     code->d_logicals = nullptr;
@@ -540,6 +607,12 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
         ce = cudaMalloc(&code->d_colQ, colQ.size() * sizeof(uint32_t));
         if (ce == cudaSuccess) ce = cudaMemcpy(code->d_colQ, colQ.data(), colQ.size() * 4, cudaMemcpyHostToDevice);
     }
+    if (ce == cudaSuccess && lv >= 0) {
+        ce = cudaMalloc(&code->d_lrec, lrec.size() * sizeof(uint16_t));
+        if (ce == cudaSuccess) ce = cudaMalloc(&code->d_lptr, lptr.size() * sizeof(int));
+        if (ce == cudaSuccess) ce = cudaMemcpy(code->d_lrec, lrec.data(), lrec.size() * 2, cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess) ce = cudaMemcpy(code->d_lptr, lptr.data(), lptr.size() * 4, cudaMemcpyHostToDevice);
+    }
     if (ce == cudaSuccess) {
         ce = cudaMalloc(&code->d_qchk, qchk.size() * sizeof(uint16_t));
         if (ce == cudaSuccess) ce = cudaMemcpy(code->d_qchk, qchk.data(), qchk.size() * 2, cudaMemcpyHostToDevice);
@@ -553,6 +626,8 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
         cudaFree(code->d_colG);
         cudaFree(code->d_vneG);
         cudaFree(code->d_colQ);
+        cudaFree(code->d_lrec);
+        cudaFree(code->d_lptr);
         delete code;
         return cuda_fail(ce, "sagms_load_code upload");
     }
@@ -572,6 +647,8 @@ void sagms_free_code(sagms_code* code) {
     cudaFree(code->d_colG);
     cudaFree(code->d_vneG);
     cudaFree(code->d_colQ);
+    cudaFree(code->d_lrec);
+    cudaFree(code->d_lptr);
     cudaFree(code->d_qchk);
     cudaFree(code->d_logicals);
     if (prev >= 0 && prev != code->device) cudaSetDevice(prev);
@@ -597,6 +674,37 @@ int sagms_code_kernels(const sagms_code* code, uint32_t* mask) {
 }  // extern "C"
 
 namespace {
+
+// The layered-schedule kernel: one shot per CTA at a time, CTAs striding over the batch.
+int launch_layered(const sagms_code* code, const DecodeArgs& a, bool per_qubit, cudaStream_t stream) {
+    if (code->lay_variant < 0)
+        return fail(SAGMS_ERR_DEGREE, "the layered schedule supports check degrees up to 24 (code has %d)",
+                    code->dc_max);
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
+    if (dev != code->device) return fail(SAGMS_ERR_ARG, "code was loaded on device %d, current is %d", code->device, dev);
+    const LayeredVariant& V = kLayeredVariants[code->lay_variant];
+    const size_t smem = layered_smem_bytes(code->Mp, code->Np, per_qubit);
+    int smem_optin = 0, sms = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (smem > (size_t)smem_optin)
+        return fail(SAGMS_ERR_SIZE, "code needs %zu B of shared memory per CTA (limit %d)", smem, smem_optin);
+    const void* fn = reinterpret_cast<const void*>(V.fn);
+    ce = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaFuncSetAttribute");
+    int per_sm = 0;
+    ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, V.t, smem);
+    if (ce != cudaSuccess) return cuda_fail(ce, "occupancy query");
+    if (per_sm < 1) return fail(SAGMS_ERR_SIZE, "kernel does not fit on an SM");
+    const long long grid = std::min<long long>(a.shots, (long long)per_sm * sms);
+    const LayeredLayout lay{code->d_lrec, code->d_lptr, code->lay_L};
+    V.fn<<<(unsigned)grid, V.t, smem, stream>>>(a, lay);
+    ce = cudaGetLastError();
+    if (ce != cudaSuccess) return cuda_fail(ce, "decode launch");
+    return SAGMS_OK;
+}
 
 int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, const uint32_t* d_syn,
                   const float* d_L0, uint32_t* d_err, uint8_t* d_conv, int32_t* d_iters, float* d_trace,
@@ -627,6 +735,7 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     a.syn = d_syn; a.L0 = d_L0; a.err = d_err; a.conv = d_conv; a.iters = d_iters; a.trace = d_trace;
     a.work = nullptr;
     a.chunk_lg = 1;
+    if (p->flags & SAGMS_FLAG_LAYERED) return launch_layered(code, a, per_qubit, stream);
 
     const Plan plan = plan_override ? *plan_override : unpack_plan(code->plan.load());
     // Kernel: the plan's choice where the code and parameters allow it, else the fastest

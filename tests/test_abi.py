@@ -57,6 +57,10 @@ def test_version_and_alpha_star(native):
     (dict(mode=0, max_iter=-1), False),
     (dict(mode=7, max_iter=10), False),
     (dict(mode=3, max_iter=10, flags=16), False),
+    (dict(mode=2, alpha_min=0.3, alpha_max=0.5, eta_unsat=1.1, max_iter=100, flags=32), True),   # layered
+    (dict(mode=0, max_iter=100, flags=32 | 1 | 2), True),
+    (dict(mode=3, max_iter=10, flags=32), False),      # layered: MS family only
+    (dict(mode=0, max_iter=10, flags=64), False),      # unknown flag
 ])
 def test_param_validation(native, kw, ok):
     p = native.sagms_params(**kw)
