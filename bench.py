@@ -303,7 +303,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--shots", type=int, default=10_000_000)
     ap.add_argument("--ref-sample", type=int, default=40000)
-    ap.add_argument("--cpu-sample", type=int, default=16000)
+    ap.add_argument("--cpu-sample", type=int, default=40000)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--mode-steps", type=int, default=3)
     ap.add_argument("--no-extras", action="store_true", help="skip the SMS / MS lines and the CPU baseline")
@@ -470,6 +470,10 @@ def main():
                                "sample": f"first {args.cpu_sample} shots of the same batch (FP64 C oracle, "
                                          f"{threads} threads)",
                                "oracle_fer_syn": float((r["conv"] == 0).mean()), "gpu_oracle_identical": same}
+        one = max(1, args.cpu_sample // 16)
+        _, dt1 = cpu_oracle_sample(code, syn, L0, one, 1)
+        out["cpu_baseline"]["single_thread"] = {"value": one / dt1, "unit": UNIT, "cores": 1,
+                                                "sample": f"first {one} shots, one thread"}
     if rank == 0:
         print(json.dumps(out))
     if dist is not None:

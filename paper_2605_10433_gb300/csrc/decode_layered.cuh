@@ -21,19 +21,23 @@
 //   sbits, rbits   input syndrome (check order) and residual bits (layer order)
 // A check's outputs take two magnitudes only, so (O1, O2, meta) rebuilds every old message
 // exactly: slot j carries O2 if it holds the first minimum, else O1 (two slots tying at the
-// minimum have O1 == O2).  The check records (columns and check index, layer order) stay in
-// global memory, read through the read-only cache.
+// minimum have O1 == O2).  A shot's first round reads no old message (all are zero), so it
+// runs a copy of the loop without the rebuild, and with one prior per shot the residual before
+// it has a closed form.  The check records (columns, check index and degree, layer order) stay
+// in global memory, read through the read-only cache.
 #pragma once
+
+#include <type_traits>
 
 #include "decode_kernel.cuh"
 
 namespace sagms {
 
-// Record of one check in layer order: its DC columns (n = padding) and then its index, as
-// u16, padded to whole 16-byte vectors.
+// Record of one check in layer order: its DC columns (n = padding), its index and its degree,
+// as u16, padded to whole 16-byte vectors.
 template <int DC>
 struct LayeredRec {
-    static constexpr int R = (DC + 1 + 7) / 8 * 8;
+    static constexpr int R = (DC + 2 + 7) / 8 * 8;
 };
 
 struct LayeredLayout {
@@ -84,6 +88,69 @@ __global__ void __launch_bounds__(T) layered_kernel(const DecodeArgs a, const La
         for (int j = 0; j < DC; ++j) col[j] = (int)((w[j >> 1] >> (16 * (j & 1))) & 0xffffu);
         return (int)((w[DC >> 1] >> (16 * (DC & 1))) & 0xffffu);
     };
+    // check index and degree of the check at layer position p
+    auto load_head = [&](int p, int& deg) {
+        const uint16_t* r = lay.rec + (size_t)p * R;
+        deg = (int)__ldg(r + DC + 1);
+        return (int)__ldg(r + DC);
+    };
+    // One round over the layers (A3 + A4).  FRESH: the shot's first round, where every old
+    // message is zero (v = P) and the check state is written without being read.
+    auto sweep = [&](auto fresh, float g0) {
+        constexpr bool FRESH = decltype(fresh)::value;
+        for (int l = 0; l < lay.L; ++l) {
+            const int p1 = __ldg(lay.lay_ptr + l + 1);
+            for (int p = __ldg(lay.lay_ptr + l) + t; p < p1; p += T) {
+                int col[DC];
+                const int i = load_rec(p, col);
+                const uint32_t s_i = (sbits[i >> 5] >> (i & 31)) & 1u;
+                const float g = (a.mode == kModeSAGMS && ((rbits[p >> 5] >> (p & 31)) & 1u)) ? g0 * a.eta : g0;
+                float v[DC];
+                uint32_t par = s_i << 31;
+                if constexpr (FRESH) {
+#pragma unroll
+                    for (int j = 0; j < DC; ++j) {
+                        v[j] = P[col[j]];
+                        par ^= __float_as_uint(v[j]);
+                    }
+                } else {
+                    const uint32_t mt = meta[p];
+                    const float q1 = O1[p], q2 = O2[p];
+                    const int am = (int)(mt >> 24);
+#pragma unroll
+                    for (int j = 0; j < DC; ++j) {
+                        const float mag = (j == am) ? q2 : q1;
+                        const float c_old = __uint_as_float(__float_as_uint(mag) | (((mt >> j) & 1u) << 31));
+                        v[j] = P[col[j]] - c_old;
+                        par ^= __float_as_uint(v[j]);
+                    }
+                }
+                par &= kSign;
+                float m1 = inf, m2 = inf;
+                int amn = 0;
+#pragma unroll
+                for (int j = 0; j < DC; ++j) {
+                    const float av = fabsf(v[j]);
+                    m2 = fminf(m2, fmaxf(m1, av));
+                    amn = (av < m1) ? j : amn;
+                    m1 = fminf(m1, av);
+                }
+                const float o1 = fminf(g * m1, kMsFamClip), o2 = fminf(g * m2, kMsFamClip);
+                uint32_t nm = (uint32_t)amn << 24;
+#pragma unroll
+                for (int j = 0; j < DC; ++j) {
+                    const uint32_t sg = (par ^ __float_as_uint(v[j])) & kSign;
+                    const float mag = (fabsf(v[j]) == m1) ? o2 : o1;
+                    P[col[j]] = v[j] + __uint_as_float(__float_as_uint(mag) | sg);
+                    nm |= (sg >> 31) << j;
+                }
+                O1[p] = o1;
+                O2[p] = o2;
+                meta[p] = nm;
+            }
+            sync();
+        }
+    };
 
     for (int c = n + t; c < Np; c += T) P[c] = inf;
     int pq_ok = 1;
@@ -114,20 +181,26 @@ __global__ void __launch_bounds__(T) layered_kernel(const DecodeArgs a, const La
             if (t == 0) { a.conv[shot] = 0; a.iters[shot] = -1; }
             continue;
         }
-        // A0: P = L0, every message zero, load s
+        // A0: P = L0, load s (every message is zero: the first round reads no check state)
         for (int c = t; c < n; c += T) P[c] = per_qubit ? PQ[c] : prior;
-        for (int p = t; p < Mp; p += T) { O1[p] = 0.0f; O2[p] = 0.0f; meta[p] = 0u; }
         for (int w = t; w < mw; w += T) sbits[w] = __ldg(a.syn + shot * mw + w);
         if (t == 0) { cnt_sh[0] = 0; cnt_sh[1] = 0; }
         sync();
 
         int it = 0, cnt = 0;
         for (;; ++it) {
-            // A5: hard decision and residual bit of every check (Eq. 1), count (Eq. 6)
+            // A5: hard decision and residual bit of every check (Eq. 1), count (Eq. 6).  Before
+            // the first round with one prior per shot every decision is [L0 < 0], so a check's
+            // residual is its syndrome bit XOR, under a negative prior, its degree's parity.
+            const bool closed = it == 0 && !per_qubit;
             for (int base = 0; base < Mp; base += T) {
                 const int p = base + t;
                 uint32_t x = 0u;
-                if (p < m) {
+                if (p < m && closed) {
+                    int deg;
+                    const int i = load_head(p, deg);
+                    x = ((sbits[i >> 5] >> (i & 31)) ^ (prior < 0.0f ? (uint32_t)deg : 0u)) & 1u;
+                } else if (p < m) {
                     int col[DC];
                     const int i = load_rec(p, col);
                     x = (sbits[i >> 5] >> (i & 31)) & 1u;
@@ -153,50 +226,8 @@ __global__ void __launch_bounds__(T) layered_kernel(const DecodeArgs a, const La
             const float g0 = (a.mode == kModeSAGMS) ? amax - (amax - a.amin) * ((float)cnt * a.inv_m)
                                                     : ((a.mode == kModeSMS) ? a.alpha : 1.0f);
             // A3 + A4, layer by layer
-            for (int l = 0; l < lay.L; ++l) {
-                const int p1 = __ldg(lay.lay_ptr + l + 1);
-                for (int p = __ldg(lay.lay_ptr + l) + t; p < p1; p += T) {
-                    int col[DC];
-                    const int i = load_rec(p, col);
-                    const uint32_t s_i = (sbits[i >> 5] >> (i & 31)) & 1u;
-                    const float g = (a.mode == kModeSAGMS && ((rbits[p >> 5] >> (p & 31)) & 1u)) ? g0 * a.eta : g0;
-                    const uint32_t mt = meta[p];
-                    const float q1 = O1[p], q2 = O2[p];
-                    const int am = (int)(mt >> 24);
-                    float v[DC];
-                    uint32_t par = s_i << 31;
-#pragma unroll
-                    for (int j = 0; j < DC; ++j) {
-                        const float mag = (j == am) ? q2 : q1;
-                        const float c_old = __uint_as_float(__float_as_uint(mag) | (((mt >> j) & 1u) << 31));
-                        v[j] = P[col[j]] - c_old;
-                        par ^= __float_as_uint(v[j]);
-                    }
-                    par &= kSign;
-                    float m1 = inf, m2 = inf;
-                    int amn = 0;
-#pragma unroll
-                    for (int j = 0; j < DC; ++j) {
-                        const float av = fabsf(v[j]);
-                        m2 = fminf(m2, fmaxf(m1, av));
-                        amn = (av < m1) ? j : amn;
-                        m1 = fminf(m1, av);
-                    }
-                    const float o1 = fminf(g * m1, kMsFamClip), o2 = fminf(g * m2, kMsFamClip);
-                    uint32_t nm = (uint32_t)amn << 24;
-#pragma unroll
-                    for (int j = 0; j < DC; ++j) {
-                        const uint32_t sg = (par ^ __float_as_uint(v[j])) & kSign;
-                        const float mag = (fabsf(v[j]) == m1) ? o2 : o1;
-                        P[col[j]] = v[j] + __uint_as_float(__float_as_uint(mag) | sg);
-                        nm |= (sg >> 31) << j;
-                    }
-                    O1[p] = o1;
-                    O2[p] = o2;
-                    meta[p] = nm;
-                }
-                sync();
-            }
+            if (it == 0) sweep(std::true_type{}, g0);
+            else sweep(std::false_type{}, g0);
         }
 
         // A7: write-out

@@ -214,6 +214,72 @@ void first_fit_layers(int m, int n, const int32_t* row_ptr, const int32_t* col_i
     for (int i = 0; i < m; ++i) order[fill[layer[i]]++] = i;
 }
 
+// Proper D-edge-colouring of a bipartite multigraph whose vertex degrees are at most D
+// (Koenig's theorem), by alternating paths: an edge takes a colour a free at its left end;
+// if a is taken at its right end, where b is free, the a/b path leaving the right end swaps
+// its colours first.  edges[e] = (left, right).  Returns the colour of every edge.
+std::vector<int> bipartite_edge_colouring(int nl, int nr, const std::vector<std::pair<int, int>>& edges, int D) {
+    std::vector<int> colour(edges.size(), -1), atl((size_t)nl * D, -1), atr((size_t)nr * D, -1);
+    std::vector<int> path;
+    for (size_t e = 0; e < edges.size(); ++e) {
+        const int u = edges[e].first, v = edges[e].second;
+        int a = 0, b = 0;
+        while (atl[(size_t)u * D + a] >= 0) ++a;
+        while (atr[(size_t)v * D + b] >= 0) ++b;
+        if (atr[(size_t)v * D + a] >= 0) {
+            path.clear();
+            int x = v, cur = a;
+            bool right = true;
+            for (;;) {
+                const int f = right ? atr[(size_t)x * D + cur] : atl[(size_t)x * D + cur];
+                if (f < 0) break;
+                path.push_back(f);
+                x = right ? edges[f].first : edges[f].second;
+                right = !right;
+                cur = (cur == a) ? b : a;
+            }
+            for (int f : path) {
+                atl[(size_t)edges[f].first * D + colour[f]] = -1;
+                atr[(size_t)edges[f].second * D + colour[f]] = -1;
+            }
+            for (int f : path) {
+                colour[f] = (colour[f] == a) ? b : a;
+                atl[(size_t)edges[f].first * D + colour[f]] = f;
+                atr[(size_t)edges[f].second * D + colour[f]] = f;
+            }
+        }
+        colour[e] = a;
+        atl[(size_t)u * D + a] = (int)e;
+        atr[(size_t)v * D + a] = (int)e;
+    }
+    return colour;
+}
+
+// Slot order of the records of one warp of the layered kernel (up to 32 checks that update
+// together): at slot step j the warp gathers one posterior per check, and two of them in the
+// same shared-memory bank (column mod 32) serialise.  Each bank is split into copies of at
+// most DC columns, and the graph of checks and bank copies is DC-edge-coloured: colour j is
+// the slot of a column, so at every step a bank serves at most as many columns as it has
+// copies, ceil(columns in the bank / DC).  rows[k]: the columns of the warp's k-th check;
+// out[k][j]: the column in slot j, pad where none.
+void warp_slot_order(const std::vector<std::vector<int>>& rows, int DC, int pad, std::vector<std::vector<int>>& out) {
+    std::vector<std::pair<int, int>> edges;
+    std::vector<int> ecol, deg(32, 0);
+    int ncopies = 0;
+    std::vector<std::vector<int>> bank_copies(32);
+    for (size_t k = 0; k < rows.size(); ++k)
+        for (int c : rows[k]) {
+            const int b = c & 31;
+            const int cp = deg[b]++ / DC;
+            if ((int)bank_copies[b].size() <= cp) bank_copies[b].push_back(ncopies++);
+            edges.push_back({(int)k, bank_copies[b][cp]});
+            ecol.push_back(c);
+        }
+    const std::vector<int> colour = bipartite_edge_colouring((int)rows.size(), ncopies, edges, DC);
+    out.assign(rows.size(), std::vector<int>(DC, pad));
+    for (size_t e = 0; e < edges.size(); ++e) out[edges[e].first][colour[e]] = ecol[e];
+}
+
 // Column-indexed slots of a code for D message rows: the CSR order when it already gives every
 // qubit distinct slots mod D, else an edge colouring (empty if neither).
 std::vector<int> column_slots(int m, int n, const int32_t* row_ptr, const int32_t* col_idx, int D) {
@@ -525,7 +591,7 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
     if (qv >= 0) colQ = qc_layout(m, row_ptr, col_idx, qslot, qc_variant(qv));
 
     // Layered schedule: first-fit layers and, in layer order, each check's record (columns,
-    // padding n, then the check index).
+    // padding n, then the check index and its degree).
     int lv = -1, lay_max = 0;
     std::vector<int> lorder, lptr;
     std::vector<uint16_t> lrec;
@@ -536,15 +602,25 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
         if (dc_max <= V.dc && V.t == (lay_max <= 64 ? 32 : 128)) lv = v;
     }
     if (lv >= 0) {
-        const int DCl = kLayeredVariants[lv].dc, R = (DCl + 1 + 7) / 8 * 8;
+        // the kernel's warps take 32 consecutive positions from the start of each layer; their
+        // slot orders spread each step's posterior gathers over the shared-memory banks
+        const int DCl = kLayeredVariants[lv].dc, R = (DCl + 2 + 7) / 8 * 8;   // LayeredRec<DCl>::R
         lrec.assign((size_t)m * R, (uint16_t)0);
-        for (int p = 0; p < m; ++p) {
-            const int i = lorder[p];
-            uint16_t* r = lrec.data() + (size_t)p * R;
-            for (int j = 0; j < DCl; ++j) r[j] = (uint16_t)n;
-            for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) r[e - row_ptr[i]] = (uint16_t)col_idx[e];
-            r[DCl] = (uint16_t)i;
-        }
+        std::vector<std::vector<int>> rows, slots;
+        for (size_t l = 0; l + 1 < lptr.size(); ++l)
+            for (int w0 = lptr[l]; w0 < lptr[l + 1]; w0 += 32) {
+                const int w1 = std::min(w0 + 32, lptr[l + 1]);
+                rows.assign(w1 - w0, {});
+                for (int p = w0; p < w1; ++p)
+                    for (int e = row_ptr[lorder[p]]; e < row_ptr[lorder[p] + 1]; ++e) rows[p - w0].push_back(col_idx[e]);
+                warp_slot_order(rows, DCl, n, slots);
+                for (int p = w0; p < w1; ++p) {
+                    uint16_t* r = lrec.data() + (size_t)p * R;
+                    for (int j = 0; j < DCl; ++j) r[j] = (uint16_t)slots[p - w0][j];
+                    r[DCl] = (uint16_t)lorder[p];
+                    r[DCl + 1] = (uint16_t)(row_ptr[lorder[p] + 1] - row_ptr[lorder[p]]);
+                }
+            }
     }
 
     // Checks of each qubit, for syndrome formation in the Monte Carlo sampler.
