@@ -306,7 +306,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=40000)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--mode-steps", type=int, default=3)
-    ap.add_argument("--no-extras", action="store_true", help="skip the SMS / MS lines and the CPU baseline")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the SMS / MS / BP / layered lines, the other configs and the CPU baseline")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -426,7 +427,10 @@ def main():
         modes = {}
         for name, p in (("sms", S.Params(mode="sms", alpha=SMS_ALPHA, max_iter=MAX_ITER)),
                         ("ms", S.Params(mode="ms", max_iter=MAX_ITER)),
-                        ("bp", S.Params(mode="bp", max_iter=MAX_ITER))):
+                        ("bp", S.Params(mode="bp", max_iter=MAX_ITER)),
+                        ("sagms_layered", S.Params(mode="sagms", alpha_min=SAGMS_KW["alpha_min"],
+                                                   alpha_max=SAGMS_KW["alpha_max"], eta_unsat=SAGMS_KW["eta_unsat"],
+                                                   max_iter=MAX_ITER, flags=S.FLAG_LAYERED))):
             m_ms, _ = timed(p, 1, args.mode_steps)
             cv = conv.cpu().numpy()
             modes[name] = {"shots_per_s": shots * world * args.mode_steps / (m_ms / 1e3),

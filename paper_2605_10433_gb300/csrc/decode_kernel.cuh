@@ -23,7 +23,8 @@
 //       BP (Eq. 3): (-1)^{...} * min(phi(sum_{k != j} phi(|v_k|)), clip), with prefix/suffix sums
 //   A4  P_c = L0_c + sum over the qubit's edges of C (Eq. 2's full sum)
 // Sign bits are read straight from the IEEE representation: no -0.0 ever arises (every
-// value is a sum whose first term is the prior, or a difference of two finite values).
+// value is a sum whose first term is the prior, or a difference of two finite values, and
+// per-qubit priors are loaded as L0 + 0, which turns a -0.0 prior into +0.0).
 #pragma once
 
 #include <cstdint>
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(1024, 1) decode_kernel(const DecodeArgs a) {
     int pq_ok = 1;
     if (per_qubit) {
         for (int c = t; c < n; c += T) {
-            const float v = __ldg(a.L0 + c);
+            const float v = __ldg(a.L0 + c) + 0.0f;   // -0 -> +0: sign bits are decisions
             PQ[c] = v;
             pq_ok &= isfinite(v) ? 1 : 0;
         }

@@ -406,7 +406,7 @@ qc_kernel(const DecodeArgs a, const uint32_t* __restrict__ colQ) {
         // per-qubit priors (LLR units), +inf past n; all finite or every shot is invalid
         float* pqs = reinterpret_cast<float*>(smem + S::PQS);
         for (int c = t; c < S::NP + 4; c += kQcThreads) {
-            const float v = (c < a.n) ? __ldg(a.L0 + c) : inf;
+            const float v = (c < a.n) ? __ldg(a.L0 + c) + 0.0f : inf;   // -0 -> +0: sign bits are decisions
             pqs[c] = v;
             if (c < a.n) pq_ok &= isfinite(v) ? 1 : 0;
         }

@@ -105,7 +105,7 @@ slot_kernel(const DecodeArgs a, const SlotLayout lay) {
     }
     for (int c = t; c < NP + 2; c += MP) P2[c] = (c < n) ? make_float2(0.0f, 0.0f) : make_float2(inf, inf);
     if (per_qubit)
-        for (int c = t; c < NP + 4; c += MP) PQ[c] = (c < n) ? __ldg(a.L0 + c) : inf;
+        for (int c = t; c < NP + 4; c += MP) PQ[c] = (c < n) ? __ldg(a.L0 + c) + 0.0f : inf;   // -0 -> +0
     if (t < 2) C2[DC * MP + t] = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int j = 0; j < DC; ++j) C2[j * MP + t] = make_float2(0.0f, 0.0f);

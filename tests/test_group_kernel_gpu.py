@@ -240,3 +240,26 @@ def test_bivariate_bicycle_code_on_the_column_indexed_kernel(dev_check):
     for mode in ("ms", "sagms"):
         assert _same(_decode_with_kernel(c, KERNEL_QC, syn, L0, PARAMS[mode]),
                      _decode_with_kernel(c, KERNEL_GENERIC, syn, L0, PARAMS[mode]))
+
+
+def test_negative_zero_priors_decide_zero(dev_check):
+    """Per-qubit priors of -0.0 (one of them on a qubit no check touches): the decision is
+    [P < 0], so such a qubit decodes to 0 on every kernel and in the layered schedule, as in
+    the oracle."""
+    g = I.gb_code(63, 3)
+    c = I.Code(m=g.m, n=g.n + 1, row_ptr=g.row_ptr, col_idx=g.col_idx)   # qubit 126: no check
+    rng = np.random.default_rng(5)
+    _, syn = I.sample(c, 0.04, 300, seed=6)
+    L0q = I.llr_prior(rng.uniform(0.01, 0.06, size=c.n)).astype(np.float32)
+    L0q[[3, 40, 126]] = -0.0
+    for mode in ("ms", "sagms"):
+        p = _with(PARAMS[mode], flags=S.FLAG_L0_PER_QUBIT)
+        ref = _decode_with_kernel(c, KERNEL_GENERIC, syn, L0q, p)
+        assert not (I.unpack_bits(ref["err"], c.n)[:, 126]).any()
+        for kernel in (KERNEL_SLOTS, KERNEL_QC):
+            assert _same(_decode_with_kernel(c, kernel, syn, L0q, p), ref), kernel
+        dc = S.DeviceCode.from_code(c)
+        G.compare(c, dc, syn, L0q, p)
+        lay = _with(p, flags=S.FLAG_L0_PER_QUBIT | S.FLAG_LAYERED)
+        G.compare(c, dc, syn, L0q, lay)
+        assert not (I.unpack_bits(G.gpu_decode(dc, syn, L0q, lay)["err"], c.n)[:, 126]).any()
