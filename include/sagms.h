@@ -152,6 +152,17 @@ int sagms_code_kernels(const sagms_code* code, uint32_t* mask);
 int sagms_column_slots(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr,
                        const int32_t* col_idx, int32_t D, int32_t* slots);
 
+/*
+ * Layers of the layered schedule (SAGMS_FLAG_LAYERED): layer[i] for every check i, the
+ * smallest layer number used by no check k < i that shares a qubit with check i (first-fit
+ * in index order), so the checks of one layer share no qubit.  *num_layers (may be NULL)
+ * receives the layer count.
+ *   layer  [m] host, out.
+ * Host only (no CUDA call).  Errors: ERR_ARG (NULL pointers), ERR_CSR.
+ */
+int sagms_check_layers(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr,
+                       const int32_t* col_idx, int32_t* layer, int32_t* num_layers);
+
 /* Validate a parameter block without decoding.  Returns SAGMS_OK or SAGMS_ERR_PARAM /
  * SAGMS_ERR_ARG.  Runs on the host only (no CUDA call). */
 int sagms_check_params(const sagms_params* params);

@@ -62,6 +62,7 @@ def _load_library():
         "sagms_free_code": (None, [vp]),
         "sagms_code_info": (ctypes.c_int, [vp, P(i32), P(i32), P(i32), P(i32)]),
         "sagms_code_kernels": (ctypes.c_int, [vp, P(ctypes.c_uint32)]),
+        "sagms_check_layers": (ctypes.c_int, [i32, i32, i64, P(i32), P(i32), P(i32), P(i32)]),
         "sagms_column_slots": (ctypes.c_int, [i32, i32, i64, P(i32), P(i32), i32, P(i32)]),
         "sagms_check_params": (ctypes.c_int, [P(sagms_params)]),
         "sagms_decode": (ctypes.c_int, [vp, P(sagms_params), i64, vp, vp, vp, vp, vp, vp]),
@@ -143,6 +144,20 @@ def sagms_code_kernels(handle):
     v = ctypes.c_uint32()
     _check(_lib.sagms_code_kernels(handle, ctypes.byref(v)))
     return v.value
+
+
+def sagms_check_layers(m, n, row_ptr, col_idx):
+    """First-fit layer of every check (int32 numpy array) and the layer count."""
+    import numpy as np
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    out = np.zeros(int(m), dtype=np.int32)
+    L = ctypes.c_int32()
+    _check(_lib.sagms_check_layers(int(m), int(n), int(rp[-1]) if len(rp) else 0,
+                                   rp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   ci.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(L)))
+    return out, L.value
 
 
 def sagms_column_slots(m, n, row_ptr, col_idx, D):

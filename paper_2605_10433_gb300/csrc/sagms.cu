@@ -451,6 +451,20 @@ int sagms_check_params(const sagms_params* p) {
     }
 }
 
+int sagms_check_layers(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+                       int32_t* layer, int32_t* num_layers) {
+    if (!layer) return fail(SAGMS_ERR_ARG, "layer is NULL");
+    int dc_max = 0, dv_max = 0;
+    const int rc = check_csr(m, n, nnz, row_ptr, col_idx, &dc_max, &dv_max);
+    if (rc != SAGMS_OK) return rc;
+    std::vector<int> order, lay_ptr;
+    first_fit_layers(m, n, row_ptr, col_idx, order, lay_ptr);
+    for (size_t l = 0; l + 1 < lay_ptr.size(); ++l)
+        for (int p = lay_ptr[l]; p < lay_ptr[l + 1]; ++p) layer[order[p]] = (int32_t)l;
+    if (num_layers) *num_layers = (int32_t)lay_ptr.size() - 1;
+    return SAGMS_OK;
+}
+
 int sagms_column_slots(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
                        int32_t D, int32_t* slots) {
     if (!slots && nnz > 0) return fail(SAGMS_ERR_ARG, "slots is NULL");

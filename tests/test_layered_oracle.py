@@ -10,6 +10,8 @@ the residual at the start of the round.
   order and from flooding (tests/golden/hand_layered_ms_chain.json);
 * codes whose checks share no qubit form a single layer, where the layered round is the
   flooding round: bitwise identical to the flooding oracle in every mode.
+The CUDA library's own layering (sagms_check_layers, host side) is checked here too, against
+the rule written out on the dense matrix.
 """
 import json
 import os
@@ -106,3 +108,35 @@ def test_layered_differs_from_flooding_on_a_loopy_code():
     a = oracle.decode_code(c, syn, L0, flags=oracle.FLAG_NO_EARLY_STOP, **kw)["trace"][:, 1]
     b = oracle.decode_code(c, syn, L0, flags=oracle.FLAG_NO_EARLY_STOP | LAYERED, **kw)["trace"][:, 1]
     assert not np.array_equal(a, b)
+
+
+def _first_fit(c):
+    """The layering rule written out on the dense matrix: check i takes the smallest layer
+    not used by an earlier check it shares a qubit with."""
+    H = c.dense().astype(bool)
+    layer = []
+    for i in range(c.m):
+        used = {layer[k] for k in range(i) if (H[k] & H[i]).any()}
+        layer.append(next(l for l in range(c.m + 1) if l not in used))
+    return np.array(layer)
+
+
+@pytest.mark.parametrize("make", [lambda: I.gb_code(63, 3), lambda: I.gb_code(127, 4), lambda: I.gb_code(255, 8),
+                                  lambda: I.tree_code(40, 3, max_deg=4)])
+def test_library_layering_is_the_first_fit_rule(make):
+    """The CUDA library's layers (host side, no GPU) follow the same rule, checked against the
+    rule written out on the dense matrix; every layer's checks share no qubit."""
+    from paper_2605_10433_gb300 import _native
+    c = make()
+    layer, L = _native.sagms_check_layers(c.m, c.n, c.row_ptr, c.col_idx)
+    assert np.array_equal(layer, _first_fit(c)) and L == layer.max() + 1
+    H = c.dense().astype(np.int64)
+    for l in range(L):
+        assert (H[layer == l].sum(axis=0) <= 1).all()
+
+
+def test_hand_chain_layers():
+    from paper_2605_10433_gb300 import _native
+    _, c, _ = _chain()
+    layer, L = _native.sagms_check_layers(c.m, c.n, c.row_ptr, c.col_idx)
+    assert list(layer) == [0, 1, 0] and L == 2
