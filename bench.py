@@ -308,6 +308,8 @@ def main():
     ap.add_argument("--mode-steps", type=int, default=3)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the SMS / MS / BP / layered lines, the other configs and the CPU baseline")
+    ap.add_argument("--layered", action="store_true",
+                    help="time the layered schedule (SAGMS_FLAG_LAYERED) instead of Algorithm 1's flooding one")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -344,7 +346,7 @@ def main():
     conv = torch.empty((shots,), dtype=torch.uint8, device="cuda")
     iters = torch.empty((shots,), dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
-    sagms = S.Params(mode="sagms", max_iter=MAX_ITER, **SAGMS_KW)
+    sagms = S.Params(mode="sagms", max_iter=MAX_ITER, flags=S.FLAG_LAYERED if args.layered else 0, **SAGMS_KW)
 
     def step(p):
         S.decode(dcode, d_syn, d_L0, p, out=(err, conv, iters), stream=stream)
@@ -389,9 +391,10 @@ def main():
     ops_launch = float(it_host.astype(np.int64).sum()) * ops_it
     achieved = ops_launch / (ms_step / 1e3)
     peak = roofline.alu_peak_ops(props.multi_processor_count, sm_max)
-    traffic = profile_traffic(shots)
+    traffic = None if args.layered else profile_traffic(shots)
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
-            "frac": achieved / peak, "traffic": traffic, "kernel": "sagms::qc_kernel<10,5,4>",
+            "frac": achieved / peak, "traffic": traffic,
+            "kernel": "sagms::layered_kernel<10,128>" if args.layered else "sagms::qc_kernel<10,5,4>",
             "note": (f"ops = sum over shots of iters x {ops_it} per iteration (Eq. 15 / Table I CN cost + VN sum, "
                      f"decision, residual XOR, popcount); peak = {props.multi_processor_count} SMs x 128 lanes x "
                      f"{sm_max:.0f} MHz (derived from unit counts and clock); HBM bound "
@@ -415,12 +418,13 @@ def main():
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": workload_name(shots), "global_batch": shots * world, "code_seed": code.seed,
+           "config": {"workload": workload_name(shots) + (", layered schedule" if args.layered else ""),
+                      "global_batch": shots * world, "code_seed": code.seed,
                       "a": list(code.a), "b": list(code.b), "k": code.k,
                       "l2": f"inputs larger than L2: {syn.nbytes / 1e9:.2f} GB syndromes per GPU",
                       "parallelism": f"shot-sharded x{world}"},
            "gpu_launches": args.steps, "mean_iters": float(it_host.mean()), "fer": fer, "roofline": roof,
-           "roofline_smem": roof_smem,
+           "roofline_smem": None if args.layered else roof_smem,
            "clocks": clk, "input_gen_s": gen_s}
 
     if not args.no_extras:
