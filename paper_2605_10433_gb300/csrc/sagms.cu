@@ -1,9 +1,12 @@
 // libsagms.so: C ABI (include/sagms.h) around the batched decoder kernels.
 //
-// Host responsibilities: validate the CSR matrix and the parameters, lay the Tanner graph
-// out for the kernel (slot-major u16 index arrays, padded to the variant's degrees), pick
-// the kernel variant and grid, and launch on the caller's stream.  Every step of the
-// decode itself runs in decode_kernel.cuh.
+// Host responsibilities: validate the CSR matrix and the parameters; at load time, fix the
+// edge order every layout shares (column-indexed slots by edge colouring where needed) and
+// lay the Tanner graph out once per kernel that covers the code (slot-major index arrays,
+// two-slot and two-group offsets, column-indexed offsets, layered-schedule records); at
+// decode time, pick the kernel and grid and launch on the caller's stream.  Every step of
+// the decode itself runs in the kernels: decode_qc.cuh, decode_groups.cuh,
+// decode_slots.cuh and decode_kernel.cuh (flooding schedule) and decode_layered.cuh.
 #include <cuda_runtime.h>
 
 #include <algorithm>
