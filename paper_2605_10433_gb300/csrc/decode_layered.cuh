@@ -21,7 +21,8 @@
 //   sbits, rbits   input syndrome (check order) and residual bits (layer order)
 // A check's outputs take two magnitudes only, so (O1, O2, meta) rebuilds every old message
 // exactly: slot j carries O2 if it holds the first minimum, else O1 (two slots tying at the
-// minimum have O1 == O2).  A shot's first round reads no old message (all are zero), so it
+// minimum have O1 == O2).  P sits at the start of shared memory, so a record's byte offsets
+// address it directly.  A shot's first round reads no old message (all are zero), so it
 // runs a copy of the loop without the rebuild, and with one prior per shot the residual before
 // it has a closed form.  The check records (columns, check index and degree, layer order) stay
 // in global memory, read through the read-only cache.
@@ -33,15 +34,15 @@
 
 namespace sagms {
 
-// Record of one check in layer order: its DC columns (n = padding), its index and its degree,
-// as u16, padded to whole 16-byte vectors.
+// Record of one check in layer order, as u32 words padded to whole 16-byte vectors: the byte
+// offsets 4 * col of its DC columns in P (4 * n for padding), then index | degree << 16.
 template <int DC>
 struct LayeredRec {
-    static constexpr int R = (DC + 2 + 7) / 8 * 8;
+    static constexpr int R = (DC + 1 + 3) / 4 * 4;
 };
 
 struct LayeredLayout {
-    const uint16_t* rec;  // [m][R]
+    const uint32_t* rec;  // [m][R]
     const int* lay_ptr;   // [L + 1] first position of each layer
     int L;
 };
@@ -71,28 +72,31 @@ __global__ void __launch_bounds__(T) layered_kernel(const DecodeArgs a, const La
     int* cnt_sh = reinterpret_cast<int*>(rbits + Mp / 32);
     const uint4* rec = reinterpret_cast<const uint4*>(lay.rec);
     const float inf = __uint_as_float(0x7f800000u);
+    const bool sagms_mode = a.mode == kModeSAGMS;
+    const float eta = a.eta;
+    auto Pat = [&](uint32_t o) -> float& { return *reinterpret_cast<float*>(smem + o); };
 
     auto sync = [] {
         if constexpr (T == 32) __syncwarp();
         else __syncthreads();
     };
-    // columns and check index of the check at layer position p
-    auto load_rec = [&](int p, int (&col)[DC]) {
-        uint32_t w[R / 2];
+    // column byte offsets and check index of the check at layer position p
+    auto load_rec = [&](int p, uint32_t (&off)[DC]) {
+        uint32_t w[R];
 #pragma unroll
-        for (int k = 0; k < R / 8; ++k) {
-            const uint4 u = __ldg(rec + (size_t)p * (R / 8) + k);
+        for (int k = 0; k < R / 4; ++k) {
+            const uint4 u = __ldg(rec + (size_t)p * (R / 4) + k);
             w[4 * k] = u.x; w[4 * k + 1] = u.y; w[4 * k + 2] = u.z; w[4 * k + 3] = u.w;
         }
 #pragma unroll
-        for (int j = 0; j < DC; ++j) col[j] = (int)((w[j >> 1] >> (16 * (j & 1))) & 0xffffu);
-        return (int)((w[DC >> 1] >> (16 * (DC & 1))) & 0xffffu);
+        for (int j = 0; j < DC; ++j) off[j] = w[j];
+        return (int)(w[DC] & 0xffffu);
     };
     // check index and degree of the check at layer position p
     auto load_head = [&](int p, int& deg) {
-        const uint16_t* r = lay.rec + (size_t)p * R;
-        deg = (int)__ldg(r + DC + 1);
-        return (int)__ldg(r + DC);
+        const uint32_t h = __ldg(lay.rec + (size_t)p * R + DC);
+        deg = (int)(h >> 16);
+        return (int)(h & 0xffffu);
     };
     // One round over the layers (A3 + A4).  FRESH: the shot's first round, where every old
     // message is zero (v = P) and the check state is written without being read.
@@ -101,16 +105,16 @@ __global__ void __launch_bounds__(T) layered_kernel(const DecodeArgs a, const La
         for (int l = 0; l < lay.L; ++l) {
             const int p1 = __ldg(lay.lay_ptr + l + 1);
             for (int p = __ldg(lay.lay_ptr + l) + t; p < p1; p += T) {
-                int col[DC];
-                const int i = load_rec(p, col);
+                uint32_t off[DC];
+                const int i = load_rec(p, off);
                 const uint32_t s_i = (sbits[i >> 5] >> (i & 31)) & 1u;
-                const float g = (a.mode == kModeSAGMS && ((rbits[p >> 5] >> (p & 31)) & 1u)) ? g0 * a.eta : g0;
+                const float g = (sagms_mode && ((rbits[p >> 5] >> (p & 31)) & 1u)) ? g0 * eta : g0;
                 float v[DC];
                 uint32_t par = s_i << 31;
                 if constexpr (FRESH) {
 #pragma unroll
                     for (int j = 0; j < DC; ++j) {
-                        v[j] = P[col[j]];
+                        v[j] = Pat(off[j]);
                         par ^= __float_as_uint(v[j]);
                     }
                 } else {
@@ -120,33 +124,32 @@ __global__ void __launch_bounds__(T) layered_kernel(const DecodeArgs a, const La
 #pragma unroll
                     for (int j = 0; j < DC; ++j) {
                         const float mag = (j == am) ? q2 : q1;
-                        const float c_old = __uint_as_float(__float_as_uint(mag) | (((mt >> j) & 1u) << 31));
-                        v[j] = P[col[j]] - c_old;
+                        const float c_old = __uint_as_float(__float_as_uint(mag) | ((mt << (31 - j)) & kSign));
+                        v[j] = Pat(off[j]) - c_old;
                         par ^= __float_as_uint(v[j]);
                     }
                 }
                 par &= kSign;
                 float m1 = inf, m2 = inf;
-                int amn = 0;
 #pragma unroll
                 for (int j = 0; j < DC; ++j) {
                     const float av = fabsf(v[j]);
                     m2 = fminf(m2, fmaxf(m1, av));
-                    amn = (av < m1) ? j : amn;
                     m1 = fminf(m1, av);
                 }
                 const float o1 = fminf(g * m1, kMsFamClip), o2 = fminf(g * m2, kMsFamClip);
-                uint32_t nm = (uint32_t)amn << 24;
+                uint32_t nm = 0u, eqm = 0u;   // output signs; slots at the minimum
 #pragma unroll
                 for (int j = 0; j < DC; ++j) {
                     const uint32_t sg = (par ^ __float_as_uint(v[j])) & kSign;
-                    const float mag = (fabsf(v[j]) == m1) ? o2 : o1;
-                    P[col[j]] = v[j] + __uint_as_float(__float_as_uint(mag) | sg);
-                    nm |= (sg >> 31) << j;
+                    const bool eq = fabsf(v[j]) == m1;
+                    Pat(off[j]) = v[j] + __uint_as_float(__float_as_uint(eq ? o2 : o1) | sg);
+                    nm |= sg >> (31 - j);
+                    eqm |= (uint32_t)eq << j;
                 }
                 O1[p] = o1;
                 O2[p] = o2;
-                meta[p] = nm;
+                meta[p] = nm | ((uint32_t)(__ffs(eqm) - 1) << 24);   // first slot at the minimum
             }
             sync();
         }
@@ -201,11 +204,11 @@ __global__ void __launch_bounds__(T) layered_kernel(const DecodeArgs a, const La
                     const int i = load_head(p, deg);
                     x = ((sbits[i >> 5] >> (i & 31)) ^ (prior < 0.0f ? (uint32_t)deg : 0u)) & 1u;
                 } else if (p < m) {
-                    int col[DC];
-                    const int i = load_rec(p, col);
+                    uint32_t off[DC];
+                    const int i = load_rec(p, off);
                     x = (sbits[i >> 5] >> (i & 31)) & 1u;
 #pragma unroll
-                    for (int j = 0; j < DC; ++j) x ^= __float_as_uint(P[col[j]]) >> 31;
+                    for (int j = 0; j < DC; ++j) x ^= __float_as_uint(Pat(off[j])) >> 31;
                 }
                 const uint32_t b = __ballot_sync(0xffffffffu, x);
                 if (lane == 0 && p < Mp) {

@@ -371,7 +371,7 @@ struct sagms_code {
     int lay_variant;       // -1: no layered-schedule kernel for this code (check degree above 24)
     int lay_L;             // layers of the first-fit partition
     int lay_max;           // checks in the largest layer
-    uint16_t* d_lrec;      // [m][R] check records in layer order (LayeredRec)
+    uint32_t* d_lrec;      // [m][R] check records in layer order (LayeredRec)
     int* d_lptr;           // [lay_L + 1] first position of each layer
     int k_logicals;        // logical operators attached for the Monte Carlo check (-1: none)
     uint32_t* d_logicals;  // [k][ceil(n/32)]
@@ -611,7 +611,7 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
     // padding n, then the check index and its degree).
     int lv = -1, lay_max = 0;
     std::vector<int> lorder, lptr;
-    std::vector<uint16_t> lrec;
+    std::vector<uint32_t> lrec;
     first_fit_layers(m, n, row_ptr, col_idx, lorder, lptr);
     for (size_t l = 0; l + 1 < lptr.size(); ++l) lay_max = std::max(lay_max, lptr[l + 1] - lptr[l]);
     for (int v = 0; v < kNumLayeredVariants && lv < 0; ++v) {
@@ -621,8 +621,8 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
     if (lv >= 0) {
         // the kernel's warps take 32 consecutive positions from the start of each layer; their
         // slot orders spread each step's posterior gathers over the shared-memory banks
-        const int DCl = kLayeredVariants[lv].dc, R = (DCl + 2 + 7) / 8 * 8;   // LayeredRec<DCl>::R
-        lrec.assign((size_t)m * R, (uint16_t)0);
+        const int DCl = kLayeredVariants[lv].dc, R = (DCl + 1 + 3) / 4 * 4;   // LayeredRec<DCl>::R
+        lrec.assign((size_t)m * R, 0u);
         std::vector<std::vector<int>> rows, slots;
         for (size_t l = 0; l + 1 < lptr.size(); ++l)
             for (int w0 = lptr[l]; w0 < lptr[l + 1]; w0 += 32) {
@@ -632,10 +632,9 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
                     for (int e = row_ptr[lorder[p]]; e < row_ptr[lorder[p] + 1]; ++e) rows[p - w0].push_back(col_idx[e]);
                 warp_slot_order(rows, DCl, n, slots);
                 for (int p = w0; p < w1; ++p) {
-                    uint16_t* r = lrec.data() + (size_t)p * R;
-                    for (int j = 0; j < DCl; ++j) r[j] = (uint16_t)slots[p - w0][j];
-                    r[DCl] = (uint16_t)lorder[p];
-                    r[DCl + 1] = (uint16_t)(row_ptr[lorder[p] + 1] - row_ptr[lorder[p]]);
+                    uint32_t* r = lrec.data() + (size_t)p * R;
+                    for (int j = 0; j < DCl; ++j) r[j] = 4u * (uint32_t)slots[p - w0][j];
+                    r[DCl] = (uint32_t)lorder[p] | ((uint32_t)(row_ptr[lorder[p] + 1] - row_ptr[lorder[p]]) << 16);
                 }
             }
     }
@@ -701,9 +700,9 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
         if (ce == cudaSuccess) ce = cudaMemcpy(code->d_colQ, colQ.data(), colQ.size() * 4, cudaMemcpyHostToDevice);
     }
     if (ce == cudaSuccess && lv >= 0) {
-        ce = cudaMalloc(&code->d_lrec, lrec.size() * sizeof(uint16_t));
+        ce = cudaMalloc(&code->d_lrec, lrec.size() * sizeof(uint32_t));
         if (ce == cudaSuccess) ce = cudaMalloc(&code->d_lptr, lptr.size() * sizeof(int));
-        if (ce == cudaSuccess) ce = cudaMemcpy(code->d_lrec, lrec.data(), lrec.size() * 2, cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess) ce = cudaMemcpy(code->d_lrec, lrec.data(), lrec.size() * 4, cudaMemcpyHostToDevice);
         if (ce == cudaSuccess) ce = cudaMemcpy(code->d_lptr, lptr.data(), lptr.size() * 4, cudaMemcpyHostToDevice);
     }
     if (ce == cudaSuccess) {
