@@ -443,6 +443,32 @@ def main():
         step(sagms)
         torch.cuda.synchronize()
         if world == 1:
+            # one batch per noise level (same size as the headline batch): shots/s, mean
+            # iterations and the issue-roofline fraction of each p on its own
+            per_p = {}
+            for k, q in enumerate(P_VALUES):
+                _, syn_q, L0_q, _ = I.workload(code, [q], shots, seed=NOISE_SEED + 1 + k)
+                ds_q = torch.from_numpy(syn_q.view(np.int32)).cuda()
+                dl_q = torch.from_numpy(L0_q).cuda()
+                for _ in range(args.warmup):
+                    S.decode(dcode, ds_q, dl_q, sagms, out=(err, conv, iters), stream=stream)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(args.mode_steps):
+                    S.decode(dcode, ds_q, dl_q, sagms, out=(err, conv, iters), stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                t_q = e0.elapsed_time(e1) / 1e3 / args.mode_steps
+                it_q = iters.cpu().numpy()
+                per_p[str(q)] = {"shots_per_s": shots / t_q, "mean_iters": float(it_q.mean()),
+                                 "fer_syn": float((conv.cpu().numpy() == 0).mean()),
+                                 "roofline_frac": float(it_q.astype(np.int64).sum()) * ops_it / t_q / peak}
+                del ds_q, dl_q
+            out["per_p"] = per_p
+            step(sagms)
+            torch.cuda.synchronize()
             out["config3_mixed_degree"] = bench_mixed_degree(S, I, args.mode_steps)
             out["serving"] = bench_serving(S, I)
             out["monte_carlo"] = bench_mc(S, I)
