@@ -129,11 +129,11 @@ void sagms_free_code(sagms_code* code);
 /* Shape of a loaded code: any output pointer may be NULL. */
 int sagms_code_info(const sagms_code* code, int32_t* m, int32_t* n, int32_t* dc_max, int32_t* dv_max);
 
-/* Kernels that can decode a loaded code in the MS family (SAGMS, SMS, MS), in the numbering of
- * a launch plan (sagms_autotune): bit k of *mask set when kernel k has a layout for the code
- * (bit 1, one shot per CTA, always; 2 two-slot; 3 two-group; 4 two-group with column-indexed
- * messages).  Parameters can still rule a kernel out (per-qubit priors: no two-group kernel;
- * BP: one shot per CTA only).  Host only.  Errors: ERR_ARG. */
+/* Kernels that can decode a loaded code, in the numbering of a launch plan (sagms_autotune):
+ * bit k of *mask set when kernel k has a layout for the code (bit 1, one shot per CTA,
+ * always; 2 two-slot; 3 two-group; 4 two-group with column-indexed messages).  Parameters
+ * can still rule a kernel out: per-qubit priors, no two-group kernel; BP, the one-shot-per-CTA
+ * kernel or, with per-shot priors, the column-indexed one.  Host only.  Errors: ERR_ARG. */
 int sagms_code_kernels(const sagms_code* code, uint32_t* mask);
 
 /*

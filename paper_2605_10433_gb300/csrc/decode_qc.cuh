@@ -72,7 +72,8 @@ __device__ __forceinline__ uint32_t qc_byte(uint32_t x, int k) { return (x >> (8
 // GC: the group index when it is fixed at compile time (one copy of the loop per group, every
 // group address an immediate), or -1 (one copy for all groups, g at run time).  PQ: one prior
 // per qubit shared by all shots (SAGMS_FLAG_L0_PER_QUBIT; LLR units), pq_ok = all finite.
-template <class S, bool AUTO, bool PQ, int GC>
+// BPK: the BP rule of Eq. 3 (per-shot priors in LLR units) instead of the MS family.
+template <class S, bool AUTO, bool PQ, int GC, bool BPK>
 __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* smem, const int tg, const int g_rt,
                                          const uint32_t (&off)[S::K][S::DC], const uint32_t degs, const bool pq_ok) {
     constexpr int DC = S::DC, DV = S::DV, K = S::K, T = S::T, NP = S::NP;
@@ -212,7 +213,8 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
                     for (int w = tg; w < nw; w += T) a.err[s * nw + w] = 0u;
                     if (tg == 0) { a.conv[s] = 0; a.iters[s] = -1; }
                 } else {
-                    const float pi = PQ ? 0.0f : ((l0 > 0.0f) ? 1.0f : ((l0 < 0.0f) ? -1.0f : 0.0f));
+                    const float pi = PQ ? 0.0f
+                                        : (BPK ? l0 + 0.0f : ((l0 > 0.0f) ? 1.0f : ((l0 < 0.0f) ? -1.0f : 0.0f)));
                     const bool flipped = PQ || pi < 0.0f;
                     // First check (l = 0), Eqs. 1 and 6: popcount of s XOR flip.
                     const uint32_t flip_lane = (flipped && lane < mw) ? flipw[lane] : 0u;
@@ -266,7 +268,7 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
 #pragma unroll
                 for (int k = 0; k < K; ++k) g[k] = (a.mode == kModeSMS) ? a.alpha : 1.0f;
             }
-            if (fresh && !PQ) {
+            if (fresh && !PQ && !BPK) {
                 // A3 on round-1 inputs: every real edge carries the prior s, padded slots +inf.
                 // The minimum and second minimum of |v| are |s| (a check with one edge has no
                 // second: +inf), the parity is the syndrome bit XOR the sign of s once per
@@ -290,12 +292,20 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
                     for (int p = 0; p < K / 2; ++p)
 #pragma unroll
                         for (int j = 0; j < DC; ++j) v[p][j] = make_float2(PQat(off[2 * p][j]), PQat(off[2 * p + 1][j]));
+                } else if (BPK && fresh) {
+                    // round-1 inputs are the shot's prior on real edges, +inf on padded slots
+                    const uint32_t pad = S::PAD + (uint32_t)PO;
+#pragma unroll
+                    for (int p = 0; p < K / 2; ++p)
+#pragma unroll
+                        for (int j = 0; j < DC; ++j)
+                            v[p][j] = make_float2(off[2 * p][j] == pad ? inf : prior, off[2 * p + 1][j] == pad ? inf : prior);
                 }
 #pragma unroll
                 for (int p = 0; p < K / 2; ++p) {
                     // A3 check-node update for checks 2p and 2p + 1 (C holds negated
                     // messages: P - L = P + D; a fresh shot has no old messages)
-                    if (!(PQ && fresh)) {
+                    if (!((PQ || BPK) && fresh)) {
 #pragma unroll
                         for (int j = 0; j < DC; ++j)
                             v[p][j] = add2(v[p][j], make_float2(Cat(j, off[2 * p][j]), Cat(j, off[2 * p + 1][j])));
@@ -308,30 +318,56 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
                     }
                     par0 &= kSign;
                     par1 &= kSign;
-                    // Smallest and second smallest |v|, two edges at a time:
-                    // m2 = min(m2, hi, max(m1, lo)), m1 = min(m1, lo).
-                    float m1a = inf, m2a = inf, m1b = inf, m2b = inf;
+                    if constexpr (BPK) {
+                        // A3, BP rule (Eq. 3): phi sums over the other edges by prefix and suffix
+                        // sums, in the slot order and arithmetic of decode_kernel.cuh (padded slots
+                        // add phi(+inf) = 0); stored negated, D = -L.
 #pragma unroll
-                    for (int j = 0; j < DC; j += 2) {
-                        const float a0 = fabsf(v[p][j].x), a1 = fabsf(v[p][j + 1].x);
-                        const float c0 = fabsf(v[p][j].y), c1 = fabsf(v[p][j + 1].y);
-                        const float loa = fminf(a0, a1), hia = fmaxf(a0, a1);
-                        const float lob = fminf(c0, c1), hib = fmaxf(c0, c1);
-                        m2a = fminf(fminf(m2a, hia), fmaxf(m1a, loa));
-                        m1a = fminf(m1a, loa);
-                        m2b = fminf(fminf(m2b, hib), fmaxf(m1b, lob));
-                        m1b = fminf(m1b, lob);
-                    }
-                    const float o1a = __uint_as_float(__float_as_uint(fminf(g[2 * p] * m1a, kMsFamClip)) | par0);
-                    const float o2a = __uint_as_float(__float_as_uint(fminf(g[2 * p] * m2a, kMsFamClip)) | par0);
-                    const float o1b = __uint_as_float(__float_as_uint(fminf(g[2 * p + 1] * m1b, kMsFamClip)) | par1);
-                    const float o2b = __uint_as_float(__float_as_uint(fminf(g[2 * p + 1] * m2b, kMsFamClip)) | par1);
+                        for (int h = 0; h < 2; ++h) {
+                            const uint32_t par = h ? par1 : par0;
+                            float ph[DC];
 #pragma unroll
-                    for (int j = 0; j < DC; ++j) {
-                        const float ma = (fabsf(v[p][j].x) == m1a) ? o2a : o1a;
-                        const float mb = (fabsf(v[p][j].y) == m1b) ? o2b : o1b;
-                        Cat(j, off[2 * p][j]) = __uint_as_float(__float_as_uint(ma) ^ (~__float_as_uint(v[p][j].x) & kSign));
-                        Cat(j, off[2 * p + 1][j]) = __uint_as_float(__float_as_uint(mb) ^ (~__float_as_uint(v[p][j].y) & kSign));
+                            for (int j = 0; j < DC; ++j) ph[j] = phi_fn(fabsf(h ? v[p][j].y : v[p][j].x));
+                            float suf[DC + 1];
+                            suf[DC] = 0.0f;
+#pragma unroll
+                            for (int j = DC - 1; j >= 0; --j) suf[j] = suf[j + 1] + ph[j];
+                            float pre = 0.0f;
+#pragma unroll
+                            for (int j = 0; j < DC; ++j) {
+                                const float Sj = pre + suf[j + 1];
+                                pre += ph[j];
+                                const float mag = fminf(phi_fn(Sj), kBpClip);
+                                const uint32_t vb = __float_as_uint(h ? v[p][j].y : v[p][j].x);
+                                Cat(j, off[2 * p + h][j]) = __uint_as_float(__float_as_uint(mag) | (~(par ^ vb) & kSign));
+                            }
+                        }
+                    } else {
+                        // Smallest and second smallest |v|, two edges at a time:
+                        // m2 = min(m2, hi, max(m1, lo)), m1 = min(m1, lo).
+                        float m1a = inf, m2a = inf, m1b = inf, m2b = inf;
+#pragma unroll
+                        for (int j = 0; j < DC; j += 2) {
+                            const float a0 = fabsf(v[p][j].x), a1 = fabsf(v[p][j + 1].x);
+                            const float c0 = fabsf(v[p][j].y), c1 = fabsf(v[p][j + 1].y);
+                            const float loa = fminf(a0, a1), hia = fmaxf(a0, a1);
+                            const float lob = fminf(c0, c1), hib = fmaxf(c0, c1);
+                            m2a = fminf(fminf(m2a, hia), fmaxf(m1a, loa));
+                            m1a = fminf(m1a, loa);
+                            m2b = fminf(fminf(m2b, hib), fmaxf(m1b, lob));
+                            m1b = fminf(m1b, lob);
+                        }
+                        const float o1a = __uint_as_float(__float_as_uint(fminf(g[2 * p] * m1a, kMsFamClip)) | par0);
+                        const float o2a = __uint_as_float(__float_as_uint(fminf(g[2 * p] * m2a, kMsFamClip)) | par0);
+                        const float o1b = __uint_as_float(__float_as_uint(fminf(g[2 * p + 1] * m1b, kMsFamClip)) | par1);
+                        const float o2b = __uint_as_float(__float_as_uint(fminf(g[2 * p + 1] * m2b, kMsFamClip)) | par1);
+#pragma unroll
+                        for (int j = 0; j < DC; ++j) {
+                            const float ma = (fabsf(v[p][j].x) == m1a) ? o2a : o1a;
+                            const float mb = (fabsf(v[p][j].y) == m1b) ? o2b : o1b;
+                            Cat(j, off[2 * p][j]) = __uint_as_float(__float_as_uint(ma) ^ (~__float_as_uint(v[p][j].x) & kSign));
+                            Cat(j, off[2 * p + 1][j]) = __uint_as_float(__float_as_uint(mb) ^ (~__float_as_uint(v[p][j].y) & kSign));
+                        }
                     }
                 }
             }
@@ -371,7 +407,7 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
 // colQ: [K][DC][T] u32, byte offset 4 * col of check tg + kT in slot j (S::PAD for a padded
 // slot or a check past m).  AUTO: the gain ceiling of each shot comes from its prior
 // (SAGMS_FLAG_AUTO_CEILING), a separate instantiation so the default one carries no trace of it.
-template <class S, bool AUTO, bool PQ>
+template <class S, bool AUTO, bool PQ, bool BPK = false>
 __global__ void __launch_bounds__(kQcThreads, S::K * S::DC <= 12 ? 2 : 1)
 qc_kernel(const DecodeArgs a, const uint32_t* __restrict__ colQ) {
     constexpr int DC = S::DC, K = S::K, T = S::T;
@@ -441,10 +477,10 @@ qc_kernel(const DecodeArgs a, const uint32_t* __restrict__ colQ) {
     }
     pq_ok = __syncthreads_and(pq_ok);
     if constexpr (S::NG == 2) {
-        if (g == 0) qc_group<S, AUTO, PQ, 0>(a, smem, tg, g, off, degs, pq_ok != 0);
-        else qc_group<S, AUTO, PQ, 1>(a, smem, tg, g, off, degs, pq_ok != 0);
+        if (g == 0) qc_group<S, AUTO, PQ, 0, BPK>(a, smem, tg, g, off, degs, pq_ok != 0);
+        else qc_group<S, AUTO, PQ, 1, BPK>(a, smem, tg, g, off, degs, pq_ok != 0);
     } else {
-        qc_group<S, AUTO, PQ, -1>(a, smem, tg, g, off, degs, pq_ok != 0);
+        qc_group<S, AUTO, PQ, -1, BPK>(a, smem, tg, g, off, degs, pq_ok != 0);
     }
 }
 

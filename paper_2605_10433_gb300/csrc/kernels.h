@@ -39,8 +39,9 @@ GroupFn group_kernel_fn();
 using QcFn = void (*)(const DecodeArgs, const uint32_t*);
 struct QcVariant {
     int dc, dv, k, t, np;
-    QcFn fn[3];      // per-shot priors, per-shot priors with the automatic ceiling, per-qubit priors
-    size_t smem[3];  // shared memory of each
+    QcFn fn[4];      // per-shot priors, per-shot priors with the automatic ceiling, per-qubit priors,
+                     // BP with per-shot priors
+    size_t smem[4];  // shared memory of each
 };
 // Two tables (kernels_qc_small.cu: n <= 512; kernels_qc_large.cu: n > 512), compiled in
 // parallel and read as one list, smallest shapes first.

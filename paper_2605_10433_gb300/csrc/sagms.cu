@@ -833,9 +833,14 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     // Kernel: the plan's choice where the code and parameters allow it, else the fastest
     // that does (two-group, two-slot, one-shot-per-CTA).
     const bool msfam_fast = !bp && !(p->flags & SAGMS_FLAG_GENERIC_KERNEL);
+    const bool bp_fast = bp && !per_qubit && !(p->flags & SAGMS_FLAG_GENERIC_KERNEL);   // BP: per-shot priors
     const bool auto_ceiling = (p->flags & SAGMS_FLAG_AUTO_CEILING) != 0;
-    const bool use_qc = msfam_fast && code->qc_variant >= 0 && (plan.kernel == 0 || plan.kernel == 4);
-    const int qc_form = per_qubit ? 2 : (auto_ceiling ? 1 : 0);   // which instantiation
+    // BP on the column-indexed kernel by default only up to 512 qubits: on the larger shapes
+    // (one 512-thread CTA per SM) its transcendental chains leave too few warps to hide them,
+    // and the one-shot-per-CTA kernel is faster (plan kernel 4 still selects it).
+    const bool use_qc = (msfam_fast || bp_fast) && code->qc_variant >= 0 &&
+                        (plan.kernel == 4 || (plan.kernel == 0 && (!bp || qc_variant(code->qc_variant).np <= 512)));
+    const int qc_form = bp ? 3 : (per_qubit ? 2 : (auto_ceiling ? 1 : 0));   // which instantiation
     const bool use_groups = !use_qc && msfam_fast && code->groups && !per_qubit &&
                             (plan.kernel == 0 || plan.kernel >= 3);
     const bool use_slots = !use_qc && !use_groups && msfam_fast && code->slot_variant >= 0 && plan.kernel != 1;
@@ -1127,7 +1132,8 @@ int sagms_autotune(const sagms_code* code, const sagms_params* params, int64_t s
     std::vector<Plan> cands;
     const bool slots_ok = params->mode != SAGMS_BP && code->slot_variant >= 0;
     const bool groups_ok = params->mode != SAGMS_BP && code->groups && !(params->flags & SAGMS_FLAG_L0_PER_QUBIT);
-    const bool qc_ok = params->mode != SAGMS_BP && code->qc_variant >= 0;
+    const bool qc_ok = code->qc_variant >= 0 &&
+                       !(params->mode == SAGMS_BP && (params->flags & SAGMS_FLAG_L0_PER_QUBIT));
     for (int kernel : {4, 3, 2, 1}) {
         if (kernel == 2 && !slots_ok) continue;
         if (kernel == 3 && !groups_ok) continue;

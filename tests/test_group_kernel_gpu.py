@@ -263,3 +263,40 @@ def test_negative_zero_priors_decide_zero(dev_check):
         lay = _with(p, flags=S.FLAG_L0_PER_QUBIT | S.FLAG_LAYERED)
         G.compare(c, dc, syn, L0q, lay)
         assert not (I.unpack_bits(G.gpu_decode(dc, syn, L0q, lay)["err"], c.n)[:, 126]).any()
+
+
+@pytest.mark.parametrize("lw", [(63, 3), (127, 4), (255, 5), (511, 5), (1023, 5), (1023, 3)])
+def test_column_indexed_bp_bitwise_identical_to_one_shot_per_cta(dev_check, lw):
+    """BP (Eq. 3, per-shot priors in LLR units) on the column-indexed kernel: the same slot
+    order, phi function and prefix / suffix sums as the one-shot-per-CTA kernel, so outputs
+    and posterior traces agree bit for bit (zero syndromes and negative priors included)."""
+    c = I.gb_code(*lw)
+    _, syn, L0, _ = I.workload(c, [0.005, 0.02, 0.06], 1501, seed=lw[0] + 7)
+    syn = syn.copy()
+    L0 = L0.copy()
+    syn[::9] = 0
+    L0[4::13] = -L0[4::13]
+    p = S.Params(mode="bp", max_iter=40)
+    dc = S.DeviceCode.from_code(c)
+    assert "two-group-qc" in dc.kernels
+    assert _same(_decode_with_kernel(c, KERNEL_QC, syn, L0, p), _decode_with_kernel(c, KERNEL_GENERIC, syn, L0, p))
+    tr = _decode_with_kernel(c, KERNEL_GENERIC, syn[:12], L0[:12], p, trace=True)["trace"]
+    tq = _decode_with_kernel(c, KERNEL_QC, syn[:12], L0[:12], p, trace=True)["trace"]
+    assert np.array_equal(np.nan_to_num(tr, nan=7.0), np.nan_to_num(tq, nan=7.0))
+
+
+def test_column_indexed_bp_on_a_recoloured_code_and_oracle_parity(dev_check):
+    """A random (5, 10) LDPC code (slots from the edge colouring, padded slots in the middle
+    of checks after dropped repeats) and GB(255, 5): BP on the column-indexed kernel equals
+    the one-shot-per-CTA kernel and meets the oracle acceptance."""
+    from tests.test_column_slots import _random_code
+    rp, ci = _random_code(1024, 2048, 5, 10, 41)
+    r = I.Code(m=1024, n=2048, row_ptr=rp, col_idx=ci)
+    _, syn, L0, _ = I.workload(r, [0.01, 0.03], 1001, seed=42)
+    p = S.Params(mode="bp", max_iter=40)
+    assert _same(_decode_with_kernel(r, KERNEL_QC, syn, L0, p), _decode_with_kernel(r, KERNEL_GENERIC, syn, L0, p))
+    c = I.gb_code(255, 5)
+    dc = S.DeviceCode.from_code(c)
+    _native.sagms_set_plan(dc.handle, KERNEL_QC)
+    _, syn, L0, _ = I.workload(c, [0.01, 0.03], 400, seed=43)
+    G.compare(c, dc, syn, L0, S.Params(mode="bp", max_iter=60))
