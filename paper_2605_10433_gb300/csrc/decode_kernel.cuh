@@ -21,6 +21,8 @@
 //       one pass for min1 / min2 / sign parity, then the extrinsic output per edge:
 //       MS family (Eqs. 4, 8): (-1)^{s_i + parity + sgn v_j} * min(g * (|v_j| == min1 ? min2 : min1), clip)
 //       BP (Eq. 3): (-1)^{...} * min(phi(sum_{k != j} phi(|v_k|)), clip), with prefix/suffix sums
+//       (in round 1 with one prior per shot every real input is the prior: the sum is
+//       (deg - 1) phi(|L0|) on every real edge)
 //   A4  P_c = L0_c + sum over the qubit's edges of C (Eq. 2's full sum)
 // Sign bits are read straight from the IEEE representation: no -0.0 ever arises (every
 // value is a sum whose first term is the prior, or a difference of two finite values, and
@@ -130,6 +132,9 @@ __global__ void __launch_bounds__(1024, 1) decode_kernel(const DecodeArgs a) {
     }
     pq_ok = __syncthreads_and(pq_ok);
     const float clip = BP ? kBpClip : kMsFamClip;
+    int deg = 0;   // real edges of this thread's check
+#pragma unroll
+    for (int j = 0; j < DC; ++j) deg += (colT[j * Mp + t] != (uint16_t)n) ? 1 : 0;
 
     for (long long shot = blockIdx.x; shot < a.shots; shot += gridDim.x) {
         float prior = 0.0f;
@@ -213,6 +218,15 @@ __global__ void __launch_bounds__(1024, 1) decode_kernel(const DecodeArgs a) {
                     const float mag = (fabsf(v[j]) == m1) ? o2 : o1;
                     C[j * Mp + t] = __uint_as_float(__float_as_uint(mag) ^ (__float_as_uint(v[j]) & kSign));
                 }
+            } else if (it == 0 && !per_qubit) {
+                // Round 1: every real input is the shot's prior, so each real edge's sum over
+                // the other edges is (deg - 1) phi(|L0|) (none for a degree-1 check)
+                const float ph0 = phi_fn(fabsf(prior));
+                const float S1 = (deg >= 2) ? (float)(deg - 1) * ph0 : 0.0f;
+                const float mag = fminf(phi_fn(S1), clip);
+#pragma unroll
+                for (int j = 0; j < DC; ++j)
+                    C[j * Mp + t] = __uint_as_float(__float_as_uint(mag) | (par ^ (__float_as_uint(v[j]) & kSign)));
             } else {
                 float ph[DC];
 #pragma unroll

@@ -268,7 +268,23 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
 #pragma unroll
                 for (int k = 0; k < K; ++k) g[k] = (a.mode == kModeSMS) ? a.alpha : 1.0f;
             }
-            if (fresh && !PQ && !BPK) {
+            if (fresh && !PQ && BPK) {
+                // A3 (Eq. 3) on round-1 inputs, as decode_kernel.cuh: each real edge's sum over
+                // the other edges is (deg - 1) phi(|s|); the parity is the syndrome bit XOR the
+                // sign of s once per edge.  Stored negated (D = -L), the same on every slot.
+                const uint32_t sgn = __float_as_uint(prior) & kSign;
+                const float ph0 = phi_fn(fabsf(prior));
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const uint32_t deg = qc_byte(degs, k);
+                    const uint32_t par = (((sbits >> k) & 1u) << 31) ^ ((deg & 1u) ? sgn : 0u);
+                    const float S1 = (deg >= 2) ? (float)(int)(deg - 1) * ph0 : 0.0f;
+                    const float mag = fminf(phi_fn(S1), kBpClip);
+                    const float d = __uint_as_float(__float_as_uint(mag) | (~(par ^ sgn) & kSign));
+#pragma unroll
+                    for (int j = 0; j < DC; ++j) Cat(j, off[k][j]) = d;
+                }
+            } else if (fresh && !PQ) {
                 // A3 on round-1 inputs: every real edge carries the prior s, padded slots +inf.
                 // The minimum and second minimum of |v| are |s| (a check with one edge has no
                 // second: +inf), the parity is the syndrome bit XOR the sign of s once per
@@ -292,20 +308,12 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
                     for (int p = 0; p < K / 2; ++p)
 #pragma unroll
                         for (int j = 0; j < DC; ++j) v[p][j] = make_float2(PQat(off[2 * p][j]), PQat(off[2 * p + 1][j]));
-                } else if (BPK && fresh) {
-                    // round-1 inputs are the shot's prior on real edges, +inf on padded slots
-                    const uint32_t pad = S::PAD + (uint32_t)PO;
-#pragma unroll
-                    for (int p = 0; p < K / 2; ++p)
-#pragma unroll
-                        for (int j = 0; j < DC; ++j)
-                            v[p][j] = make_float2(off[2 * p][j] == pad ? inf : prior, off[2 * p + 1][j] == pad ? inf : prior);
                 }
 #pragma unroll
                 for (int p = 0; p < K / 2; ++p) {
                     // A3 check-node update for checks 2p and 2p + 1 (C holds negated
                     // messages: P - L = P + D; a fresh shot has no old messages)
-                    if (!((PQ || BPK) && fresh)) {
+                    if (!(PQ && fresh)) {
 #pragma unroll
                         for (int j = 0; j < DC; ++j)
                             v[p][j] = add2(v[p][j], make_float2(Cat(j, off[2 * p][j]), Cat(j, off[2 * p + 1][j])));

@@ -835,11 +835,12 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     const bool msfam_fast = !bp && !(p->flags & SAGMS_FLAG_GENERIC_KERNEL);
     const bool bp_fast = bp && !per_qubit && !(p->flags & SAGMS_FLAG_GENERIC_KERNEL);   // BP: per-shot priors
     const bool auto_ceiling = (p->flags & SAGMS_FLAG_AUTO_CEILING) != 0;
-    // BP on the column-indexed kernel by default only up to 512 qubits: on the larger shapes
-    // (one 512-thread CTA per SM) its transcendental chains leave too few warps to hide them,
-    // and the one-shot-per-CTA kernel is faster (plan kernel 4 still selects it).
+    // BP on the column-indexed kernel by default only up to 128 qubits: on the larger shapes
+    // (one 512-thread CTA of 128-register threads per SM) BP's transcendental chains leave
+    // too few warps to hide them, and the 1024-thread one-shot-per-CTA kernel is faster
+    // (plan kernel 4 still selects it).
     const bool use_qc = (msfam_fast || bp_fast) && code->qc_variant >= 0 &&
-                        (plan.kernel == 4 || (plan.kernel == 0 && (!bp || qc_variant(code->qc_variant).np <= 512)));
+                        (plan.kernel == 4 || (plan.kernel == 0 && (!bp || qc_variant(code->qc_variant).np <= 128)));
     const int qc_form = bp ? 3 : (per_qubit ? 2 : (auto_ceiling ? 1 : 0));   // which instantiation
     const bool use_groups = !use_qc && msfam_fast && code->groups && !per_qubit &&
                             (plan.kernel == 0 || plan.kernel >= 3);
