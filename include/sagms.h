@@ -48,8 +48,8 @@ enum {
     SAGMS_FLAG_L0_PER_QUBIT = 1u,
     /* Run exactly max_iter rounds even after the residual syndrome reaches zero. */
     SAGMS_FLAG_NO_EARLY_STOP = 2u,
-    /* Use the one-shot-per-CTA kernel even where a faster MS-family kernel exists
-     * (cross-checks: all kernels give bitwise identical results). */
+    /* Use the one-shot-per-CTA kernel even where a faster kernel exists (cross-checks:
+     * all kernels give bitwise identical results, BP included). */
     SAGMS_FLAG_GENERIC_KERNEL = 4u,
     /* SAGMS only, per-shot priors only: the gain ceiling of Corollary 1.  Each shot's
      * alpha_max is alpha*(|L0|, d_c) of Eq. 9 for its own prior L0 and the code's largest
