@@ -67,3 +67,50 @@ def mc_run_checkpointed(code, code_name, params, seed, q, checkpoint, L0=None, t
         with open(checkpoint, "a") as f:
             f.write(json.dumps({**key, **counts}) + "\n")
     return counts
+
+
+COUNT_KEYS = ("shots", "failures", "not_converged", "logical", "iters_sum")
+
+
+def mc_frames(code, params, seed, q, shot0, shots, L0):
+    """Counts of frames shot0 .. shot0 + shots - 1 of the on-device generator: sample, decode
+    and logical check on the GPU (logicals attached to ``code``)."""
+    from . import decode, mc_check, mc_sample
+    if shots <= 0:
+        return dict.fromkeys(COUNT_KEYS, 0)
+    err, syn, l0 = mc_sample(code, seed, q, shot0, shots, L0=L0)
+    e_hat, conv, iters = decode(code, syn, l0, params)
+    _, counts = mc_check(code, err, e_hat, conv, iters)
+    return counts
+
+
+def mc_run_sharded(code, params, seed, q, L0=None, target_failures=500, max_shots=20_000_000, batch=1 << 22,
+                   group=None, frames=None):
+    """The Monte Carlo protocol of Sec. V (setup) split across the ranks of a process group
+    (one GPU per rank).  In round k rank r decodes frames [(kW + r)B, (kW + r + 1)B) of the
+    counter-based generator (W ranks, batch B, clipped at ``max_shots``); one all-reduce then
+    sums the five counters, and every rank applies the stopping rule to the sums, so the ranks
+    stop together.  The frames decoded are those of a single-process ``mc_run`` with batch W*B
+    and the totals equal its counts.  Without an initialised process group this is that run on
+    one GPU.  ``frames`` replaces the per-rank batch runner (``mc_frames``)."""
+    import torch
+    import torch.distributed as dist
+    from . import llr
+    frames = frames or mc_frames
+    on = dist.is_available() and dist.is_initialized()
+    world = dist.get_world_size(group) if on else 1
+    rank = dist.get_rank(group) if on else 0
+    dev = "cuda" if on and dist.get_backend(group) == "nccl" else "cpu"
+    prior = llr(q) if L0 is None else float(L0)
+    total = dict.fromkeys(COUNT_KEYS, 0)
+    k = 0
+    while total["failures"] < target_failures and total["shots"] < max_shots:
+        s0 = (k * world + rank) * batch
+        c = frames(code, params, seed, q, s0, max(0, min(batch, max_shots - s0)), prior)
+        t = torch.tensor([int(c[key]) for key in COUNT_KEYS], dtype=torch.int64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, group=group)
+        for key, v in zip(COUNT_KEYS, t.tolist()):
+            total[key] += v
+        k += 1
+    return total

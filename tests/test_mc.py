@@ -303,3 +303,18 @@ def test_checkpointed_run_on_the_gpu_equals_one_run(dev, tmp_path):
     got = sweep.mc_run_checkpointed(dc, "GB(127,4)", p, 5, 0.04, ck, target_failures=10**9, max_shots=10240,
                                     batch=2048)
     assert got == S.mc_run(dc, p, 5, 0.04, target_failures=10**9, max_shots=10240, batch=10240)
+
+
+@gpu
+def test_sharded_run_on_one_gpu_equals_one_run(dev):
+    """mc_run_sharded without a process group (one rank): its per-batch sample -> decode ->
+    check through the Python entry points counts the same frames as the library's fused
+    mc_run, failure target and frame cap included."""
+    from paper_2605_10433_gb300 import sweep
+    c = I.gb_code(127, 4)
+    dc = S.DeviceCode.from_code(c)
+    dc.set_logicals(S.x_logicals(c))
+    p = S.Params(mode="sagms", max_iter=40)
+    for target, cap in ((25, 10**6), (10**9, 9000)):
+        got = sweep.mc_run_sharded(dc, p, 5, 0.05, target_failures=target, max_shots=cap, batch=2048)
+        assert got == S.mc_run(dc, p, 5, 0.05, target_failures=target, max_shots=cap, batch=2048)

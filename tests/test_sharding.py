@@ -58,3 +58,58 @@ def test_two_rank_shards_match_single_process(tmp_path):
     r = oracle.decode_code(code, syn_all, L0_all.astype(np.float64), mode=oracle.SAGMS, max_iter=100)
     got = np.load(os.path.join(tmp_path, "counters.npy"))
     assert list(got) == [world * SHOTS_PER_RANK, int((r["conv"] == 0).sum()), int(r["iters"].sum())]
+
+
+def _fake_frames(code, params, seed, q, shot0, shots, L0):
+    """Stand-in for the GPU batch runner: counts of frames shot0 .. shot0 + shots - 1 as a
+    fixed function of the frame index (a failure every 97 frames, half of them logical)."""
+    t = np.arange(shot0, shot0 + max(shots, 0), dtype=np.int64)
+    fail = ((t * 7 + seed) % 97) == 0
+    logical = fail & (t % 2 == 0)
+    return {"shots": int(t.size), "failures": int(fail.sum()), "not_converged": int((fail & ~logical).sum()),
+            "logical": int(logical.sum()), "iters_sum": int((1 + t % 3).sum())}
+
+
+def _mc_rank_main(rank, world, port, outdir, target, max_shots, batch):
+    import sys
+    sys.path.insert(0, ROOT)
+    import json
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_2605_10433_gb300 import sweep
+    seen = []
+
+    def frames(code, params, seed, q, shot0, shots, L0):
+        seen.append([shot0, shots])
+        return _fake_frames(code, params, seed, q, shot0, shots, L0)
+
+    total = sweep.mc_run_sharded(None, None, 5, 0.01, target_failures=target, max_shots=max_shots, batch=batch,
+                                 frames=frames)
+    with open(os.path.join(outdir, f"mc{rank}.json"), "w") as f:
+        json.dump({"total": total, "seen": seen}, f)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("target,max_shots", [(40, 10**7), (10**9, 23_000)])
+def test_two_rank_monte_carlo_matches_single_process(tmp_path, target, max_shots):
+    """The sharded Monte Carlo protocol on two gloo ranks: the ranks decode disjoint frame
+    ranges that together are [0, K W B), stop in the same round (failure target or frame cap,
+    clipped at the cap), and both end with the counts of one process running the protocol with
+    batch W B."""
+    import json
+    from paper_2605_10433_gb300 import sweep
+    world, batch = 2, 1000
+    mp.start_processes(_mc_rank_main, args=(world, _free_port(), str(tmp_path), target, max_shots, batch),
+                       nprocs=world, join=True, start_method="spawn")
+    out = [json.load(open(os.path.join(tmp_path, f"mc{r}.json"))) for r in range(world)]
+    ref = dict.fromkeys(sweep.COUNT_KEYS, 0)
+    while ref["failures"] < target and ref["shots"] < max_shots:
+        c = _fake_frames(None, None, 5, 0.01, ref["shots"], min(world * batch, max_shots - ref["shots"]), 0.0)
+        for k in sweep.COUNT_KEYS:
+            ref[k] += c[k]
+    assert out[0]["total"] == ref and out[1]["total"] == ref
+    ranges = sorted((s0, s0 + n) for o in out for s0, n in o["seen"] if n > 0)
+    assert ranges[0][0] == 0 and all(a[1] == b[0] for a, b in zip(ranges, ranges[1:]))
+    assert ranges[-1][1] == ref["shots"]
