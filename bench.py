@@ -394,7 +394,7 @@ def main():
     traffic = None if args.layered else profile_traffic(shots)
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
             "frac": achieved / peak, "traffic": traffic,
-            "kernel": "sagms::layered_kernel<10,128>" if args.layered else "sagms::qc_kernel<10,5,4>",
+            "kernel": "sagms::layered_kernel<10,64>" if args.layered else "sagms::qc_kernel<10,5,4>",
             "note": (f"ops = sum over shots of iters x {ops_it} per iteration (Eq. 15 / Table I CN cost + VN sum, "
                      f"decision, residual XOR, popcount); peak = {props.multi_processor_count} SMs x 128 lanes x "
                      f"{sm_max:.0f} MHz (derived from unit counts and clock); HBM bound "

@@ -12,7 +12,7 @@
 // Checks of one layer touch disjoint qubits, so one thread per check updates P in place.
 // The gains of a round come from the residual syndrome at its start (Eqs. 1, 6, 7).
 //
-// One CTA of T threads decodes one shot at a time (static stride over shots).  Shared
+// One CTA of T threads (32, 64 or 128) decodes one shot at a time (static stride over shots).  Shared
 // memory holds, per shot:
 //   P[Np]          posteriors (column n and up: +inf, the target of padded check slots)
 //   PQ[Np]         per-qubit priors (SAGMS_FLAG_L0_PER_QUBIT only)

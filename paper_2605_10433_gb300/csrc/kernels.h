@@ -56,7 +56,7 @@ inline const QcVariant& qc_variant(int v) {
 
 // Layered schedule (decode_layered.cuh), MS family: (padded check degree, threads per CTA).
 // A code takes the first check degree that covers it, with 32 threads when no layer holds
-// more than 64 checks and 128 otherwise.
+// more than 64 checks, 64 when none holds more than 128, and 128 otherwise.
 using LayeredFn = void (*)(const DecodeArgs, const sagms::LayeredLayout);
 struct LayeredVariant { int dc, t; LayeredFn fn; };
 extern const LayeredVariant kLayeredVariants[];
