@@ -61,7 +61,8 @@ def _load():
                                       ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_int, ctypes.c_uint, ctypes.c_int64,
                                       P(ctypes.c_uint32), P(ctypes.c_double), P(ctypes.c_uint32),
-                                      P(ctypes.c_uint8), P(ctypes.c_int32), P(ctypes.c_double)]
+                                      P(ctypes.c_uint8), P(ctypes.c_int32), P(ctypes.c_double),
+                                      P(ctypes.c_double)]
         lib.oracle_decode.restype = ctypes.c_int
         lib.oracle_alpha_star.argtypes = [ctypes.c_double, ctypes.c_int]
         lib.oracle_alpha_star.restype = ctypes.c_double
@@ -82,7 +83,8 @@ def decode(m, n, row_ptr, col_idx, syn, L0, mode=SAGMS, alpha=0.75, alpha_min=0.
     ``L0``: [shots] per-shot prior, or [n] with FLAG_L0_PER_QUBIT.  Returns a dict with
     ``err`` [shots][ceil(n/32)] uint32, ``conv`` [shots] uint8, ``iters`` [shots] int32 and,
     with ``trace=True``, ``trace`` [shots][max_iter+1][n] float64 posteriors (units the
-    decoder runs in: L0-normalised for the MS family with a per-shot prior)."""
+    decoder runs in: L0-normalised for the MS family with a per-shot prior) and ``scale``
+    (same shape): |L0_j| + sum of |messages| into qubit j, the size of P_j's terms."""
     lib = _load()
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
     col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
@@ -99,6 +101,7 @@ def decode(m, n, row_ptr, col_idx, syn, L0, mode=SAGMS, alpha=0.75, alpha_min=0.
     conv = np.zeros(shots, dtype=np.uint8)
     iters = np.zeros(shots, dtype=np.int32)
     tr = np.zeros((shots, max_iter + 1, n), dtype=np.float64) if trace else None
+    sc = np.zeros((shots, max_iter + 1, n), dtype=np.float64) if trace else None
 
     def run(lo, hi):
         if hi <= lo:
@@ -108,7 +111,8 @@ def decode(m, n, row_ptr, col_idx, syn, L0, mode=SAGMS, alpha=0.75, alpha_min=0.
                                alpha, alpha_min, alpha_max, eta_unsat, max_iter, flags, hi - lo,
                                _p(syn[lo:hi], ctypes.c_uint32), _p(np.ascontiguousarray(Ls), ctypes.c_double),
                                _p(err[lo:hi], ctypes.c_uint32), _p(conv[lo:hi], ctypes.c_uint8),
-                               _p(iters[lo:hi], ctypes.c_int32), _p(tr[lo:hi] if tr is not None else None, ctypes.c_double))
+                               _p(iters[lo:hi], ctypes.c_int32), _p(tr[lo:hi] if tr is not None else None, ctypes.c_double),
+                               _p(sc[lo:hi] if sc is not None else None, ctypes.c_double))
         if rc != 0:
             raise RuntimeError("oracle_decode: bad arguments")
 
@@ -122,6 +126,7 @@ def decode(m, n, row_ptr, col_idx, syn, L0, mode=SAGMS, alpha=0.75, alpha_min=0.
     out = {"err": err, "conv": conv, "iters": iters}
     if tr is not None:
         out["trace"] = tr
+        out["scale"] = sc
     return out
 
 

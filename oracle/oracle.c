@@ -122,13 +122,16 @@ static void cn_update(int i, const int32_t* row_ptr, int s_i, int msfam, double 
  *   conv:  [shots] 1 if s~ = 0 at return (out).   iters: [shots] (out).
  *   trace: optional [shots][max_iter+1][n] posteriors P_j at each check (i),
  *          in the units the decoder runs in; rows after the return are left as is.
+ *   scale: optional, same layout: |L0_j| + sum_{i in N(j)} |r(i,j)| at each check (i), the
+ *          magnitude of the terms of P_j's sum, which bounds the rounding error a
+ *          lower-precision evaluation of P_j carries (test acceptance; not part of the method).
  * Returns 0, or -1 on bad arguments / allocation failure.
  */
 int oracle_decode(int m, int n, const int32_t* row_ptr, const int32_t* col_idx,
                   int mode, double alpha, double alpha_min, double alpha_max, double eta_unsat,
                   int max_iter, unsigned flags, int64_t shots,
                   const uint32_t* syn, const double* L0,
-                  uint32_t* err, uint8_t* conv, int32_t* iters, double* trace) {
+                  uint32_t* err, uint8_t* conv, int32_t* iters, double* trace, double* scale) {
     if (m < 0 || n <= 0 || max_iter < 0 || shots < 0 || !row_ptr || !col_idx || !syn || !L0 ||
         !err || !conv || !iters || mode < 0 || mode > 3)
         return -1;
@@ -206,6 +209,7 @@ int oracle_decode(int m, int n, const int32_t* row_ptr, const int32_t* col_idx,
         const uint32_t* sy = syn + (size_t)s * mw;
         uint32_t* eo = err + (size_t)s * nw;
         double* tr = trace ? trace + (size_t)s * (size_t)(max_iter + 1) * (size_t)n : NULL;
+        double* sc = scale ? scale + (size_t)s * (size_t)(max_iter + 1) * (size_t)n : NULL;
 
         /* A non-finite prior marks the shot invalid: e_hat = 0, conv = 0, iters = -1. */
         int bad = 0;
@@ -245,6 +249,13 @@ int oracle_decode(int m, int n, const int32_t* row_ptr, const int32_t* col_idx,
                 ehat[j] = (acc < 0.0) ? 1 : 0;
             }
             if (tr) memcpy(tr + (size_t)l * n, P, sizeof(double) * (size_t)n);
+            if (sc) {
+                for (int j = 0; j < n; ++j) {
+                    double a = fabs(prior[j]);
+                    for (int t = vn_ptr[j]; t < vn_ptr[j + 1]; ++t) a += fabs(r[vn_edges[t]]);
+                    sc[(size_t)l * n + j] = a;
+                }
+            }
             int unsat = 0;
             for (int i = 0; i < m; ++i) {
                 int x = bit_of(sy, i);

@@ -45,6 +45,8 @@ struct LayeredLayout {
     const uint32_t* rec;  // [m][R]
     const int* lay_ptr;   // [L + 1] first position of each layer
     int L;
+    const uint16_t* qe;   // [n][QE] edges of each qubit: layer position << 5 | record slot, 0xFFFF pads
+    int QE;
 };
 
 __host__ __device__ inline size_t layered_smem_bytes(int Mp, int Np, bool per_qubit) {
@@ -155,6 +157,26 @@ __global__ void __launch_bounds__(T) layered_kernel(const DecodeArgs a, const La
         }
     };
 
+    // Posteriors rebuilt from the current messages, P_c = L0_c + sum over the qubit's edges in
+    // a fixed order (Eq. 2): run after every round but the first, so that a posterior's
+    // rounding error depends on the messages of that round only, not on every value it took
+    // while updated in place (round 1 starts from zero messages and needs no rebuild).
+    auto rebuild = [&](float prior_c) {
+        for (int c = t; c < n; c += T) {
+            float acc = per_qubit ? PQ[c] : prior_c;
+            const uint16_t* q = lay.qe + (size_t)c * lay.QE;
+            for (int k = 0; k < lay.QE; ++k) {
+                const uint32_t e = __ldg(q + k);
+                if (e == 0xffffu) break;
+                const int p = (int)(e >> 5), j = (int)(e & 31u);
+                const uint32_t mt = meta[p];
+                const float mag = (j == (int)(mt >> 24)) ? O2[p] : O1[p];
+                acc += __uint_as_float(__float_as_uint(mag) | ((mt << (31 - j)) & kSign));
+            }
+            P[c] = acc;
+        }
+    };
+
     for (int c = n + t; c < Np; c += T) P[c] = inf;
     int pq_ok = 1;
     if (per_qubit) {
@@ -229,8 +251,13 @@ __global__ void __launch_bounds__(T) layered_kernel(const DecodeArgs a, const La
             const float g0 = (a.mode == kModeSAGMS) ? amax - (amax - a.amin) * ((float)cnt * a.inv_m)
                                                     : ((a.mode == kModeSMS) ? a.alpha : 1.0f);
             // A3 + A4, layer by layer
-            if (it == 0) sweep(std::true_type{}, g0);
-            else sweep(std::false_type{}, g0);
+            if (it == 0) {
+                sweep(std::true_type{}, g0);
+            } else {
+                sweep(std::false_type{}, g0);
+                rebuild(prior);
+                sync();
+            }
         }
 
         // A7: write-out

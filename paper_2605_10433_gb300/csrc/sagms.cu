@@ -379,6 +379,7 @@ struct sagms_code {
     int lay_max;           // checks in the largest layer
     uint32_t* d_lrec;      // [m][R] check records in layer order (LayeredRec)
     int* d_lptr;           // [lay_L + 1] first position of each layer
+    uint16_t* d_lqe;       // [n][dv_max] edges of each qubit (layer position << 5 | slot), 0xFFFF pads
     int k_logicals;        // logical operators attached for the Monte Carlo check (-1: none)
     uint32_t* d_logicals;  // [k][ceil(n/32)]
     // Launch plan chosen by sagms_autotune (0 = defaults), packed so decodes on other
@@ -618,6 +619,7 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
     int lv = -1, lay_max = 0;
     std::vector<int> lorder, lptr;
     std::vector<uint32_t> lrec;
+    std::vector<uint16_t> lqe;
     first_fit_layers(m, n, row_ptr, col_idx, lorder, lptr);
     for (size_t l = 0; l + 1 < lptr.size(); ++l) lay_max = std::max(lay_max, lptr[l + 1] - lptr[l]);
     for (int v = 0; v < kNumLayeredVariants && lv < 0; ++v) {
@@ -643,6 +645,16 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
                     r[DCl] = (uint32_t)lorder[p] | ((uint32_t)(row_ptr[lorder[p] + 1] - row_ptr[lorder[p]]) << 16);
                 }
             }
+        // qubit-to-edge lists for the posterior rebuild, in layer-position order
+        lqe.assign((size_t)n * std::max(dv_max, 1), (uint16_t)0xFFFFu);
+        std::vector<int> fillq(n, 0);
+        for (int p = 0; p < m; ++p)
+            for (int j = 0; j < DCl; ++j) {
+                const uint32_t o = lrec[(size_t)p * R + j];
+                if (o == 4u * (uint32_t)n) continue;
+                const int c = (int)(o / 4u);
+                lqe[(size_t)c * dv_max + fillq[c]++] = (uint16_t)((p << 5) | j);
+            }
     }
 
     // Checks of each qubit, for syndrome formation in the Monte Carlo sampler.
@@ -660,6 +672,7 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
     code->lay_max = lay_max;
     code->d_lrec = nullptr;
     code->d_lptr = nullptr;
+    code->d_lqe = nullptr;
     code->d_qchk = nullptr;
     code->k_logicals = -1;
     code->d_logicals = nullptr;
@@ -710,6 +723,8 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
         if (ce == cudaSuccess) ce = cudaMalloc(&code->d_lptr, lptr.size() * sizeof(int));
         if (ce == cudaSuccess) ce = cudaMemcpy(code->d_lrec, lrec.data(), lrec.size() * 4, cudaMemcpyHostToDevice);
         if (ce == cudaSuccess) ce = cudaMemcpy(code->d_lptr, lptr.data(), lptr.size() * 4, cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess) ce = cudaMalloc(&code->d_lqe, lqe.size() * sizeof(uint16_t));
+        if (ce == cudaSuccess) ce = cudaMemcpy(code->d_lqe, lqe.data(), lqe.size() * 2, cudaMemcpyHostToDevice);
     }
     if (ce == cudaSuccess) {
         ce = cudaMalloc(&code->d_qchk, qchk.size() * sizeof(uint16_t));
@@ -726,6 +741,7 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
         cudaFree(code->d_colQ);
         cudaFree(code->d_lrec);
         cudaFree(code->d_lptr);
+        cudaFree(code->d_lqe);
         delete code;
         return cuda_fail(ce, "sagms_load_code upload");
     }
@@ -747,6 +763,7 @@ void sagms_free_code(sagms_code* code) {
     cudaFree(code->d_colQ);
     cudaFree(code->d_lrec);
     cudaFree(code->d_lptr);
+    cudaFree(code->d_lqe);
     cudaFree(code->d_qchk);
     cudaFree(code->d_logicals);
     if (prev >= 0 && prev != code->device) cudaSetDevice(prev);
@@ -797,7 +814,7 @@ int launch_layered(const sagms_code* code, const DecodeArgs& a, bool per_qubit, 
     if (ce != cudaSuccess) return cuda_fail(ce, "occupancy query");
     if (per_sm < 1) return fail(SAGMS_ERR_SIZE, "kernel does not fit on an SM");
     const long long grid = std::min<long long>(a.shots, (long long)per_sm * sms);
-    const LayeredLayout lay{code->d_lrec, code->d_lptr, code->lay_L};
+    const LayeredLayout lay{code->d_lrec, code->d_lptr, code->lay_L, code->d_lqe, std::max(code->dv_max, 1)};
     V.fn<<<(unsigned)grid, V.t, smem, stream>>>(a, lay);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return cuda_fail(ce, "decode launch");

@@ -1,0 +1,93 @@
+"""Seeded random cross-checks of every kernel on random codes.
+
+Each case draws an irregular code (m up to 1024 checks, qubit degrees up to 8, check degrees
+up to 16, random column order in every row), a decoder mode and flags, priors with negative
+and zero entries and random (not necessarily reachable) syndromes.  Every kernel that has a
+layout for the code must agree bit for bit with the one-shot-per-CTA kernel, and the first
+shots go to the FP64 oracle under the acceptance of tests/gpu_helpers.py; the layered
+schedule is checked against the oracle's layered schedule."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2605_10433_gb300 as S
+from paper_2605_10433_gb300 import _native
+from paper_2605_10433_gb300 import inputs as I
+from tests import gpu_helpers as G
+
+pytestmark = pytest.mark.gpu
+
+KERNELS = {"two-slot": 2, "two-group": 3, "two-group-qc": 4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def dev_check():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _random_case(seed):
+    rng = np.random.default_rng(seed)
+    m = int(rng.choice([17, 60, 128, 250, 511, 700, 1024]))
+    n = int(rng.integers(m + 1, 2 * m + 2))
+    dv_max = int(rng.integers(2, 9))
+    dc_cap = int(rng.integers(4, 17))
+    deg = rng.integers(1, dv_max + 1, size=n)
+    rows = [set() for _ in range(m)]
+    for c in range(n):
+        for i in rng.choice(m, size=min(int(deg[c]), m), replace=False):
+            if len(rows[i]) < dc_cap:
+                rows[i].add(c)
+    rows = [rng.permutation(sorted(r)).tolist() for r in rows]
+    rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    code = I.Code(m=m, n=n, row_ptr=rp, col_idx=np.array([c for r in rows for c in r], dtype=np.int32))
+    mode = str(rng.choice(["ms", "sms", "sagms", "sagms", "bp"]))
+    flags = 0
+    if mode != "bp" and rng.random() < 0.3:
+        flags |= S.FLAG_AUTO_CEILING if mode == "sagms" and rng.random() < 0.5 else 0
+    per_qubit = rng.random() < 0.3 and not (flags & S.FLAG_AUTO_CEILING)
+    if per_qubit:
+        flags |= S.FLAG_L0_PER_QUBIT
+    p = S.Params(mode=mode, alpha=float(rng.uniform(0.5, 1.0)), alpha_min=0.3, alpha_max=0.5, eta_unsat=1.1,
+                 max_iter=int(rng.integers(1, 40)), flags=flags)
+    shots = int(rng.integers(1, 700))
+    syn = rng.integers(0, 2**32, size=(shots, (m + 31) // 32), dtype=np.uint64).astype(np.uint32)
+    if m % 32:
+        syn[:, -1] &= np.uint32((1 << (m % 32)) - 1)
+    syn[rng.random(shots) < 0.5] = 0
+    density = rng.uniform(0.0, 0.1)
+    sparse = I.sample(code, density, shots, seed=seed)[1]
+    keep = rng.random(shots) < 0.7
+    syn[keep] = sparse[keep]
+    if per_qubit:
+        L0 = rng.uniform(-2.0, 8.0, size=n).astype(np.float32)
+        L0[rng.random(n) < 0.05] = 0.0
+    else:
+        L0 = rng.uniform(-2.0, 8.0, size=shots).astype(np.float32)
+        L0[rng.random(shots) < 0.05] = 0.0
+    return code, p, syn, L0
+
+
+def _decode(code, kernel, syn, L0, p):
+    dc = S.DeviceCode.from_code(code)
+    _native.sagms_set_plan(dc.handle, kernel)
+    return dc, G.gpu_decode(dc, syn, L0, p)
+
+
+def _same(a, b):
+    return all(np.array_equal(a[k], b[k]) for k in ("err", "conv", "iters"))
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_code_all_kernels_and_oracle(seed):
+    code, p, syn, L0 = _random_case(seed)
+    dc, ref = _decode(code, 1, syn, L0, p)
+    for name in dc.kernels:
+        if name in KERNELS:
+            _, got = _decode(code, KERNELS[name], syn, L0, p)
+            assert _same(got, ref), (seed, name, p)
+    k = min(len(syn), 60)
+    G.compare(code, dc, syn[:k], L0 if p.flags & S.FLAG_L0_PER_QUBIT else L0[:k], p)
+    if p.mode != "bp" and code.row_ptr.size and np.diff(code.row_ptr).max() <= 24:
+        lay = S.Params(**{**p.__dict__, "flags": p.flags | S.FLAG_LAYERED})
+        G.compare(code, dc, syn[:k], L0 if p.flags & S.FLAG_L0_PER_QUBIT else L0[:k], lay)

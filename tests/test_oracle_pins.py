@@ -295,3 +295,15 @@ def test_exact_modes_are_invariant_under_relabelling(mode, alpha):
     assert np.array_equal(e1, I.unpack_bits(r0["err"], c.n))
     assert np.array_equal(r1["conv"], r0["conv"]) and np.array_equal(r1["iters"], r0["iters"])
     assert 0 < r0["conv"].sum() < 300          # both outcomes occur
+
+
+@pytest.mark.parametrize("layered", [False, True])
+def test_scale_trace_bounds_the_posterior(layered):
+    """The acceptance helper of the GPU tests: the scale trace is |L0_j| + sum of |messages|,
+    so it bounds |P_j| (triangle inequality) and equals |L0_j| before the first round."""
+    c = I.gb_code(63, 3)
+    _, syn, L0, _ = I.workload(c, [0.04, 0.08], 20, seed=12)
+    r = oracle.decode_code(c, syn, L0, mode=oracle.SAGMS, max_iter=6, trace=True,
+                           flags=oracle.FLAG_NO_EARLY_STOP | (oracle.FLAG_LAYERED if layered else 0))
+    assert (r["scale"] >= np.abs(r["trace"]) - 1e-12).all()
+    np.testing.assert_array_equal(r["scale"][:, 0, :], np.abs(r["trace"][:, 0, :]))
