@@ -31,6 +31,8 @@ FLAG_NO_EARLY_STOP = 2
 FLAG_NATURAL_UNITS = 8
 FLAG_AUTO_CEILING = 16
 FLAG_LAYERED = 32
+FLAG_PERTURB = 64        # test acceptance only: FP32 rounding model (oracle.c)
+FLAG_PERTURB_NEG = 128   # its mirror image
 
 MSFAM_CLIP = 1.0e6
 BP_CLIP = 23.718998

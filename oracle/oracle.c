@@ -64,6 +64,14 @@
  *     outputs r(i,j) by the rule of (iv) with the round's gain g_i;
  *   - the gains of a round come from the residual at its start, (i)-(iii), as in
  *     the flooding schedule.
+ *
+ * ORACLE_FLAG_PERTURB (test acceptance only, not part of the method): a model of FP32
+ * rounding for the conditioning analysis of the GPU tests.  Every posterior of (i) and every
+ * VN->CN input of (v) or of a layered round is moved by s * 2^-23 * (|L0_j| + the sum of the
+ * magnitudes of its terms), with s = +-1 a fixed pseudo-random sign per item and round
+ * (the splitmix64 finaliser of Steele, Lea and Flood, OOPSLA 2014, on the item and round
+ * numbers), all signs flipped under ORACLE_FLAG_PERTURB_NEG.  A shot whose outcome moves
+ * under it has no answer that FP32 arithmetic determines.
  */
 #include <math.h>
 #include <stdint.h>
@@ -80,6 +88,8 @@
 #define ORACLE_FLAG_NATURAL_UNITS 8u  /* oracle only: keep the MS family in LLR units */
 #define ORACLE_FLAG_AUTO_CEILING 16u
 #define ORACLE_FLAG_LAYERED 32u
+#define ORACLE_FLAG_PERTURB 64u       /* test only: the FP32 rounding model below */
+#define ORACLE_FLAG_PERTURB_NEG 128u  /* test only: its mirror image */
 
 double oracle_alpha_star(double L0, int dc);
 
@@ -87,6 +97,15 @@ static const double MSFAM_CLIP = 1.0e6;
 static const double BP_CLIP = 23.718998;
 
 static int bit_of(const uint32_t* w, int k) { return (int)((w[k >> 5] >> (k & 31)) & 1u); }
+
+/* +1 or -1, a fixed function of (item, round) (ORACLE_FLAG_PERTURB). */
+static double pert_sign(uint64_t item, uint64_t round) {
+    uint64_t z = item * 0x9E3779B97F4A7C15ull + (round + 1u) * 0xD1B54A32D192ED03ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (z & 1u) ? 1.0 : -1.0;
+}
 
 /* (iv) for one check i: every outgoing message r(i,j) from the incoming q over M(i)\j,
  * leave-one-out written out directly (Eqs. 3, 4, 8). */
@@ -182,6 +201,7 @@ int oracle_decode(int m, int n, const int32_t* row_ptr, const int32_t* col_idx,
     const int normalise = msfam && !per_qubit && !(flags & ORACLE_FLAG_NATURAL_UNITS);
     const int early_stop = !(flags & ORACLE_FLAG_NO_EARLY_STOP);
     const int layered = (flags & ORACLE_FLAG_LAYERED) != 0;
+    const double pert = (flags & ORACLE_FLAG_PERTURB) ? ((flags & ORACLE_FLAG_PERTURB_NEG) ? -0x1p-23 : 0x1p-23) : 0.0;
     if (layered) {
         /* first-fit layer of every check in index order, then the checks by (layer, index) */
         int nlayers = 0;
@@ -243,8 +263,12 @@ int oracle_decode(int m, int n, const int32_t* row_ptr, const int32_t* col_idx,
         for (;;) {
             /* (i) posterior, hard decision, residual syndrome (Eq. 1) */
             for (int j = 0; j < n; ++j) {
-                double acc = prior[j];
-                for (int t = vn_ptr[j]; t < vn_ptr[j + 1]; ++t) acc += r[vn_edges[t]];
+                double acc = prior[j], mag = fabs(prior[j]);
+                for (int t = vn_ptr[j]; t < vn_ptr[j + 1]; ++t) {
+                    acc += r[vn_edges[t]];
+                    mag += fabs(r[vn_edges[t]]);
+                }
+                if (pert != 0.0) acc += pert * pert_sign((uint64_t)nnz + (uint64_t)j, (uint64_t)l) * mag;
                 P[j] = acc;
                 ehat[j] = (acc < 0.0) ? 1 : 0;
             }
@@ -284,9 +308,13 @@ int oracle_decode(int m, int n, const int32_t* row_ptr, const int32_t* col_idx,
                 for (int j = 0; j < n; ++j) {
                     for (int t = vn_ptr[j]; t < vn_ptr[j + 1]; ++t) {
                         const int e = vn_edges[t];
-                        double acc = prior[j];
+                        double acc = prior[j], mag = fabs(prior[j]);
                         for (int u = vn_ptr[j]; u < vn_ptr[j + 1]; ++u)
-                            if (u != t) acc += r[vn_edges[u]];
+                            if (u != t) {
+                                acc += r[vn_edges[u]];
+                                mag += fabs(r[vn_edges[u]]);
+                            }
+                        if (pert != 0.0) acc += pert * pert_sign((uint64_t)e, (uint64_t)l) * mag;
                         q[e] = acc;
                     }
                 }
@@ -297,9 +325,13 @@ int oracle_decode(int m, int n, const int32_t* row_ptr, const int32_t* col_idx,
                     const int i = order[o];
                     for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
                         const int j = col_idx[e];
-                        double acc = prior[j];
+                        double acc = prior[j], mag = fabs(prior[j]);
                         for (int u = vn_ptr[j]; u < vn_ptr[j + 1]; ++u)
-                            if (vn_edges[u] != e) acc += r[vn_edges[u]];
+                            if (vn_edges[u] != e) {
+                                acc += r[vn_edges[u]];
+                                mag += fabs(r[vn_edges[u]]);
+                            }
+                        if (pert != 0.0) acc += pert * pert_sign((uint64_t)e, (uint64_t)l) * mag;
                         q[e] = acc;
                     }
                     cn_update(i, row_ptr, bit_of(sy, i), msfam, gain[i], q, r);

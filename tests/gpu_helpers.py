@@ -5,7 +5,10 @@ Acceptance (the tolerances of the decoder's specification, with the readings bel
 * Per-shot outputs (e_hat, conv, iters) identical on >= 99.99% of shots.  Every
   mismatching shot is traced to its first divergent check l_d.  A shot whose FP64 outcome
   itself changes under an FP32-level perturbation (exact ties of symmetric error patterns,
-  chaotic trajectories) has no FP32-determined answer: it is reported, not counted.  So is
+  chaotic trajectories, FP32 rounding errors of large terms carried through the graph:
+  priors and gains scaled by 1 +- 2^-23, and the oracle's rounding model that moves every
+  posterior and every VN->CN input by +-2^-23 times the size of its terms) has no
+  FP32-determined answer: it is reported, not counted.  So is
   a divergence past the shot's conditioning horizon (below), and one whose differing
   posteriors all lie within the FP32 resolution of their own sums: |P_j| < 64 * 2^-24 * S_j,
   with S_j = |L0_j| + sum of |messages into j| at that check or the one before (the oracle's
@@ -103,8 +106,11 @@ def _normwise(a, b):
 
 
 def conditioning(code, syn1, L01, p: S.Params):
-    """FP64 trajectory of one shot and its 1 +- 2^-23 perturbations.  Returns (trace, outcome
-    stable?, horizon), horizon = last check whose normwise posterior change stays <= 1e-6."""
+    """FP64 trajectory of one shot and its FP32-level perturbations: priors and gains scaled by
+    1 +- 2^-23, and the oracle's FP32 rounding model (every posterior and every VN->CN input
+    moved by +-2^-23 times the size of its terms, both sign patterns).  Returns (trace,
+    outcome stable?, horizon), horizon = last check whose normwise posterior change stays
+    <= 1e-6 under all of them."""
     o = oracle_decode(code, syn1, L01, p, trace=True)
     n = code.n
     last = int(o["iters"][0])
@@ -121,6 +127,15 @@ def conditioning(code, syn1, L01, p: S.Params):
             if _normwise(q["trace"][0, l, :n], o["trace"][0, l, :n]) > HORIZON_RTOL:
                 horizon = min(horizon, l - 1)
                 break
+    if not (p.mode == "ms" and not (p.flags & 1)):   # L0-normalised MS is integer-exact
+        for extra in (oracle.FLAG_PERTURB, oracle.FLAG_PERTURB | oracle.FLAG_PERTURB_NEG):
+            q = oracle_decode(code, syn1, L01, S.Params(**{**p.__dict__, "flags": p.flags | extra}), trace=True)
+            if not (np.array_equal(q["err"], o["err"]) and q["iters"][0] == o["iters"][0] and q["conv"][0] == o["conv"][0]):
+                stable = False
+            for l in range(min(last, int(q["iters"][0])) + 1):
+                if _normwise(q["trace"][0, l, :n], o["trace"][0, l, :n]) > HORIZON_RTOL:
+                    horizon = min(horizon, l - 1)
+                    break
     return o, stable, horizon
 
 
