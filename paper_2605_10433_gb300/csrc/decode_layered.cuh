@@ -53,8 +53,13 @@ __host__ __device__ inline size_t layered_smem_bytes(int Mp, int Np, bool per_qu
     return (size_t)Np * 4 * (per_qubit ? 2 : 1) + (size_t)Mp * 12 + (size_t)(Mp / 32) * 8 + 16;
 }
 
+// Posteriors are rebuilt after a round in which one reached this magnitude (L0-normalised
+// units; always with per-qubit priors): below it, an in-place update's rounding error is at
+// most 2^-24 * 128 = 8e-6.
+constexpr float kLayeredRebuild = 64.0f;
+
 template <int DC, int T>
-__global__ void __launch_bounds__(T) layered_kernel(const DecodeArgs a, const LayeredLayout lay) {
+__global__ void __launch_bounds__(T, T == 32 ? 32 : (T == 64 ? 12 : 6)) layered_kernel(const DecodeArgs a, const LayeredLayout lay) {
     constexpr int R = LayeredRec<DC>::R;
     static_assert(DC <= 24 && T % 32 == 0, "layout");
     extern __shared__ __align__(16) unsigned char smem[];
@@ -104,6 +109,7 @@ __global__ void __launch_bounds__(T) layered_kernel(const DecodeArgs a, const La
     // message is zero (v = P) and the check state is written without being read.
     auto sweep = [&](auto fresh, float g0) {
         constexpr bool FRESH = decltype(fresh)::value;
+        float pmax = 0.0f;   // largest |posterior| written this round
         for (int l = 0; l < lay.L; ++l) {
             const int p1 = __ldg(lay.lay_ptr + l + 1);
             for (int p = __ldg(lay.lay_ptr + l) + t; p < p1; p += T) {
@@ -145,7 +151,9 @@ __global__ void __launch_bounds__(T) layered_kernel(const DecodeArgs a, const La
                 for (int j = 0; j < DC; ++j) {
                     const uint32_t sg = (par ^ __float_as_uint(v[j])) & kSign;
                     const bool eq = fabsf(v[j]) == m1;
-                    Pat(off[j]) = v[j] + __uint_as_float(__float_as_uint(eq ? o2 : o1) | sg);
+                    const float pn = v[j] + __uint_as_float(__float_as_uint(eq ? o2 : o1) | sg);
+                    Pat(off[j]) = pn;
+                    pmax = fmaxf(pmax, fabsf(pn));
                     nm |= sg >> (31 - j);
                     eqm |= (uint32_t)eq << j;
                 }
@@ -155,12 +163,13 @@ __global__ void __launch_bounds__(T) layered_kernel(const DecodeArgs a, const La
             }
             sync();
         }
+        return pmax;
     };
 
     // Posteriors rebuilt from the current messages, P_c = L0_c + sum over the qubit's edges in
-    // a fixed order (Eq. 2): run after every round but the first, so that a posterior's
-    // rounding error depends on the messages of that round only, not on every value it took
-    // while updated in place (round 1 starts from zero messages and needs no rebuild).
+    // a fixed order (Eq. 2), after a round (not the first, which starts from zero messages) in
+    // which a posterior grew large: a posterior's rounding error then depends on the messages
+    // of that round only, not on every large value it took while updated in place.
     auto rebuild = [&](float prior_c) {
         for (int c = t; c < n; c += T) {
             float acc = per_qubit ? PQ[c] : prior_c;
@@ -250,13 +259,18 @@ __global__ void __launch_bounds__(T) layered_kernel(const DecodeArgs a, const La
             // A2: the round's gain (Eq. 7), boosted on unsatisfied checks
             const float g0 = (a.mode == kModeSAGMS) ? amax - (amax - a.amin) * ((float)cnt * a.inv_m)
                                                     : ((a.mode == kModeSMS) ? a.alpha : 1.0f);
-            // A3 + A4, layer by layer
+            // A3 + A4, layer by layer; then the rebuild when the round had a large posterior
             if (it == 0) {
                 sweep(std::true_type{}, g0);
             } else {
-                sweep(std::false_type{}, g0);
-                rebuild(prior);
-                sync();
+                const float pmax = sweep(std::false_type{}, g0);
+                bool big = per_qubit || pmax > kLayeredRebuild;
+                if constexpr (T == 32) big = __any_sync(0xffffffffu, big);
+                else big = __syncthreads_or(big);
+                if (big) {
+                    rebuild(prior);
+                    sync();
+                }
             }
         }
 
