@@ -12,20 +12,24 @@
 // Checks of one layer touch disjoint qubits, so one thread per check updates P in place.
 // The gains of a round come from the residual syndrome at its start (Eqs. 1, 6, 7).
 //
-// One CTA of T threads (32, 64 or 128) decodes one shot at a time (static stride over shots).  Shared
-// memory holds, per shot:
+// One CTA of T threads (32, 64 or 128) decodes one shot at a time (static stride over
+// shots).  Shared memory holds, per shot:
 //   P[Np]          posteriors (column n and up: +inf, the target of padded check slots)
 //   PQ[Np]         per-qubit priors (SAGMS_FLAG_L0_PER_QUBIT only)
 //   O1[Mp], O2[Mp] magnitudes min(g*min1, clip), min(g*min2, clip) of each check's last output
 //   meta[Mp]       bit j: sign of the output on slot j; bits 24..28: slot of the first minimum
 //   sbits, rbits   input syndrome (check order) and residual bits (layer order)
-// A check's outputs take two magnitudes only, so (O1, O2, meta) rebuilds every old message
+// A check's outputs take two magnitudes only, so (O1, O2, meta) reproduces every old message
 // exactly: slot j carries O2 if it holds the first minimum, else O1 (two slots tying at the
 // minimum have O1 == O2).  P sits at the start of shared memory, so a record's byte offsets
-// address it directly.  A shot's first round reads no old message (all are zero), so it
-// runs a copy of the loop without the rebuild, and with one prior per shot the residual before
-// it has a closed form.  The check records (columns, check index and degree, layer order) stay
-// in global memory, read through the read-only cache.
+// address it directly.  A shot's first round reads no old message (all are zero), so it runs
+// a copy of the loop without that step, and with one prior per shot the residual before it
+// has a closed form.  After a later round in which a posterior exceeded 64 (normalised
+// units; every round with per-qubit priors) the posteriors are summed afresh from the
+// messages, through qubit-to-edge lists: in-place updates alone would keep the rounding error
+// of every large value a posterior ever held.  The check records (columns, check index and
+// degree, layer order) and the qubit-to-edge lists stay in global memory, read through the
+// read-only cache.
 #pragma once
 
 #include <type_traits>
@@ -105,8 +109,9 @@ __global__ void __launch_bounds__(T, T == 32 ? 32 : (T == 64 ? 12 : 6)) layered_
         deg = (int)(h >> 16);
         return (int)(h & 0xffffu);
     };
-    // One round over the layers (A3 + A4).  FRESH: the shot's first round, where every old
-    // message is zero (v = P) and the check state is written without being read.
+    // One round over the layers (A3 + A4); returns the largest |posterior| it wrote.  FRESH:
+    // the shot's first round, where every old message is zero (v = P) and the check state is
+    // written without being read.
     auto sweep = [&](auto fresh, float g0) {
         constexpr bool FRESH = decltype(fresh)::value;
         float pmax = 0.0f;   // largest |posterior| written this round
