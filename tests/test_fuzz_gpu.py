@@ -91,3 +91,37 @@ def test_random_code_all_kernels_and_oracle(seed):
     if p.mode != "bp" and code.row_ptr.size and np.diff(code.row_ptr).max() <= 24:
         lay = S.Params(**{**p.__dict__, "flags": p.flags | S.FLAG_LAYERED})
         G.compare(code, dc, syn[:k], L0 if p.flags & S.FLAG_L0_PER_QUBIT else L0[:k], lay)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_random_codes_in_one_multi_code_launch(seed):
+    """Four random cases (different codes, modes and flags) in one sagms_decode_multi call:
+    each job's outputs equal the separate decode of the same batch, bit for bit."""
+    cases = [_random_case(100 + 4 * seed + k) for k in range(4)]
+    jobs, refs = [], []
+    for code, p, syn, L0 in cases:
+        dc = S.DeviceCode.from_code(code)
+        refs.append(G.gpu_decode(dc, syn, L0, p))
+        d_syn = torch.from_numpy(np.ascontiguousarray(syn).view(np.int32)).cuda()
+        d_L0 = torch.from_numpy(np.ascontiguousarray(L0, dtype=np.float32)).cuda()
+        jobs.append(S.Job(dc, d_syn, d_L0, p))
+    S.decode_multi(jobs)
+    torch.cuda.synchronize()
+    for j, ref in zip(jobs, refs):
+        got = {"err": j.err.cpu().numpy().view(np.uint32), "conv": j.conv.cpu().numpy(), "iters": j.iters.cpu().numpy()}
+        assert _same(got, ref)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_sampler_on_random_codes(seed):
+    """The on-device Monte Carlo sampler on random irregular codes (qubits of degree 1 to 8,
+    empty checks, qubits in no check): frames and syndromes bit-exact with the input
+    generator from an arbitrary frame offset."""
+    code, _, _, _ = _random_case(200 + seed)
+    dc = S.DeviceCode.from_code(code)
+    q = float(np.random.default_rng(seed).uniform(0.001, 0.2))
+    shot0 = 1000 * seed + 7
+    err, syn, _ = S.mc_sample(dc, 11 + seed, q, shot0, 777)
+    e_ref, s_ref = I.sample(code, q, 777, seed=11 + seed, shot0=shot0)
+    assert np.array_equal(err.cpu().numpy().view(np.uint32), e_ref)
+    assert np.array_equal(syn.cpu().numpy().view(np.uint32), s_ref)
