@@ -64,7 +64,7 @@ def _load():
                                       ctypes.c_double, ctypes.c_int, ctypes.c_uint, ctypes.c_int64,
                                       P(ctypes.c_uint32), P(ctypes.c_double), P(ctypes.c_uint32),
                                       P(ctypes.c_uint8), P(ctypes.c_int32), P(ctypes.c_double),
-                                      P(ctypes.c_double)]
+                                      P(ctypes.c_double), P(ctypes.c_int64)]
         lib.oracle_decode.restype = ctypes.c_int
         lib.oracle_alpha_star.argtypes = [ctypes.c_double, ctypes.c_int]
         lib.oracle_alpha_star.restype = ctypes.c_double
@@ -83,7 +83,8 @@ def decode(m, n, row_ptr, col_idx, syn, L0, mode=SAGMS, alpha=0.75, alpha_min=0.
     """Decode packed syndromes ``syn`` [shots][ceil(m/32)].
 
     ``L0``: [shots] per-shot prior, or [n] with FLAG_L0_PER_QUBIT.  Returns a dict with
-    ``err`` [shots][ceil(n/32)] uint32, ``conv`` [shots] uint8, ``iters`` [shots] int32 and,
+    ``err`` [shots][ceil(n/32)] uint32, ``conv`` [shots] uint8, ``iters`` [shots] int32,
+    ``clips`` [shots] int64 (check-node outputs the clip bound) and,
     with ``trace=True``, ``trace`` [shots][max_iter+1][n] float64 posteriors (units the
     decoder runs in: L0-normalised for the MS family with a per-shot prior) and ``scale``
     (same shape): |L0_j| + sum of |messages| into qubit j, the size of P_j's terms."""
@@ -102,6 +103,7 @@ def decode(m, n, row_ptr, col_idx, syn, L0, mode=SAGMS, alpha=0.75, alpha_min=0.
     err = np.zeros((shots, nw), dtype=np.uint32)
     conv = np.zeros(shots, dtype=np.uint8)
     iters = np.zeros(shots, dtype=np.int32)
+    clips = np.zeros(shots, dtype=np.int64)
     tr = np.zeros((shots, max_iter + 1, n), dtype=np.float64) if trace else None
     sc = np.zeros((shots, max_iter + 1, n), dtype=np.float64) if trace else None
 
@@ -114,7 +116,8 @@ def decode(m, n, row_ptr, col_idx, syn, L0, mode=SAGMS, alpha=0.75, alpha_min=0.
                                _p(syn[lo:hi], ctypes.c_uint32), _p(np.ascontiguousarray(Ls), ctypes.c_double),
                                _p(err[lo:hi], ctypes.c_uint32), _p(conv[lo:hi], ctypes.c_uint8),
                                _p(iters[lo:hi], ctypes.c_int32), _p(tr[lo:hi] if tr is not None else None, ctypes.c_double),
-                               _p(sc[lo:hi] if sc is not None else None, ctypes.c_double))
+                               _p(sc[lo:hi] if sc is not None else None, ctypes.c_double),
+                               _p(clips[lo:hi], ctypes.c_int64))
         if rc != 0:
             raise RuntimeError("oracle_decode: bad arguments")
 
@@ -125,7 +128,7 @@ def decode(m, n, row_ptr, col_idx, syn, L0, mode=SAGMS, alpha=0.75, alpha_min=0.
         bounds = np.linspace(0, shots, threads + 1).astype(int)
         with ThreadPoolExecutor(threads) as ex:
             list(ex.map(lambda k: run(bounds[k], bounds[k + 1]), range(threads)))
-    out = {"err": err, "conv": conv, "iters": iters}
+    out = {"err": err, "conv": conv, "iters": iters, "clips": clips}
     if tr is not None:
         out["trace"] = tr
         out["scale"] = sc

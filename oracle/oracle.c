@@ -109,7 +109,8 @@ static double pert_sign(uint64_t item, uint64_t round) {
 
 /* (iv) for one check i: every outgoing message r(i,j) from the incoming q over M(i)\j,
  * leave-one-out written out directly (Eqs. 3, 4, 8). */
-static void cn_update(int i, const int32_t* row_ptr, int s_i, int msfam, double g, const double* q, double* r) {
+static void cn_update(int i, const int32_t* row_ptr, int s_i, int msfam, double g, const double* q, double* r,
+                      int64_t* nclip) {
     for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
         int neg = s_i;
         double mn = INFINITY, prod = 1.0;
@@ -123,10 +124,10 @@ static void cn_update(int i, const int32_t* row_ptr, int s_i, int msfam, double 
         double mag;
         if (msfam) {
             mag = g * mn;
-            if (mag > MSFAM_CLIP) mag = MSFAM_CLIP;
+            if (mag > MSFAM_CLIP) { mag = MSFAM_CLIP; ++*nclip; }
         } else {
             mag = (prod >= 1.0) ? INFINITY : 2.0 * atanh(prod);
-            if (mag > BP_CLIP) mag = BP_CLIP;
+            if (mag > BP_CLIP) { mag = BP_CLIP; ++*nclip; }
         }
         r[e] = neg ? -mag : mag;
     }
@@ -144,13 +145,14 @@ static void cn_update(int i, const int32_t* row_ptr, int s_i, int msfam, double 
  *   scale: optional, same layout: |L0_j| + sum_{i in N(j)} |r(i,j)| at each check (i), the
  *          magnitude of the terms of P_j's sum, which bounds the rounding error a
  *          lower-precision evaluation of P_j carries (test acceptance; not part of the method).
+ *   clips: optional [shots] (out): CN outputs of the shot that the clip bound.
  * Returns 0, or -1 on bad arguments / allocation failure.
  */
 int oracle_decode(int m, int n, const int32_t* row_ptr, const int32_t* col_idx,
                   int mode, double alpha, double alpha_min, double alpha_max, double eta_unsat,
                   int max_iter, unsigned flags, int64_t shots,
                   const uint32_t* syn, const double* L0,
-                  uint32_t* err, uint8_t* conv, int32_t* iters, double* trace, double* scale) {
+                  uint32_t* err, uint8_t* conv, int32_t* iters, double* trace, double* scale, int64_t* clips) {
     if (m < 0 || n <= 0 || max_iter < 0 || shots < 0 || !row_ptr || !col_idx || !syn || !L0 ||
         !err || !conv || !iters || mode < 0 || mode > 3)
         return -1;
@@ -230,6 +232,7 @@ int oracle_decode(int m, int n, const int32_t* row_ptr, const int32_t* col_idx,
         uint32_t* eo = err + (size_t)s * nw;
         double* tr = trace ? trace + (size_t)s * (size_t)(max_iter + 1) * (size_t)n : NULL;
         double* sc = scale ? scale + (size_t)s * (size_t)(max_iter + 1) * (size_t)n : NULL;
+        int64_t nclip = 0;
 
         /* A non-finite prior marks the shot invalid: e_hat = 0, conv = 0, iters = -1. */
         int bad = 0;
@@ -303,7 +306,7 @@ int oracle_decode(int m, int n, const int32_t* row_ptr, const int32_t* col_idx,
 
             if (!layered) {
                 /* (iv) CN update of every check (Eqs. 3, 4, 8) */
-                for (int i = 0; i < m; ++i) cn_update(i, row_ptr, bit_of(sy, i), msfam, gain[i], q, r);
+                for (int i = 0; i < m; ++i) cn_update(i, row_ptr, bit_of(sy, i), msfam, gain[i], q, r, &nclip);
                 /* (v) VN update, leave-one-out over N(j)\i (Eq. 2) */
                 for (int j = 0; j < n; ++j) {
                     for (int t = vn_ptr[j]; t < vn_ptr[j + 1]; ++t) {
@@ -334,7 +337,7 @@ int oracle_decode(int m, int n, const int32_t* row_ptr, const int32_t* col_idx,
                         if (pert != 0.0) acc += pert * pert_sign((uint64_t)e, (uint64_t)l) * mag;
                         q[e] = acc;
                     }
-                    cn_update(i, row_ptr, bit_of(sy, i), msfam, gain[i], q, r);
+                    cn_update(i, row_ptr, bit_of(sy, i), msfam, gain[i], q, r, &nclip);
                 }
             }
             ++l;
@@ -342,6 +345,7 @@ int oracle_decode(int m, int n, const int32_t* row_ptr, const int32_t* col_idx,
         for (int k = 0; k < nw; ++k) eo[k] = 0u;
         for (int j = 0; j < n; ++j)
             if (ehat[j]) eo[j >> 5] |= 1u << (j & 31);
+        if (clips) clips[s] = nclip;
     }
 
 done:

@@ -307,3 +307,21 @@ def test_scale_trace_bounds_the_posterior(layered):
                            flags=oracle.FLAG_NO_EARLY_STOP | (oracle.FLAG_LAYERED if layered else 0))
     assert (r["scale"] >= np.abs(r["trace"]) - 1e-12).all()
     np.testing.assert_array_equal(r["scale"][:, 0, :], np.abs(r["trace"][:, 0, :]))
+
+
+@pytest.mark.parametrize("lw,q,max_iter", [((63, 3), 0.05, 50), ((127, 4), 0.04 * 2 / 3, 100), ((255, 5), 0.02, 100)])
+def test_clip_frequency_on_the_configs(lw, q, max_iter):
+    """Readings 8 and 9 (the paper is silent on message overflow): the MS-family clip (1e6 in
+    L0 units) never binds on a converging shot of these workloads, and here on none at all;
+    the BP clip (ln 2e10) binds on some converging shots (strong priors saturate the rule).
+    Both frequencies are reported."""
+    c = I.gb_code(*lw)
+    _, syn, L0, _ = I.workload(c, [q], 1500, seed=7)
+    for mode in (oracle.MS, oracle.SMS, oracle.SAGMS, oracle.BP):
+        r = oracle.decode_code(c, syn, L0.astype(np.float64), mode=mode, max_iter=max_iter, threads=4)
+        conv = r["conv"] == 1
+        fired = r["clips"] > 0
+        print(f"GB{lw} mode {mode}: clip binds on {int(fired[conv].sum())}/{int(conv.sum())} converging and "
+              f"{int(fired[~conv].sum())}/{int((~conv).sum())} failing shots")
+        if mode != oracle.BP:
+            assert not fired.any()
