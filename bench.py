@@ -427,6 +427,28 @@ def main():
            "roofline_smem": None if args.layered else roof_smem,
            "clocks": clk, "input_gen_s": gen_s}
 
+    # e2e: the C-ABI host entry point, host<->device copies inside the timed region
+    h_syn = torch.from_numpy(syn.view(np.int32)).pin_memory()
+    h_L0 = torch.from_numpy(L0).pin_memory()
+    h_err = torch.empty((shots, code.nw), dtype=torch.int32).pin_memory()
+    h_conv = torch.empty((shots,), dtype=torch.uint8).pin_memory()
+    h_it = torch.empty((shots,), dtype=torch.int32).pin_memory()
+    S.decode_host(dcode, h_syn, h_L0, sagms, out=(h_err, h_conv, h_it))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        S.decode_host(dcode, h_syn, h_L0, sagms, out=(h_err, h_conv, h_it))
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    assert np.array_equal(h_it.numpy(), it_host), "host path disagrees with the device path"
+    out["e2e"] = {"value": shots * world * args.e2e_steps / e2e_s, "unit": UNIT,
+                  "h2d_bytes_per_step": int(syn.nbytes + L0.nbytes),
+                  "d2h_bytes_per_step": int(shots * code.nw * 4 + shots + shots * 4),
+                  "api": "sagms_decode_host (pinned host buffers, chunked copy/compute overlap)"}
+
     if not args.no_extras:
         modes = {}
         for name, p in (("sms", S.Params(mode="sms", alpha=SMS_ALPHA, max_iter=MAX_ITER)),
@@ -472,28 +494,6 @@ def main():
             out["config3_mixed_degree"] = bench_mixed_degree(S, I, args.mode_steps)
             out["serving"] = bench_serving(S, I)
             out["monte_carlo"] = bench_mc(S, I)
-
-    # e2e: the C-ABI host entry point, host<->device copies inside the timed region
-    h_syn = torch.from_numpy(syn.view(np.int32)).pin_memory()
-    h_L0 = torch.from_numpy(L0).pin_memory()
-    h_err = torch.empty((shots, code.nw), dtype=torch.int32).pin_memory()
-    h_conv = torch.empty((shots,), dtype=torch.uint8).pin_memory()
-    h_it = torch.empty((shots,), dtype=torch.int32).pin_memory()
-    S.decode_host(dcode, h_syn, h_L0, sagms, out=(h_err, h_conv, h_it))
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        S.decode_host(dcode, h_syn, h_L0, sagms, out=(h_err, h_conv, h_it))
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    assert np.array_equal(h_it.numpy(), it_host), "host path disagrees with the device path"
-    out["e2e"] = {"value": shots * world * args.e2e_steps / e2e_s, "unit": UNIT,
-                  "h2d_bytes_per_step": int(syn.nbytes + L0.nbytes),
-                  "d2h_bytes_per_step": int(shots * code.nw * 4 + shots + shots * 4),
-                  "api": "sagms_decode_host (pinned host buffers, chunked copy/compute overlap)"}
 
     if rank == 0 and world == 1 and not args.no_extras:
         threads = os.cpu_count() or 1
