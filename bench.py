@@ -310,6 +310,8 @@ def main():
                     help="skip the SMS / MS / BP / layered lines, the other configs and the CPU baseline")
     ap.add_argument("--layered", action="store_true",
                     help="time the layered schedule (SAGMS_FLAG_LAYERED) instead of Algorithm 1's flooding one")
+    ap.add_argument("--mode", default="sagms", choices=["sagms", "sms", "ms", "bp"],
+                    help="decoder timed (default SAGMS, the headline; the others for profiling)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -346,7 +348,8 @@ def main():
     conv = torch.empty((shots,), dtype=torch.uint8, device="cuda")
     iters = torch.empty((shots,), dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
-    sagms = S.Params(mode="sagms", max_iter=MAX_ITER, flags=S.FLAG_LAYERED if args.layered else 0, **SAGMS_KW)
+    sagms = S.Params(mode=args.mode, alpha=SMS_ALPHA, max_iter=MAX_ITER, flags=S.FLAG_LAYERED if args.layered else 0,
+                     **SAGMS_KW)
 
     def step(p):
         S.decode(dcode, d_syn, d_L0, p, out=(err, conv, iters), stream=stream)
@@ -387,14 +390,15 @@ def main():
     props = torch.cuda.get_device_properties(local)
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0)
-    ops_it = roofline.ops_per_iteration("sagms", code.row_ptr, code.col_idx, code.n)
+    ops_it = roofline.ops_per_iteration(args.mode, code.row_ptr, code.col_idx, code.n)
     ops_launch = float(it_host.astype(np.int64).sum()) * ops_it
     achieved = ops_launch / (ms_step / 1e3)
     peak = roofline.alu_peak_ops(props.multi_processor_count, sm_max)
-    traffic = None if args.layered else profile_traffic(shots)
+    traffic = None if (args.layered or args.mode != "sagms") else profile_traffic(shots)
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
             "frac": achieved / peak, "traffic": traffic,
-            "kernel": "sagms::layered_kernel<10,64>" if args.layered else "sagms::qc_kernel<10,5,4>",
+            "kernel": ("sagms::layered_kernel<10,64>" if args.layered else
+                       "sagms::decode_kernel<10,5,BP>" if args.mode == "bp" else "sagms::qc_kernel<10,5,4>"),
             "note": (f"ops = sum over shots of iters x {ops_it} per iteration (Eq. 15 / Table I CN cost + VN sum, "
                      f"decision, residual XOR, popcount); peak = {props.multi_processor_count} SMs x 128 lanes x "
                      f"{sm_max:.0f} MHz (derived from unit counts and clock); HBM bound "
@@ -418,7 +422,8 @@ def main():
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": workload_name(shots) + (", layered schedule" if args.layered else ""),
+           "config": {"workload": workload_name(shots) + (", layered schedule" if args.layered else "")
+                      + ("" if args.mode == "sagms" else f", decoder {args.mode} instead of SAGMS"),
                       "global_batch": shots * world, "code_seed": code.seed,
                       "a": list(code.a), "b": list(code.b), "k": code.k,
                       "l2": f"inputs larger than L2: {syn.nbytes / 1e9:.2f} GB syndromes per GPU",
