@@ -163,6 +163,16 @@ int sagms_column_slots(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr
 int sagms_check_layers(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr,
                        const int32_t* col_idx, int32_t* layer, int32_t* num_layers);
 
+/*
+ * The BP rule's phi(x) = -ln tanh(x/2) (Eq. 3) as the decoder evaluates it, for tests of
+ * its accuracy: d_y[i] = phi(d_x[i]) for 0 <= d_x[i] <= +inf.  form 0: the decoder's
+ * evaluation (two series, one expf or logf each); form 1: the library composition
+ * log1pf(2 / expm1f(x)), the reference it is checked against.
+ *   d_x, d_y  [n] device.
+ * Asynchronous on `stream`.  Errors: ERR_ARG (NULL pointers, n < 0, unknown form), ERR_CUDA.
+ */
+int sagms_phi(const float* d_x, float* d_y, int64_t n, int32_t form, void* stream);
+
 /* Validate a parameter block without decoding.  Returns SAGMS_OK or SAGMS_ERR_PARAM /
  * SAGMS_ERR_ARG.  Runs on the host only (no CUDA call). */
 int sagms_check_params(const sagms_params* params);

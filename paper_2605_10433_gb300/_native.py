@@ -62,6 +62,7 @@ def _load_library():
         "sagms_free_code": (None, [vp]),
         "sagms_code_info": (ctypes.c_int, [vp, P(i32), P(i32), P(i32), P(i32)]),
         "sagms_code_kernels": (ctypes.c_int, [vp, P(ctypes.c_uint32)]),
+        "sagms_phi": (ctypes.c_int, [vp, vp, i64, i32, vp]),
         "sagms_check_layers": (ctypes.c_int, [i32, i32, i64, P(i32), P(i32), P(i32), P(i32)]),
         "sagms_column_slots": (ctypes.c_int, [i32, i32, i64, P(i32), P(i32), i32, P(i32)]),
         "sagms_check_params": (ctypes.c_int, [P(sagms_params)]),
@@ -144,6 +145,16 @@ def sagms_code_kernels(handle):
     v = ctypes.c_uint32()
     _check(_lib.sagms_code_kernels(handle, ctypes.byref(v)))
     return v.value
+
+
+def sagms_phi(x, form=0, stream=None):
+    """phi(x) = -ln tanh(x/2) on the GPU for a float32 CUDA tensor x (form 0: the decoder's
+    evaluation, form 1: log1pf(2 / expm1f(x)))."""
+    import torch
+    y = torch.empty_like(x)
+    _check(_lib.sagms_phi(x.data_ptr(), y.data_ptr(), int(x.numel()), int(form),
+                          stream.cuda_stream if stream is not None else None))
+    return y
 
 
 def sagms_check_layers(m, n, row_ptr, col_idx):

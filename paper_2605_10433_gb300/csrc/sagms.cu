@@ -461,6 +461,27 @@ int sagms_check_params(const sagms_params* p) {
     }
 }
 
+}  // extern "C"
+
+namespace {
+__global__ void phi_kernel(const float* __restrict__ x, float* __restrict__ y, long long n, int form) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = form ? phi_ref(x[i]) : phi_fn(x[i]);
+}
+}  // namespace
+
+extern "C" {
+
+int sagms_phi(const float* d_x, float* d_y, int64_t n, int32_t form, void* stream) {
+    if (n < 0 || (n > 0 && (!d_x || !d_y))) return fail(SAGMS_ERR_ARG, "bad phi arguments");
+    if (form != 0 && form != 1) return fail(SAGMS_ERR_ARG, "unknown phi form %d", form);
+    if (n == 0) return SAGMS_OK;
+    const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+    phi_kernel<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(d_x, d_y, n, form);
+    const cudaError_t ce = cudaGetLastError();
+    return ce == cudaSuccess ? SAGMS_OK : cuda_fail(ce, "phi launch");
+}
+
 int sagms_check_layers(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
                        int32_t* layer, int32_t* num_layers) {
     if (!layer) return fail(SAGMS_ERR_ARG, "layer is NULL");
