@@ -94,8 +94,9 @@ typedef struct sagms_code sagms_code; /* opaque, library-owned */
  *   mode:       SAGMS_MS / SAGMS_SMS / SAGMS_SAGMS / SAGMS_BP.
  *   alpha:      SMS scale, 0 < alpha <= 1 (Eq. 4 and the SMS rule of Sec. II).
  *   alpha_min, alpha_max, eta_unsat: SAGMS gain of Eq. 7, with
- *               0 < alpha_min <= alpha_max <= 1, eta_unsat >= 1 and
+ *               2^-20 <= alpha_min <= alpha_max <= 1, eta_unsat >= 1 and
  *               alpha_max * eta_unsat <= 1 (the stability constraint of Sec. III-A).
+ *               The lower bound on alpha_min keeps the FP32 gain positive.
  *               eta_unsat = 0 selects the default 1.10 used in the paper's experiments.
  *   max_iter:   message-passing rounds, 0 <= max_iter <= 100000 (l_max of Algorithm 1).
  *   flags:      SAGMS_FLAG_* bits.

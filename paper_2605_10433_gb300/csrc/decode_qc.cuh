@@ -26,8 +26,9 @@
 // round stores one closed-form value per check instead of running the check-node minimum
 // search.
 //
-// The arithmetic of every check and qubit is, operation for operation, that of
-// decode_kernel.cuh: results are bitwise identical to the other kernels.
+// The arithmetic of every check and qubit is that of decode_kernel.cuh, operation for
+// operation, except the MS-family check-node output of shapes up to DC = 10, which takes an
+// exactly equivalent form (see there): results are bitwise identical to the other kernels.
 #pragma once
 
 #include "decode_groups.cuh"
@@ -348,6 +349,37 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
                                 const float mag = fminf(phi_fn(Sj), kBpClip);
                                 const uint32_t vb = __float_as_uint(h ? v[p][j].y : v[p][j].x);
                                 Cat(j, off[2 * p + h][j]) = __uint_as_float(__float_as_uint(mag) | (~(par ^ vb) & kSign));
+                            }
+                        }
+                    } else if constexpr (DC <= 10 && !(PQ && T == 128)) {
+                        // Eqs. 4 and 8: edge j receives min(g * min_{i != j} |v_i|, clip) with
+                        // the parity of the other edges.  The gain is positive (host-checked),
+                        // so fl(g x) is monotone in x and the minimum may be taken after the
+                        // scaling: min_{i != j} fl(g |v_i|).  The parity bit rides on the gain,
+                        // making every scaled value of the check the same sign, and floats of
+                        // one sign order like their bit patterns as unsigned integers.  So
+                        // each edge's output is an unsigned minimum over the others, from a
+                        // suffix pass (seeded with the clip) and a running prefix: the same
+                        // bits as the smallest / second-smallest selection below, with no
+                        // compare and select per edge.  (Shapes where the suffix values do not
+                        // fit the register budget keep the selection.)
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const uint32_t par = h ? par1 : par0;
+                            const float gs = __uint_as_float(__float_as_uint(g[2 * p + h]) | par);
+                            uint32_t x[DC], suf[DC];
+#pragma unroll
+                            for (int j = 0; j < DC; ++j) x[j] = __float_as_uint(gs * fabsf(h ? v[p][j].y : v[p][j].x));
+                            suf[DC - 1] = __float_as_uint(kMsFamClip) | par;
+#pragma unroll
+                            for (int j = DC - 2; j >= 0; --j) suf[j] = min(suf[j + 1], x[j + 1]);
+                            uint32_t pre = x[0];
+#pragma unroll
+                            for (int j = 0; j < DC; ++j) {
+                                const uint32_t o = (j == 0) ? suf[0] : min(pre, suf[j]);
+                                if (j > 0) pre = min(pre, x[j]);
+                                const uint32_t vb = __float_as_uint(h ? v[p][j].y : v[p][j].x);
+                                Cat(j, off[2 * p + h][j]) = __uint_as_float(o ^ (~vb & kSign));
                             }
                         }
                     } else {

@@ -411,6 +411,12 @@ double sagms_alpha_star(double L0, int32_t dc) {
     return 2.0 * std::atanh(std::pow(std::tanh(0.5 * L0), (double)(dc - 1))) / L0;
 }
 
+// Smallest alpha_min accepted.  Eq. 7's gain is at least alpha_min > 0 in exact arithmetic; in
+// FP32 the term (alpha_max - alpha_min) * |s~|_0 / m can round above alpha_max - alpha_min by
+// about 2^-22 alpha_max, so alpha_min >= 2^-20 (alpha_max <= 1) keeps every computed gain
+// positive, which the kernels' check-node arithmetic relies on.
+constexpr float kMinAlphaMin = 0x1p-20f;
+
 int sagms_check_params(const sagms_params* p) {
     if (!p) return fail(SAGMS_ERR_ARG, "params is NULL");
     if (p->flags & ~(uint32_t)(SAGMS_FLAG_L0_PER_QUBIT | SAGMS_FLAG_NO_EARLY_STOP | SAGMS_FLAG_GENERIC_KERNEL |
@@ -437,8 +443,8 @@ int sagms_check_params(const sagms_params* p) {
             const float eta = (p->eta_unsat == 0.0f) ? 1.10f : p->eta_unsat;
             if (auto_ceiling) {
                 // alpha_max comes from each shot's prior, clamped to [alpha_min, 1/eta]
-                if (!(p->alpha_min > 0.0f && p->alpha_min <= 1.0f))
-                    return fail(SAGMS_ERR_PARAM, "need 0 < alpha_min <= 1 (got %g)", (double)p->alpha_min);
+                if (!(p->alpha_min >= kMinAlphaMin && p->alpha_min <= 1.0f))
+                    return fail(SAGMS_ERR_PARAM, "need 2^-20 <= alpha_min <= 1 (got %g)", (double)p->alpha_min);
                 if (!(eta >= 1.0f) || !std::isfinite(eta))
                     return fail(SAGMS_ERR_PARAM, "eta_unsat %g must be >= 1", (double)eta);
                 if ((double)p->alpha_min * (double)eta > 1.0 + 1e-6)
@@ -446,8 +452,8 @@ int sagms_check_params(const sagms_params* p) {
                                 (double)p->alpha_min * (double)eta);
                 return SAGMS_OK;
             }
-            if (!(p->alpha_min > 0.0f && p->alpha_min <= p->alpha_max && p->alpha_max <= 1.0f))
-                return fail(SAGMS_ERR_PARAM, "need 0 < alpha_min <= alpha_max <= 1 (got %g, %g)",
+            if (!(p->alpha_min >= kMinAlphaMin && p->alpha_min <= p->alpha_max && p->alpha_max <= 1.0f))
+                return fail(SAGMS_ERR_PARAM, "need 2^-20 <= alpha_min <= alpha_max <= 1 (got %g, %g)",
                             (double)p->alpha_min, (double)p->alpha_max);
             if (!(eta >= 1.0f) || !std::isfinite(eta))
                 return fail(SAGMS_ERR_PARAM, "eta_unsat %g must be >= 1", (double)eta);

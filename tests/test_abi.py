@@ -50,6 +50,9 @@ def test_version_and_alpha_star(native):
     (dict(mode=2, alpha_min=0.3, alpha_max=0.95, eta_unsat=1.1, max_iter=100), False),  # a_max eta > 1
     (dict(mode=2, alpha_min=0.6, alpha_max=0.5, eta_unsat=1.1, max_iter=100), False),   # a_min > a_max
     (dict(mode=2, alpha_min=0.0, alpha_max=0.5, eta_unsat=1.1, max_iter=100), False),
+    (dict(mode=2, alpha_min=2.0 ** -20, alpha_max=0.5, eta_unsat=1.1, max_iter=100), True),
+    (dict(mode=2, alpha_min=2.0 ** -21, alpha_max=0.5, eta_unsat=1.1, max_iter=100), False),  # gain may round to 0
+    (dict(mode=2, alpha_min=1e-7, max_iter=100, flags=16), False),                            # same, auto ceiling
     (dict(mode=2, alpha_min=0.3, alpha_max=0.5, eta_unsat=0.9, max_iter=100), False),   # eta < 1
     (dict(mode=1, alpha=0.75, max_iter=100), True),
     (dict(mode=1, alpha=0.0, max_iter=100), False),
