@@ -107,10 +107,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
+def kernel_code(text):
+    """Source text without comments and blank lines: what decides the compiled kernel."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = (re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines())
+    return "\n".join(ln for ln in lines if ln.strip())
+
+
 def kernel_sha():
     h = hashlib.sha256()
     for f in KERNEL_SRC:
-        h.update(open(f, "rb").read())
+        h.update(kernel_code(open(f).read()).encode())
     return h.hexdigest()[:16]
 
 
