@@ -358,28 +358,35 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
                         // scaling: min_{i != j} fl(g |v_i|).  The parity bit rides on the gain,
                         // making every scaled value of the check the same sign, and floats of
                         // one sign order like their bit patterns as unsigned integers.  So
-                        // each edge's output is an unsigned minimum over the others, from a
-                        // suffix pass (seeded with the clip) and a running prefix: the same
+                        // each edge's output is an unsigned minimum over the others: over its
+                        // slot pair's partner, the pairs before it (running prefix) and the
+                        // pairs after it (suffix, seeded with the clip).  These are the same
                         // bits as the smallest / second-smallest selection below, with no
-                        // compare and select per edge.  (Shapes where the suffix values do not
-                        // fit the register budget keep the selection.)
+                        // compare and select per edge and a short dependency chain.  (Shapes
+                        // where the values do not fit the register budget keep the selection.)
+                        constexpr int NPR = DC / 2;
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             const uint32_t par = h ? par1 : par0;
                             const float gs = __uint_as_float(__float_as_uint(g[2 * p + h]) | par);
-                            uint32_t x[DC], suf[DC];
+                            uint32_t x[DC], pm[NPR], sp[NPR];
 #pragma unroll
                             for (int j = 0; j < DC; ++j) x[j] = __float_as_uint(gs * fabsf(h ? v[p][j].y : v[p][j].x));
-                            suf[DC - 1] = __float_as_uint(kMsFamClip) | par;
 #pragma unroll
-                            for (int j = DC - 2; j >= 0; --j) suf[j] = min(suf[j + 1], x[j + 1]);
-                            uint32_t pre = x[0];
+                            for (int i = 0; i < NPR; ++i) pm[i] = min(x[2 * i], x[2 * i + 1]);
+                            sp[NPR - 1] = __float_as_uint(kMsFamClip) | par;
 #pragma unroll
-                            for (int j = 0; j < DC; ++j) {
-                                const uint32_t o = (j == 0) ? suf[0] : min(pre, suf[j]);
-                                if (j > 0) pre = min(pre, x[j]);
-                                const uint32_t vb = __float_as_uint(h ? v[p][j].y : v[p][j].x);
-                                Cat(j, off[2 * p + h][j]) = __uint_as_float(o ^ (~vb & kSign));
+                            for (int i = NPR - 2; i >= 0; --i) sp[i] = min(sp[i + 1], pm[i + 1]);
+                            uint32_t pre = 0u;
+#pragma unroll
+                            for (int i = 0; i < NPR; ++i) {
+                                const uint32_t o0 = i ? __vimin3_u32(x[2 * i + 1], pre, sp[i]) : min(x[1], sp[0]);
+                                const uint32_t o1 = i ? __vimin3_u32(x[2 * i], pre, sp[i]) : min(x[0], sp[0]);
+                                pre = i ? min(pre, pm[i]) : pm[0];
+                                const uint32_t b0 = __float_as_uint(h ? v[p][2 * i].y : v[p][2 * i].x);
+                                const uint32_t b1 = __float_as_uint(h ? v[p][2 * i + 1].y : v[p][2 * i + 1].x);
+                                Cat(2 * i, off[2 * p + h][2 * i]) = __uint_as_float(o0 ^ (~b0 & kSign));
+                                Cat(2 * i + 1, off[2 * p + h][2 * i + 1]) = __uint_as_float(o1 ^ (~b1 & kSign));
                             }
                         }
                     } else {
