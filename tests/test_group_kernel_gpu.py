@@ -103,6 +103,48 @@ def test_group_kernel_bitwise_identical_to_other_kernels(group_codes, mode, key)
         assert np.array_equal(np.nan_to_num(tr, nan=7.0), np.nan_to_num(tg, nan=7.0)), kernel
 
 
+# Gains at the edges of what the parameter check accepts, and gain 1.
+EXTREME_GAINS = {
+    "sagms-floor": S.Params(mode="sagms", alpha_min=2.0 ** -20, alpha_max=0.9, eta_unsat=1.1, max_iter=40),
+    "sagms-auto-floor": S.Params(mode="sagms", alpha_min=2.0 ** -20, eta_unsat=1.1, max_iter=40,
+                                 flags=S.FLAG_AUTO_CEILING),
+    "sms-subnormal": S.Params(mode="sms", alpha=float(np.nextafter(np.float32(0), np.float32(1))), max_iter=40),
+    "sms-one": S.Params(mode="sms", alpha=1.0, max_iter=40),
+}
+
+
+@pytest.mark.parametrize("name", list(EXTREME_GAINS))
+@pytest.mark.parametrize("lw", [(63, 3), (255, 4), (1023, 5)])
+def test_check_node_output_at_gain_extremes(dev_check, lw, name):
+    """The column-indexed kernel forms each edge's check-node output as an unsigned minimum
+    over the other edges' sign-carrying scaled magnitudes, which needs a positive gain.  At
+    the smallest gains the parameter check accepts it must still agree bit for bit with the
+    one-shot-per-CTA kernel's smallest / second-smallest selection, posterior traces
+    included.  The cases:
+    - alpha_min = 2^-20, with every check unsatisfied in a third of the shots, which puts
+      Eq. 7's gain at its floor;
+    - the same with the automatic ceiling;
+    - SMS with the smallest subnormal scale, where most scaled values underflow to zero;
+    - gain 1."""
+    c = I.gb_code(*lw)
+    shots = 1500
+    _, syn, L0, _ = I.workload(c, [0.01, 0.05], shots, seed=31 * lw[0] + lw[1])
+    syn = syn.copy()
+    rng = np.random.default_rng(lw[0] + 17 * len(name))
+    k = shots // 3
+    syn[:k] = rng.integers(0, 2 ** 32, size=(k, syn.shape[1]), dtype=np.uint64).astype(np.uint32)
+    syn[-k:] = np.uint32(0xFFFFFFFF)
+    if c.m % 32:
+        syn[:, -1] &= np.uint32((1 << (c.m % 32)) - 1)
+    p = EXTREME_GAINS[name]
+    ref = _decode_with_kernel(c, KERNEL_GENERIC, syn, L0, p)
+    assert _same(_decode_with_kernel(c, KERNEL_QC, syn, L0, p), ref)
+    sel = np.r_[0:4, k:k + 4, shots - 4:shots]
+    tr = _decode_with_kernel(c, KERNEL_GENERIC, syn[sel], L0[sel], p, trace=True)["trace"]
+    tq = _decode_with_kernel(c, KERNEL_QC, syn[sel], L0[sel], p, trace=True)["trace"]
+    assert np.array_equal(np.nan_to_num(tr, nan=7.0), np.nan_to_num(tq, nan=7.0))
+
+
 @pytest.mark.parametrize("kernel", [KERNEL_GROUPS, KERNEL_QC])
 @pytest.mark.parametrize("shots", [1, 2, 3, 5, 300, 305])
 def test_group_kernel_small_and_ragged_batches(group_codes, shots, kernel):
