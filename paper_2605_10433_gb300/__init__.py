@@ -42,6 +42,8 @@ class DeviceCode:
         from . import _native
         self._native = _native
         self.m, self.n = int(m), int(n)
+        import torch
+        self.device = torch.cuda.current_device()   # sagms_load_code uploads to the current device
         self.handle = _native.sagms_load_code(m, n, row_ptr, col_idx)
         _, _, self.dc_max, self.dv_max = _native.sagms_code_info(self.handle)
 
@@ -91,6 +93,61 @@ def ctypes_void(x):
     return ctypes.c_void_p(int(x))
 
 
+# Element kinds and sizes of the decode buffers: (name, numpy kinds, itemsize).
+_BUFFERS = (("syn", "iu", 4), ("L0", "f", 4), ("err", "iu", 4), ("conv", "u", 1), ("iters", "i", 4))
+
+
+def _buffer_facts(a):
+    """(numpy dtype, shape, C-contiguous, device) of a torch tensor or numpy array; device is
+    'cpu' or 'cuda:<index>'."""
+    import numpy as np
+    if hasattr(a, "data_ptr"):
+        try:
+            dt = np.dtype(str(a.dtype).replace("torch.", ""))
+        except TypeError:   # a torch type numpy does not have (bfloat16, ...)
+            raise TypeError(f"unsupported buffer dtype {a.dtype}") from None
+        dev = f"cuda:{a.device.index}" if a.is_cuda else "cpu"
+        return dt, tuple(a.shape), a.is_contiguous(), dev
+    a = np.asarray(a)
+    return a.dtype, a.shape, a.flags.c_contiguous, "cpu"
+
+
+def _check_buffers(code: "DeviceCode", params: "Params", bufs, host: bool):
+    """Check the caller's buffers against the code before their pointers reach the library:
+    a wrong dtype or shape would let a kernel or a copy run past a buffer's end.  ``bufs`` are
+    (syn, L0, err, conv, iters); syn's rows give the shot count.  Output buffers may hold more
+    rows than shots (only the first rows are written); row widths and L0's length must match.
+    Raises TypeError or ValueError; returns the shot count."""
+    facts = [_buffer_facts(a) for a in bufs]
+    shots = facts[0][1][0] if len(facts[0][1]) == 2 else -1
+    per_qubit = bool(params.flags & FLAG_L0_PER_QUBIT)
+    for (name, kinds, size), (dt, shape, contig, dev) in zip(_BUFFERS, facts):
+        if dt.kind not in kinds or dt.itemsize != size:
+            raise TypeError(f"{name}: dtype {dt} (need a {size}-byte {'/'.join(kinds)} type)")
+        if not contig:
+            raise ValueError(f"{name}: not contiguous")
+        if host and dev != "cpu":
+            raise ValueError(f"{name}: must be in host memory (numpy or a CPU tensor), got {dev}")
+        if not host and dev != f"cuda:{code.device}":
+            raise ValueError(f"{name}: must be a CUDA tensor on cuda:{code.device} (the code's device), got {dev}")
+        if name == "syn":
+            ok = len(shape) == 2 and shape[1] == code.mw
+            want = f"[shots, {code.mw}]"
+        elif name == "L0":
+            want_len = code.n if per_qubit else shots
+            ok = shape == (want_len,)
+            want = f"[{want_len}]" + (" (one prior per qubit)" if per_qubit else " (one prior per shot)")
+        elif name == "err":
+            ok = len(shape) == 2 and shape[1] == code.nw and shape[0] >= shots
+            want = f"[>= {shots}, {code.nw}]"
+        else:
+            ok = len(shape) == 1 and shape[0] >= shots
+            want = f"[>= {shots}]"
+        if not ok:
+            raise ValueError(f"{name}: shape {list(shape)}, need {want}")
+    return shots
+
+
 def decode(code: DeviceCode, syn, L0, params: Params | None = None, out=None, stream=None, trace=False):
     """Decode packed syndromes on the GPU.
 
@@ -103,14 +160,13 @@ def decode(code: DeviceCode, syn, L0, params: Params | None = None, out=None, st
     params = params or Params()
     shots = syn.shape[0]
     dev = syn.device
-    assert syn.dtype == torch.int32 and syn.is_cuda and syn.is_contiguous()
-    assert L0.dtype == torch.float32 and L0.is_cuda and L0.is_contiguous()
     if out is None:
         err = torch.empty((shots, code.nw), dtype=torch.int32, device=dev)
         conv = torch.empty((shots,), dtype=torch.uint8, device=dev)
         iters = torch.empty((shots,), dtype=torch.int32, device=dev)
     else:
         err, conv, iters = out
+    _check_buffers(code, params, (syn, L0, err, conv, iters), host=False)
     p = params.to_c()
     sp = _stream_ptr(stream)
     if trace:
@@ -140,6 +196,7 @@ def decode_host(code: DeviceCode, syn, L0, params: Params | None = None, out=Non
         iters = np.empty((shots,), dtype=np.int32)
     else:
         err, conv, iters = out
+    _check_buffers(code, params, (syn, L0, err, conv, iters), host=True)
     _native.sagms_decode_host(code.handle, params.to_c(), shots, ptr(syn), ptr(L0), ptr(err), ptr(conv), ptr(iters))
     return err, conv, iters
 
@@ -167,6 +224,7 @@ class Job:
                    torch.empty((shots,), dtype=torch.uint8, device=syn.device),
                    torch.empty((shots,), dtype=torch.int32, device=syn.device))
         self.err, self.conv, self.iters = out
+        _check_buffers(code, self.params, (syn, L0, self.err, self.conv, self.iters), host=False)
 
     def to_c(self):
         from . import _native
@@ -214,6 +272,7 @@ def autotune(code: DeviceCode, syn, L0, params: Params | None = None, stream=Non
     err = torch.empty((shots, code.nw), dtype=torch.int32, device=syn.device)
     conv = torch.empty((shots,), dtype=torch.uint8, device=syn.device)
     iters = torch.empty((shots,), dtype=torch.int32, device=syn.device)
+    _check_buffers(code, params, (syn, L0, err, conv, iters), host=False)
     return _native.sagms_autotune(code.handle, params.to_c(), shots, syn.data_ptr(), L0.data_ptr(), err.data_ptr(),
                                   conv.data_ptr(), iters.data_ptr(), _stream_ptr(stream))
 
@@ -234,14 +293,23 @@ class Server:
                                                          int(shots_per_cta), ctypes.byref(h)))
         self.handle = h.value
         self._bufs = {}
+        self._codes = {}   # code id -> (DeviceCode, Params), to check request buffers
 
     def add_code(self, code: DeviceCode, params: Params | None = None) -> int:
         import ctypes
         cid = ctypes.c_int32()
-        p = (params or Params()).to_c()
+        params = params or Params()
+        p = params.to_c()
         self._native._check(self._native.lib().sagms_server_add_code(self.handle, code.handle, ctypes.byref(p),
                                                                      ctypes.byref(cid)))
+        self._codes[cid.value] = (code, params)
         return cid.value
+
+    def _check_request(self, code_id, bufs):
+        # an unknown id is left to the library, which refuses it
+        if int(code_id) in self._codes:
+            code, params = self._codes[int(code_id)]
+            _check_buffers(code, params, bufs, host=True)
 
     @staticmethod
     def _ptr(a):
@@ -251,6 +319,7 @@ class Server:
         import ctypes
         t = ctypes.c_uint64()
         shots = syn.shape[0]
+        self._check_request(code_id, (syn, L0, err, conv, iters))
         self._native._check(self._native.lib().sagms_server_submit(
             self.handle, int(code_id), shots, self._ptr(syn), self._ptr(L0), self._ptr(err), self._ptr(conv),
             self._ptr(iters), ctypes.byref(t)))
@@ -285,6 +354,8 @@ class Server:
         import ctypes
         import numpy as np
         n = len(requests)
+        for cid, r in zip(code_ids, requests):
+            self._check_request(cid, r)
         VP = ctypes.c_void_p * n
         cols = list(zip(*requests)) if n else [[]] * 5
         ptrs = [VP(*[self._ptr(a) for a in col]) for col in cols]
@@ -347,12 +418,25 @@ def mc_sample(code: DeviceCode, seed: int, q: float, shot0: int, shots: int, L0:
     return err, syn, l0
 
 
+def _check_mc_frames(code, name, a, shots, tail, kinds, size):
+    dt, shape, contig, dev = _buffer_facts(a)
+    if dt.kind not in kinds or dt.itemsize != size:
+        raise TypeError(f"{name}: dtype {dt} (need a {size}-byte {'/'.join(kinds)} type)")
+    if not contig or dev != f"cuda:{code.device}" or shape != (shots, *tail):
+        raise ValueError(f"{name}: need a contiguous CUDA tensor on cuda:{code.device} of shape "
+                         f"{[shots, *tail]}, got {list(shape)} on {dev}")
+
+
 def mc_check(code: DeviceCode, err, err_hat, conv, iters, stream=None):
     """Logical check of decoded frames (logicals attached): (fail uint8 [shots] with 0 success,
     1 not converged, 2 logical error; counts dict).  Synchronises ``stream``."""
     import torch
     from . import _native
     shots = err.shape[0]
+    for name, a in (("err", err), ("err_hat", err_hat)):
+        _check_mc_frames(code, name, a, shots, (code.nw,), "iu", 4)
+    _check_mc_frames(code, "conv", conv, shots, (), "u", 1)
+    _check_mc_frames(code, "iters", iters, shots, (), "i", 4)
     fail = torch.empty((shots,), dtype=torch.uint8, device="cuda")
     counts = torch.zeros((5,), dtype=torch.int64, device="cuda")
     _native.sagms_mc_check(code.handle, shots, err.data_ptr(), err_hat.data_ptr(), conv.data_ptr(), iters.data_ptr(),
