@@ -190,6 +190,9 @@ int sagms_check_params(const sagms_params* params);
  *   d_iters [shots] device, out: message-passing rounds completed when the residual first
  *           became zero (0 for a zero syndrome); max_iter when it never did.
  *   stream  cudaStream_t to launch on (NULL = legacy default stream).
+ * The caller owns every buffer; d_syn, d_L0, d_err and d_iters must be 4-byte aligned
+ * (ERR_ARG otherwise, before anything is launched).  The library cannot see buffer sizes:
+ * each must hold the elements stated above.
  * Asynchronous: results are valid once `stream` has reached this point.  shots == 0 is
  * a no-op.  Errors: ERR_ARG, ERR_PARAM, ERR_SIZE, ERR_OOM, ERR_CUDA.
  */

@@ -376,6 +376,10 @@ int sagms_mc_check(const sagms_code* code, int64_t shots, const uint32_t* d_err,
     if (shots < 0) return mc_fail(SAGMS_ERR_ARG, "shots < 0");
     if (shots == 0) return SAGMS_OK;
     if (!d_err || !d_err_hat || !d_conv || !d_iters || !d_counts) return mc_fail(SAGMS_ERR_ARG, "NULL device buffer");
+    // 4-byte words and counts; the counters are 64-bit atomics
+    const auto misaligned = [](const void* ptr, uintptr_t a) { return (reinterpret_cast<uintptr_t>(ptr) & (a - 1)) != 0; };
+    if (misaligned(d_err, 4) || misaligned(d_err_hat, 4) || misaligned(d_iters, 4) || misaligned(d_counts, 8))
+        return mc_fail(SAGMS_ERR_ARG, "device buffers misaligned (4-byte words, 8-byte counters)");
     const CodeView v = sagms_internal::code_view(code);
     if (v.k_logicals < 0) return mc_fail(SAGMS_ERR_ARG, "no logical operators attached (sagms_mc_set_logicals)");
     const int rc = on_code_device(v);

@@ -848,16 +848,25 @@ int launch_layered(const sagms_code* code, const DecodeArgs& a, bool per_qubit, 
     return SAGMS_OK;
 }
 
+bool aligned4(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 3u) == 0; }
+
 int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, const uint32_t* d_syn,
                   const float* d_L0, uint32_t* d_err, uint8_t* d_conv, int32_t* d_iters, float* d_trace,
                   cudaStream_t stream, const Plan* plan_override = nullptr) {
     const sagms_internal::NvtxRange nvtx("sagms_decode");
+    if (shots < 0) return fail(SAGMS_ERR_ARG, "shots < 0");
+    if (shots > 0) {
+        if (!d_syn || !d_L0 || !d_err || !d_conv || !d_iters) return fail(SAGMS_ERR_ARG, "NULL device buffer");
+        // the kernels move syndrome words, priors, error words, counts and traces as 4-byte
+        // elements (cp.async and plain loads/stores): a misaligned buffer would fault them
+        if (!aligned4(d_syn) || !aligned4(d_L0) || !aligned4(d_err) || !aligned4(d_iters) ||
+            (d_trace && !aligned4(d_trace)))
+            return fail(SAGMS_ERR_ARG, "device buffers must be 4-byte aligned (uint32 / float / int32 elements)");
+    }
     if (!code) return fail(SAGMS_ERR_ARG, "code is NULL");
     int rc = sagms_check_params(p);
     if (rc != SAGMS_OK) return rc;
-    if (shots < 0) return fail(SAGMS_ERR_ARG, "shots < 0");
     if (shots == 0) return SAGMS_OK;
-    if (!d_syn || !d_L0 || !d_err || !d_conv || !d_iters) return fail(SAGMS_ERR_ARG, "NULL device buffer");
     const bool bp = p->mode == SAGMS_BP;
     const bool per_qubit = (p->flags & SAGMS_FLAG_L0_PER_QUBIT) != 0;
     DecodeArgs a;

@@ -113,6 +113,26 @@ def test_null_arguments_are_rejected(native):
     assert lib.sagms_decode_host(None, ctypes.byref(p), 10, None, None, None, None, None) == -1
 
 
+def test_device_buffer_checks_come_before_any_launch(native):
+    """sagms_decode refuses NULL or misaligned device buffers before it touches the code
+    handle or CUDA (the pointers below are never dereferenced)."""
+    lib = native.lib()
+    p = native.sagms_params(mode=2, alpha_min=0.3, alpha_max=0.5, eta_unsat=1.1, max_iter=10)
+    A, M = 0x10000, 0x10002            # a 4-byte aligned and a misaligned address
+    ok = [A, A, A, A, A]
+    assert lib.sagms_decode(None, ctypes.byref(p), 10, None, A, A, A, A, None) == -1
+    assert "NULL device buffer" in native.sagms_last_error_string()
+    for k in (0, 1, 2, 4):             # d_syn, d_L0, d_err, d_iters (d_conv holds bytes)
+        args = list(ok)
+        args[k] = M
+        assert lib.sagms_decode(None, ctypes.byref(p), 10, *args, None) == -1
+        assert "4-byte aligned" in native.sagms_last_error_string()
+    args = list(ok)
+    args[3] = A + 1                    # a byte buffer may start anywhere
+    assert lib.sagms_decode(None, ctypes.byref(p), 10, *args, None) == -1
+    assert "code is NULL" in native.sagms_last_error_string()
+
+
 def test_oracle_source_shares_nothing_with_the_cuda_path():
     """The FP64 checker and the CUDA library include none of each other's files."""
     cu = open(os.path.join(ROOT, "paper_2605_10433_gb300", "csrc", "sagms.cu")).read()
