@@ -31,3 +31,33 @@ def test_profile_traffic_only_for_the_captured_code():
         assert 300 < float(per_shot.group(1)) < 500   # the algorithmic 393 B/shot, no re-reads
     else:
         assert t is None
+
+
+def _run_bench(args, env_extra=None):
+    import json
+    import subprocess
+    env = {**os.environ, **(env_extra or {})}
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], capture_output=True, text=True,
+                       env=env, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    return [json.loads(ln) for ln in lines]
+
+
+def test_reference_arm_prints_one_contract_line():
+    """`bench.py --impl reference` times the FP64 oracle on the host cores (no GPU) and prints
+    one JSON line with the keys the contract names, on bench.py's metric and unit."""
+    (line,) = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "3", "--ref-sample", "300"])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["steps"] == 1 and line["warmup"] == 3 and line["value"] > 0 and line["higher_is_better"] is True
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and "300" in cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    assert _run_bench(["--impl", "reference", "--steps", "1", "--ref-sample", "50"], {"RANK": "1"}) == []
