@@ -317,7 +317,9 @@ int sagms_set_plan(sagms_code* code, int32_t plan);   /* 0 restores the defaults
  *   - SAGMS_SERVE_PLAIN: the baseline -- one request at a time on one stream, full grid.
  * Results are those of sagms_decode for the same code, parameters and inputs.
  * Host buffers must stay valid until the request finishes (page-locked memory copies
- * fastest).  Errors: ERR_ARG, ERR_SIZE (request larger than the budget), ERR_BUSY (server
+ * fastest).  A registered code handle must stay loaded until the server is destroyed.
+ * A cancelled request leaves the admission queue at once and may be released right away.
+ * Errors: ERR_ARG, ERR_SIZE (request larger than the budget), ERR_BUSY (server
  * stopping, or cancel of a running request), ERR_TIMEOUT (poll), ERR_CANCELLED.
  */
 enum { SAGMS_SERVE_CONTINUOUS = 0, SAGMS_SERVE_PLAIN = 1 };

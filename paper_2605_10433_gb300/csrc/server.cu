@@ -194,8 +194,9 @@ void sagms_server::run() {
         }
         // admissions in arrival order, gated by a free slot and arena memory
         while (!queue.empty()) {
-            Request& r = *reqs[queue.front()];
-            if (r.state == kCancelled) { queue.pop_front(); continue; }
+            const auto it = reqs.find(queue.front());
+            if (it == reqs.end() || it->second->state == kCancelled) { queue.pop_front(); continue; }
+            Request& r = *it->second;
             int slot = -1;
             for (size_t k = 0; k < slot_req.size(); ++k)
                 if (!slot_req[k]) { slot = (int)k; break; }
@@ -343,6 +344,9 @@ int sagms_server_cancel(sagms_server* s, uint64_t ticket) {
     if (r.state != kQueued) return set_error(SAGMS_ERR_BUSY, "request already admitted or finished");
     r.state = kCancelled;
     r.t_done = now_ns();
+    // out of the admission queue now, so a release right after the cancel leaves no stale id
+    const auto q = std::find(s->queue.begin(), s->queue.end(), ticket);
+    if (q != s->queue.end()) s->queue.erase(q);
     s->cv_done.notify_all();
     return SAGMS_OK;
 }
@@ -376,8 +380,11 @@ int sagms_server_destroy(sagms_server* s) {
         std::lock_guard<std::mutex> lk(s->mu);
         s->stop = true;
         for (uint64_t id : s->queue) {
-            Request& r = *s->reqs[id];
-            if (r.state == kQueued) { r.state = kCancelled; r.t_done = now_ns(); }
+            const auto it = s->reqs.find(id);
+            if (it != s->reqs.end() && it->second->state == kQueued) {
+                it->second->state = kCancelled;
+                it->second->t_done = now_ns();
+            }
         }
         s->queue.clear();
         s->cv_work.notify_all();

@@ -114,6 +114,7 @@ def test_cancel_malformed_requests_and_timeouts_leave_the_server_serving(codes):
     assert srv.poll(t_q[-1], 0) == -7
     assert srv.cancel(t_q[1]) == 0
     assert srv.poll(t_q[1], 1000) == -10            # cancelled
+    assert srv.release(t_q[1]) == 0                 # released while its turn is still ahead
     # malformed requests mid-stream are refused on the host and change nothing
     bad = req(10, 99)
     with pytest.raises(S._native.SagmsError):
