@@ -278,6 +278,8 @@ int on_code_device(const CodeView& v) {
     return SAGMS_OK;
 }
 
+bool misaligned(const void* ptr, uintptr_t bytes) { return (reinterpret_cast<uintptr_t>(ptr) & (bytes - 1)) != 0; }
+
 int sample_launch(const CodeView& v, uint64_t seed, double q, float L0, int64_t shot0, int64_t shots,
                   const uint32_t* d_T, uint32_t* d_err, uint32_t* d_syn, float* d_L0, cudaStream_t st) {
     const size_t smem = (size_t)(kMcThreads / 32) * (((v.n + 31) / 32) + ((v.m + 31) / 32)) * 4;
@@ -345,9 +347,12 @@ int sagms_mc_set_logicals(sagms_code* code, int32_t k, const uint32_t* logicals)
 
 int sagms_mc_sample(const sagms_code* code, uint64_t seed, double q, float L0, int64_t shot0, int64_t shots,
                     uint32_t* d_err, uint32_t* d_syn, float* d_L0, void* stream) {
-    if (!code) return mc_fail(SAGMS_ERR_ARG, "code is NULL");
     if (!(q >= 0.0 && q < 1.0)) return mc_fail(SAGMS_ERR_PARAM, "flip probability outside [0, 1)");
     if (shots < 0 || shot0 < 0) return mc_fail(SAGMS_ERR_ARG, "negative shot range");
+    // each output is optional; those given take 4-byte words
+    if (misaligned(d_err, 4) || misaligned(d_syn, 4) || misaligned(d_L0, 4))
+        return mc_fail(SAGMS_ERR_ARG, "device buffers must be 4-byte aligned");
+    if (!code) return mc_fail(SAGMS_ERR_ARG, "code is NULL");
     if (shots == 0) return SAGMS_OK;
     const CodeView v = sagms_internal::code_view(code);
     int rc = on_code_device(v);
@@ -372,14 +377,16 @@ int sagms_mc_sample(const sagms_code* code, uint64_t seed, double q, float L0, i
 int sagms_mc_check(const sagms_code* code, int64_t shots, const uint32_t* d_err, const uint32_t* d_err_hat,
                    const uint8_t* d_conv, const int32_t* d_iters, uint8_t* d_fail, sagms_mc_counts* d_counts,
                    void* stream) {
-    if (!code) return mc_fail(SAGMS_ERR_ARG, "code is NULL");
     if (shots < 0) return mc_fail(SAGMS_ERR_ARG, "shots < 0");
+    if (shots > 0) {
+        if (!d_err || !d_err_hat || !d_conv || !d_iters || !d_counts)
+            return mc_fail(SAGMS_ERR_ARG, "NULL device buffer");
+        // 4-byte words and counts; the counters are 64-bit atomics
+        if (misaligned(d_err, 4) || misaligned(d_err_hat, 4) || misaligned(d_iters, 4) || misaligned(d_counts, 8))
+            return mc_fail(SAGMS_ERR_ARG, "device buffers misaligned (4-byte words, 8-byte counters)");
+    }
+    if (!code) return mc_fail(SAGMS_ERR_ARG, "code is NULL");
     if (shots == 0) return SAGMS_OK;
-    if (!d_err || !d_err_hat || !d_conv || !d_iters || !d_counts) return mc_fail(SAGMS_ERR_ARG, "NULL device buffer");
-    // 4-byte words and counts; the counters are 64-bit atomics
-    const auto misaligned = [](const void* ptr, uintptr_t a) { return (reinterpret_cast<uintptr_t>(ptr) & (a - 1)) != 0; };
-    if (misaligned(d_err, 4) || misaligned(d_err_hat, 4) || misaligned(d_iters, 4) || misaligned(d_counts, 8))
-        return mc_fail(SAGMS_ERR_ARG, "device buffers misaligned (4-byte words, 8-byte counters)");
     const CodeView v = sagms_internal::code_view(code);
     if (v.k_logicals < 0) return mc_fail(SAGMS_ERR_ARG, "no logical operators attached (sagms_mc_set_logicals)");
     const int rc = on_code_device(v);

@@ -133,6 +133,23 @@ def test_device_buffer_checks_come_before_any_launch(native):
     assert "code is NULL" in native.sagms_last_error_string()
 
 
+def test_monte_carlo_buffer_checks_come_before_any_launch(native):
+    """The sampler's optional outputs and the logical check's buffers are checked for NULL and
+    alignment before the code handle or CUDA is touched."""
+    lib = native.lib()
+    A, M = 0x10000, 0x10002
+    assert lib.sagms_mc_sample(None, 1, 0.1, 4.0, 0, 10, M, None, None, None) == -1
+    assert "aligned" in native.sagms_last_error_string()
+    assert lib.sagms_mc_sample(None, 1, 0.1, 4.0, 0, 10, None, None, None, None) == -1
+    assert "code is NULL" in native.sagms_last_error_string()   # all three outputs may be NULL
+    assert lib.sagms_mc_check(None, 10, A, A, A, A, None, None, None) == -1
+    assert "NULL device buffer" in native.sagms_last_error_string()
+    assert lib.sagms_mc_check(None, 10, A, A, A, A, None, A + 4, None) == -1   # counters are 8-byte
+    assert "misaligned" in native.sagms_last_error_string()
+    assert lib.sagms_mc_check(None, 10, A, A, A + 1, A, None, A, None) == -1   # conv holds bytes
+    assert "code is NULL" in native.sagms_last_error_string()
+
+
 def test_oracle_source_shares_nothing_with_the_cuda_path():
     """The FP64 checker and the CUDA library include none of each other's files."""
     cu = open(os.path.join(ROOT, "paper_2605_10433_gb300", "csrc", "sagms.cu")).read()
