@@ -11,7 +11,7 @@ Prints one JSON line (rank 0).  Under torchrun each rank decodes its own 1e7-sho
 its own GPU (weak scaling, no data-path collective); the timed region is bracketed by a
 barrier and a device synchronize, and the slowest rank's time is reported.
 
---impl reference times the FP64 CPU oracle (the reference arm of this build) on the host
+--impl reference times the FP64 CPU oracle (the reference arm of the comparison) on the host
 cores, on a bounded sample of the same workload.
 """
 from __future__ import annotations
