@@ -325,3 +325,22 @@ def test_clip_frequency_on_the_configs(lw, q, max_iter):
               f"{int(fired[~conv].sum())}/{int((~conv).sum())} failing shots")
         if mode != oracle.BP:
             assert not fired.any()
+
+
+@pytest.mark.parametrize("mode", [oracle.MS, oracle.SMS, oracle.SAGMS, oracle.BP])
+def test_per_qubit_priors_equal_to_the_shot_prior_decode_identically(mode):
+    """The per-qubit prior path (SAGMS_FLAG_L0_PER_QUBIT, LLR units) with every qubit's prior
+    set to the shot's L0 is the per-shot path in LLR units: same decisions, iteration counts
+    and posterior traces, bit for bit, in every mode.  This ties the two prior plumbings to
+    each other (a wrong prior index or a unit slip in either one breaks it)."""
+    c = I.gb_code(127, 4)
+    shots = 40
+    _, syn = I.sample(c, 0.03, shots, seed=21)
+    L0 = I.llr_prior(np.full(shots, 0.03))
+    units = 0 if mode == oracle.BP else oracle.FLAG_NATURAL_UNITS
+    a = oracle.decode_code(c, syn, L0, mode=mode, max_iter=25, flags=units, trace=True)
+    for s in range(shots):
+        b = oracle.decode_code(c, syn[s:s + 1], np.full(c.n, L0[s]), mode=mode, max_iter=25,
+                               flags=oracle.FLAG_L0_PER_QUBIT, trace=True)
+        assert np.array_equal(a["err"][s], b["err"][0]) and a["iters"][s] == b["iters"][0]
+        assert np.array_equal(np.nan_to_num(a["trace"][s], nan=7.0), np.nan_to_num(b["trace"][0], nan=7.0))
