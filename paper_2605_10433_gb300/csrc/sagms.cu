@@ -511,6 +511,7 @@ int sagms_column_slots(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr
     if (D < 1 || D > 32) return fail(SAGMS_ERR_ARG, "D = %d outside [1, 32]", D);
     if (dv_max > D || dc_max > 2 * D)
         return fail(SAGMS_ERR_DEGREE, "degrees dc=%d dv=%d need more than %d message rows", dc_max, dv_max, D);
+    if (nnz == 0) return SAGMS_OK;   // no edges: the empty assignment
     const std::vector<int> s = column_slots(m, n, row_ptr, col_idx, D);
     if (s.empty()) return fail(SAGMS_ERR_DEGREE, "no column-indexed slot assignment found");
     std::copy(s.begin(), s.end(), slots);

@@ -107,3 +107,37 @@ def test_errors():
     with pytest.raises(_native.SagmsError) as ex:
         _native.sagms_column_slots(1, 4, rp, np.array([0, 1, 2], dtype=np.int32), 0)
     assert ex.value.code == -1   # ERR_ARG
+
+
+def test_qubit_degree_above_the_row_count_is_refused():
+    rp = np.array([0, 1, 2], dtype=np.int32)
+    with pytest.raises(_native.SagmsError) as ex:   # qubit 0 in two checks, one message row
+        _native.sagms_column_slots(2, 3, rp, np.array([0, 0], dtype=np.int32), 1)
+    assert ex.value.code == -3   # ERR_DEGREE
+
+
+def test_property_on_small_irregular_codes():
+    """Any code with qubit degrees <= D and check degrees <= 2D, in any column order, with
+    empty checks and unused qubits, gets valid slots (hypothesis draws the graphs)."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+
+    @hyp.settings(max_examples=300, deadline=None, derandomize=True)
+    @hyp.given(D=st.integers(1, 6), m=st.integers(1, 24), n=st.integers(1, 40), seed=st.integers(0, 2 ** 32 - 1),
+               fill=st.floats(0.0, 1.0))
+    def check(D, m, n, seed, fill):
+        rng = np.random.default_rng(seed)
+        qdeg = np.zeros(n, dtype=int)
+        rows = []
+        for _ in range(m):
+            want = int(rng.integers(0, 2 * D + 1) * fill + 0.5)
+            free = [c for c in rng.permutation(n).tolist() if qdeg[c] < D][:want]
+            for c in free:
+                qdeg[c] += 1
+            rows.append(free)
+        rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+        ci = np.array([c for r in rows for c in r], dtype=np.int32)
+        s = _native.sagms_column_slots(m, n, rp, ci, D)
+        assert _valid(m, n, rp, ci, s, D)
+
+    check()
