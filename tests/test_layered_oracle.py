@@ -140,3 +140,25 @@ def test_hand_chain_layers():
     _, c, _ = _chain()
     layer, L = _native.sagms_check_layers(c.m, c.n, c.row_ptr, c.col_idx)
     assert list(layer) == [0, 1, 0] and L == 2
+
+
+def test_library_layering_property_on_small_irregular_codes():
+    """The first-fit rule on small irregular codes drawn by hypothesis (empty checks, unused
+    qubits, repeated neighbourhoods), against the rule written out on the dense matrix."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+    from paper_2605_10433_gb300 import _native
+
+    @hyp.settings(max_examples=300, deadline=None, derandomize=True)
+    @hyp.given(m=st.integers(1, 20), n=st.integers(1, 30), seed=st.integers(0, 2 ** 32 - 1),
+               dmax=st.integers(0, 8))
+    def check(m, n, seed, dmax):
+        rng = np.random.default_rng(seed)
+        rows = [sorted(rng.choice(n, size=min(int(rng.integers(0, dmax + 1)), n), replace=False).tolist())
+                for _ in range(m)]
+        rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+        c = I.Code(m=m, n=n, row_ptr=rp, col_idx=np.array([x for r in rows for x in r], dtype=np.int32))
+        layer, L = _native.sagms_check_layers(c.m, c.n, c.row_ptr, c.col_idx)
+        assert np.array_equal(layer, _first_fit(c)) and L == layer.max() + 1
+
+    check()
