@@ -72,6 +72,62 @@ def test_gb_logicals_span_kernel_modulo_stabilizers(lw):
     assert _rank(list(HX) + list(X)) == rx + L.shape[0]       # independent modulo rowspace H_X
 
 
+def _nullspace(H, n):
+    """Basis of {x : H x = 0 over GF(2)} by row reduction (test-side, dense)."""
+    A = (np.array(H, dtype=np.uint8).reshape(-1, n) & 1).copy()
+    piv, r = [], 0
+    for c in range(n):
+        rows = [i for i in range(r, A.shape[0]) if A[i, c]]
+        if not rows:
+            continue
+        A[[r, rows[0]]] = A[[rows[0], r]]
+        for i in range(A.shape[0]):
+            if i != r and A[i, c]:
+                A[i] ^= A[r]
+        piv.append(c)
+        r += 1
+    basis = []
+    for f in (c for c in range(n) if c not in piv):
+        x = np.zeros(n, dtype=np.uint8)
+        x[f] = 1
+        for i, c in enumerate(piv):
+            x[c] = A[i, f]
+        basis.append(x)
+    return basis
+
+
+def test_logicals_property_on_random_css_pairs():
+    """Random CSS pairs drawn by hypothesis (H_Z random, H_X random combinations of ker H_Z, so
+    H_X H_Z^T = 0, with repeated and empty rows): k = n - rank H_X - rank H_Z, every returned
+    vector lies in ker H_Z, and they are independent modulo the rowspace of H_X."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+
+    @hyp.settings(max_examples=200, deadline=None, derandomize=True)
+    @hyp.given(n=st.integers(1, 24), mz=st.integers(1, 10), mx=st.integers(1, 10), seed=st.integers(0, 2 ** 32 - 1))
+    def check(n, mz, mx, seed):
+        rng = np.random.default_rng(seed)
+        HZ = (rng.random((mz, n)) < rng.uniform(0.1, 0.6)).astype(np.uint8)
+        ker = _nullspace(HZ, n)
+        HX = np.zeros((mx, n), dtype=np.uint8)
+        for i in range(mx):
+            for b in ker:
+                if rng.random() < 0.5:
+                    HX[i] ^= b
+        rows = lambda H: [np.nonzero(r)[0].tolist() for r in H]
+        rp, ci = _csr(rows(HX), n)
+        rz, cz = _csr(rows(HZ), n)
+        L = _native.sagms_x_logicals(n, rp, ci, rz, cz)
+        rx, rzk = _rank(list(HX)), _rank(list(HZ))
+        assert L.shape[0] == n - rx - rzk
+        if L.shape[0]:
+            X = np.array([_bits(v, n) for v in L])
+            assert not (HZ.astype(np.int64) @ X.T % 2).any()
+            assert _rank(list(HX) + list(X)) == rx + L.shape[0]
+
+    check()
+
+
 def test_logicals_reject_non_css_and_bad_csr():
     rp, ci = _csr([[0, 1]], 3)
     rz, cz = _csr([[1, 2]], 3)   # overlap 1: H_X H_Z^T = 1
