@@ -107,3 +107,35 @@ def test_a_negative_gain_would_break_the_identity():
     v = np.array([1.0, 2.0, 3.0, -4.0], np.float32)
     g = np.float32(-0.5)
     assert not np.array_equal(excluded_minimum_form(v, g, np.uint32(0)), selection_form(v, g, np.uint32(0)))
+
+
+def _worst_base(amin, amaxes):
+    """Smallest FP32 base gain a_max - (a_max - a_min) * (float(cnt) * inv_m), inv_m = 1.0f / m,
+    over m <= 1024 and 0 <= cnt <= m, both with two roundings and with one (FMA contraction)."""
+    from fractions import Fraction
+    worst = np.inf
+    for m in range(1, 1025):
+        inv_m = np.float32(1.0) / np.float32(m)
+        frac = (np.arange(m + 1, dtype=np.float32) * inv_m).astype(np.float32)
+        for amax in amaxes:
+            d = np.float32(amax - amin)
+            plain = (amax - (d * frac).astype(np.float32)).astype(np.float32)
+            fma = Fraction(float(amax)) - Fraction(float(d)) * Fraction(float(frac.max()))
+            worst = min(worst, float(plain.min()), float(fma))
+    return worst
+
+
+AMAXES = np.float32([1.0, np.nextafter(np.float32(1), np.float32(0)), 0.9, 0.5, 2.0 ** -10, 2.0 ** -19])
+
+
+def test_smallest_accepted_alpha_min_keeps_the_fp32_gain_positive():
+    """Eq. 7's base gain as the kernels evaluate it in FP32 stays positive at the library's
+    smallest a_min = 2^-20 for every code size m <= 1024 (the library's limit), every
+    unsatisfied count and a range of a_max in [a_min, 1] (the automatic ceiling keeps a_max
+    there too), whether or not the compiler contracts the product and the difference into one
+    FMA.  The bound comes from a worst-case rounding analysis; measured, the gain first
+    reaches zero at a_min = 2^-25, so the accepted range keeps a factor-16 margin."""
+    amin = np.float32(2.0 ** -20)
+    assert _worst_base(amin, list(AMAXES) + [amin]) > 0
+    assert _worst_base(np.float32(2.0 ** -24), AMAXES) > 0
+    assert _worst_base(np.float32(2.0 ** -25), AMAXES) <= 0
