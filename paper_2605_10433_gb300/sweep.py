@@ -44,7 +44,9 @@ def mc_run_checkpointed(code, code_name, params, seed, q, checkpoint, L0=None, t
     every batch one line records the run's identity (code name, parameters, q, L0, seed) and
     its cumulative counts.  Calling again with the same identity resumes from the last line:
     frames are indexed by a counter-based generator, so the continued run is the same frame
-    sequence an uninterrupted one would draw.  Returns the counts."""
+    sequence an uninterrupted one would draw.  A record torn by a crash mid-write (a line
+    that does not parse) is skipped, so the run resumes from the last complete record; each
+    record is flushed to stable storage before the next batch starts.  Returns the counts."""
     import json
     import os
     from . import llr, mc_run
@@ -57,15 +59,27 @@ def mc_run_checkpointed(code, code_name, params, seed, q, checkpoint, L0=None, t
                 line = line.strip()
                 if not line:
                     continue
-                rec = json.loads(line)
+                try:
+                    rec = json.loads(line)
+                except json.JSONDecodeError:   # torn by an interrupted write
+                    continue
                 if all(rec.get(k) == v for k, v in key.items()):
                     counts = {k: rec[k] for k in ("shots", "failures", "not_converged", "logical", "iters_sum")}
     counts = counts or {"shots": 0, "failures": 0, "not_converged": 0, "logical": 0, "iters_sum": 0}
+    if os.path.exists(checkpoint) and os.path.getsize(checkpoint) > 0:
+        with open(checkpoint, "rb") as f:
+            f.seek(-1, os.SEEK_END)
+            torn = f.read(1) != b"\n"
+        if torn:   # end the torn line, so the next record starts a line of its own
+            with open(checkpoint, "a") as f:
+                f.write("\n")
     while counts["failures"] < target_failures and counts["shots"] < max_shots:
         counts = mc_run(code, params, seed, q, L0=prior, target_failures=target_failures,
                         max_shots=min(counts["shots"] + batch, max_shots), batch=batch, counts=counts)
         with open(checkpoint, "a") as f:
             f.write(json.dumps({**key, **counts}) + "\n")
+            f.flush()
+            os.fsync(f.fileno())
     return counts
 
 

@@ -346,6 +346,19 @@ def test_checkpointed_run_resumes_from_the_last_record(tmp_path, monkeypatch):
     lines = [json.loads(x) for x in open(ck)]
     assert len(lines) == 1 + 10 and lines[-1]["shots"] == 10000 and lines[0]["seed"] == 99
 
+    # a crash mid-write leaves a torn last record: the run resumes from the last complete one
+    torn = str(tmp_path / "torn.jsonl")
+    sweep.mc_run_checkpointed(None, "GB(63,3)", p, 3, 0.01, torn, target_failures=10**9, max_shots=4000, batch=1000)
+    good = open(torn).read()
+    with open(torn, "a") as f:
+        f.write(good.splitlines()[-1][:37])            # half of a 5000-shot record, no newline
+    again = sweep.mc_run_checkpointed(None, "GB(63,3)", p, 3, 0.01, torn, target_failures=10**9, max_shots=10000,
+                                      batch=1000)
+    assert again == ref
+    recs = [x for x in open(torn).read().splitlines() if x]
+    assert len(recs) == 4 + 1 + 6 and all(json.loads(x)["shots"] == 1000 * (k + 1)
+                                          for k, x in enumerate(recs[:4] + recs[5:]))
+
 
 @gpu
 def test_checkpointed_run_on_the_gpu_equals_one_run(dev, tmp_path):
