@@ -113,3 +113,59 @@ def test_two_rank_monte_carlo_matches_single_process(tmp_path, target, max_shots
     ranges = sorted((s0, s0 + n) for o in out for s0, n in o["seen"] if n > 0)
     assert ranges[0][0] == 0 and all(a[1] == b[0] for a, b in zip(ranges, ranges[1:]))
     assert ranges[-1][1] == ref["shots"]
+
+
+def _mc_failing_rank_main(rank, world, port, outdir, batch):
+    """Rank 1's batch runner fails in round 2 and the process dies at once (as after a crash);
+    rank 0 records how its own run ended."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import datetime
+    import json
+    import time
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=20))
+    from paper_2605_10433_gb300 import sweep
+    calls = []
+
+    def frames(code, params, seed, q, shot0, shots, L0):
+        calls.append(shot0)
+        if rank == 1 and len(calls) == 2:
+            raise RuntimeError("injected batch failure")
+        return _fake_frames(code, params, seed, q, shot0, shots, L0)
+
+    t0 = time.monotonic()
+    try:
+        total = sweep.mc_run_sharded(None, None, 5, 0.01, target_failures=10**9, max_shots=10**6, batch=batch,
+                                     frames=frames)
+        outcome = {"returned": total}
+    except Exception as e:   # recorded for the test, then this rank leaves without further collectives
+        outcome = {"error": type(e).__name__, "message": str(e)[:200]}
+    outcome["seconds"] = time.monotonic() - t0
+    outcome["rounds"] = len(calls)
+    with open(os.path.join(outdir, f"fail{rank}.json"), "w") as f:
+        json.dump(outcome, f)
+    os._exit(3 if rank == 1 else 0)
+
+
+def test_a_failing_rank_ends_the_sharded_run_on_every_rank(tmp_path):
+    """Failure detection without a GPU: when one rank's batch fails and its process dies, the
+    other rank learns of it in its next all-reduce and leaves the run with an error in bounded
+    time instead of waiting forever or returning partial totals."""
+    import json
+    world = 2
+    ctx = mp.start_processes(_mc_failing_rank_main, args=(world, _free_port(), str(tmp_path), 1000),
+                             nprocs=world, join=False, start_method="spawn")
+    for p in ctx.processes:
+        p.join(120)
+    alive = [p.pid for p in ctx.processes if p.is_alive()]
+    for p in ctx.processes:
+        if p.is_alive():
+            p.kill()
+    assert not alive, "a rank did not finish"
+    assert [p.exitcode for p in ctx.processes] == [0, 3]
+    r0 = json.load(open(os.path.join(tmp_path, "fail0.json")))
+    r1 = json.load(open(os.path.join(tmp_path, "fail1.json")))
+    assert r1["error"] == "RuntimeError" and "injected" in r1["message"] and r1["rounds"] == 2
+    assert "error" in r0 and "returned" not in r0 and r0["seconds"] < 60
