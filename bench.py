@@ -54,6 +54,14 @@ def workload_name(shots):
             f"eta=1.10, max_iter={MAX_ITER}")
 
 
+def rank_inputs(code, shots, rank):
+    """One rank's shard of the workload: shots [rank * shots, (rank + 1) * shots) of the
+    seeded batch (weak scaling: every rank decodes its own, disjoint shots).  Returns the
+    generator's (err, syn, L0, q) tuple."""
+    from paper_2605_10433_gb300 import inputs as I
+    return I.workload(code, P_VALUES, shots, seed=NOISE_SEED, shot0=rank * shots)
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -346,7 +354,7 @@ def main():
     code = I.gb_code(L, W)
     shots = args.shots
     t0 = time.perf_counter()
-    _, syn, L0, qv = I.workload(code, P_VALUES, shots, seed=NOISE_SEED, shot0=rank * shots)
+    _, syn, L0, qv = rank_inputs(code, shots, rank)
     gen_s = time.perf_counter() - t0
     dcode = S.DeviceCode.from_code(code)
     d_syn = torch.from_numpy(syn.view(np.int32)).cuda()

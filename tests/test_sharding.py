@@ -169,3 +169,19 @@ def test_a_failing_rank_ends_the_sharded_run_on_every_rank(tmp_path):
     r1 = json.load(open(os.path.join(tmp_path, "fail1.json")))
     assert r1["error"] == "RuntimeError" and "injected" in r1["message"] and r1["rounds"] == 2
     assert "error" in r0 and "returned" not in r0 and r0["seconds"] < 60
+
+
+def test_bench_rank_shards_tile_the_single_process_batch():
+    """bench.py's per-rank inputs: the shards of ranks 0 .. W-1 are disjoint, consecutive
+    slices of the one-process batch of W times the shots, with the same noise levels."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2605_10433_gb300 import inputs as I
+    code = I.gb_code(63, 3)
+    shots, world = 301, 3
+    _, syn_all, L0_all, q_all = I.workload(code, bench.P_VALUES, shots * world, seed=bench.NOISE_SEED)
+    for r in range(world):
+        _, syn, L0, q = bench.rank_inputs(code, shots, r)
+        sl = slice(r * shots, (r + 1) * shots)
+        assert np.array_equal(syn, syn_all[sl]) and np.array_equal(L0, L0_all[sl]) and np.array_equal(q, q_all[sl])
