@@ -62,6 +62,18 @@ def rank_inputs(code, shots, rank):
     return I.workload(code, P_VALUES, shots, seed=NOISE_SEED, shot0=rank * shots)
 
 
+def slowest(value, dist, device):
+    """The largest of the ranks' values (the job ends with its slowest rank): an all-reduce
+    MAX over the process group (``dist`` is torch.distributed, or None for one process, which
+    returns ``value``).  NCCL groups reduce on ``device`` "cuda", gloo groups on "cpu"."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -389,11 +401,7 @@ def main():
         ms = e0.elapsed_time(e1)
         clk = sampler.stop() if sampler else None
         barrier()
-        if dist is not None:
-            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms, clk
+        return slowest(ms, dist, "cuda"), clk
 
     ms, clk = timed(sagms, args.warmup, args.steps, clocks=True)
     it_host = iters.cpu().numpy()
@@ -458,11 +466,7 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         S.decode_host(dcode, h_syn, h_L0, sagms, out=(h_err, h_conv, h_it))
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = slowest(time.perf_counter() - t0, dist, "cuda")
     assert np.array_equal(h_it.numpy(), it_host), "host path disagrees with the device path"
     out["e2e"] = {"value": shots * world * args.e2e_steps / e2e_s, "unit": UNIT,
                   "h2d_bytes_per_step": int(syn.nbytes + L0.nbytes),

@@ -185,3 +185,32 @@ def test_bench_rank_shards_tile_the_single_process_batch():
         _, syn, L0, q = bench.rank_inputs(code, shots, r)
         sl = slice(r * shots, (r + 1) * shots)
         assert np.array_equal(syn, syn_all[sl]) and np.array_equal(L0, L0_all[sl]) and np.array_equal(q, q_all[sl])
+
+
+def _slowest_rank_main(rank, world, port, outdir):
+    import sys
+    sys.path.insert(0, ROOT)
+    import json
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    got = bench.slowest(100.0 + 37.5 * rank, dist, "cpu")   # each rank's own timed region
+    with open(os.path.join(outdir, f"slow{rank}.json"), "w") as f:
+        json.dump(got, f)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_bench_reports_the_slowest_rank():
+    """bench.py's timing rule on two gloo ranks: every rank ends with the largest of the ranks'
+    times (the job's time), and one process keeps its own."""
+    import json
+    import sys
+    import tempfile
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.slowest(12.5, None, "cpu") == 12.5
+    with tempfile.TemporaryDirectory() as d:
+        mp.start_processes(_slowest_rank_main, args=(2, _free_port(), d), nprocs=2, join=True, start_method="spawn")
+        assert [json.load(open(os.path.join(d, f"slow{r}.json"))) for r in range(2)] == [137.5, 137.5]
