@@ -146,7 +146,8 @@ int sagms_code_kernels(const sagms_code* code, uint32_t* mask);
  * colouring of the graph of qubits and check halves (Koenig's theorem: it exists whenever every
  * qubit degree is <= D and every check degree <= 2D), preferring colours that keep cyclic-shift
  * structure.  sagms_load_code uses it with D = the message rows of the kernel shape it picks.
- *   slots  [nnz] host, out.
+ *   slots  [nnz] host, out (may be NULL when nnz = 0: a code without edges has the empty
+ *          assignment).
  * Host only (no CUDA call).  Errors: ERR_ARG (NULL pointers, D outside [1, 32]), ERR_CSR,
  * ERR_DEGREE (a qubit degree above D or a check degree above 2D).
  */
