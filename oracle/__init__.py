@@ -42,13 +42,20 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 
+# Compiler flags of the checker (portable: the same source builds on x86 and Arm hosts).
+CFLAGS = ["-O2", "-std=c99", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off"]
+
+
 def build_lib(force: bool = False) -> str:
-    """Compile oracle.c (portable flags: the same source builds on x86 and Arm hosts)."""
+    """Compile oracle.c.  With ORACLE_LIB_OVERRIDE set (tests that plant mistakes in a copy
+    of oracle.c and check that the pins fail), that prebuilt library is used instead."""
+    override = os.environ.get("ORACLE_LIB_OVERRIDE")
+    if override:
+        return override
     src = os.path.join(_HERE, "oracle.c")
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(src):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fno-fast-math",
-                               "-ffp-contract=off", src, "-o", tmp, "-lm"])
+        subprocess.check_call(["gcc", *CFLAGS, src, "-o", tmp, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -56,8 +63,7 @@ def build_lib(force: bool = False) -> str:
 def _load():
     global _lib
     if _lib is None:
-        build_lib()
-        lib = ctypes.CDLL(_LIB_PATH)
+        lib = ctypes.CDLL(build_lib())
         P = ctypes.POINTER
         lib.oracle_decode.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_int32), P(ctypes.c_int32),
                                       ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,

@@ -95,6 +95,46 @@ def test_zero_syndrome_gives_zero_error_at_iteration_zero(mode):
     assert (r["conv"] == 1).all() and (r["iters"] == 0).all()
 
 
+@pytest.mark.parametrize("mode", [oracle.MS, oracle.SMS, oracle.SAGMS, oracle.BP])
+def test_zero_posterior_decides_no_flip(mode):
+    """Reading of the binary hard decision: e_hat_j = 1 iff P_j < 0, so a posterior of exactly
+    zero decides 0.  With a zero prior every posterior is zero at the first check: e_hat = 0
+    and, on a zero syndrome, the decoder stops there; a qubit in no check with a zero prior
+    keeps e_hat = 0 however the rest decodes."""
+    c = I.gb_code(63, 3)
+    syn = np.zeros((3, c.mw), dtype=np.uint32)
+    r = oracle.decode_code(c, syn, np.zeros(3), mode=mode, max_iter=10)
+    assert not r["err"].any() and (r["iters"] == 0).all() and (r["conv"] == 1).all()
+    code = I.code_from_dense(_dense_code([[0, 1], [1, 2]], 4))   # qubit 3 is in no check
+    syn = np.array([[0b01], [0b11]], dtype=np.uint32)
+    r = oracle.decode_code(code, syn, np.array([2.0, 1.5, 2.5, 0.0]), mode=mode, max_iter=10,
+                           flags=oracle.FLAG_L0_PER_QUBIT)
+    assert not (r["err"][:, 0] >> 3 & 1).any()
+
+
+@pytest.mark.parametrize("mode", [oracle.MS, oracle.SMS, oracle.SAGMS, oracle.BP])
+def test_no_early_stop_runs_every_round_and_reports_convergence(mode):
+    """SAGMS_FLAG_NO_EARLY_STOP: a zero syndrome still runs all max_iter rounds; the shot ends
+    with iters = max_iter and conv = 1 (the residual is zero at return) and e_hat = 0."""
+    c = I.gb_code(63, 3)
+    syn = np.zeros((3, c.mw), dtype=np.uint32)
+    r = oracle.decode_code(c, syn, np.full(3, 2.9), mode=mode, max_iter=7, flags=oracle.FLAG_NO_EARLY_STOP)
+    assert not r["err"].any() and (r["iters"] == 7).all() and (r["conv"] == 1).all()
+
+
+def test_negative_prior_decides_every_qubit_flipped():
+    """A per-shot prior below zero (flip probability above one half) makes every qubit's first
+    decision a flip: on a code with even check degrees the all-flipped pattern satisfies the
+    zero syndrome, so the decoder stops at the first check with e_hat = all ones, in
+    L0-normalised and in LLR units alike."""
+    c = I.gb_code(63, 3)      # check degree 6
+    syn = np.zeros((2, c.mw), dtype=np.uint32)
+    for flags in (0, oracle.FLAG_NATURAL_UNITS):
+        r = oracle.decode_code(c, syn, np.full(2, -2.9), mode=oracle.SAGMS, max_iter=10, flags=flags)
+        bits = np.unpackbits(r["err"].view(np.uint8), axis=1, bitorder="little")[:, :c.n]
+        assert bits.all() and (r["iters"] == 0).all() and (r["conv"] == 1).all()
+
+
 def test_sagms_first_round_closed_form():
     """At l = 1 all CN inputs equal the prior, so Eq. 8 gives (-1)^{s_i} g_i with
     g_i = [a_max - (a_max - a_min) |s|/m] (eta if s_i else 1) (Eqs. 6, 7), and the
