@@ -15,6 +15,9 @@ Parity status per function:
   first-fit layering on a hand-drawn graph, single-layer codes, information speed on
   a chain).
 * ``alpha_star`` / ``alpha_star_approx``: pinned to the values the paper prints (Sec. V).
+* The pins themselves are checked by ``tests/test_oracle_mutants.py``: mistakes planted in a
+  copy of ``oracle.c`` (one per case, across Eqs. 1-8, Algorithm 1, the readings, the
+  automatic ceiling and the layered schedule) must each make a pin fail.
 """
 from __future__ import annotations
 
