@@ -111,3 +111,46 @@ def test_tree_code_is_a_forest():
                 assert a != b, "cycle"
                 parent[a] = b
         assert edges <= c.n + c.m - 1
+
+
+def _gap_sampler_by_definition(n, q, seed, shot):
+    """The documented sampler, restated in plain Python for one frame: uniform u32 draws
+    u_d = Philox4x32-10(counter (d // 4, shot low, shot high, 0x53414721), key (seed low,
+    seed high))[d mod 4]; the gap table T[g] = floor((1 - q)^g 2^32) with the powers formed
+    by repeated double multiplication, T[0] = 2^32 - 1 and T[g] = 2^32 - 1 while the product
+    is at least 2^32, 0 once it drops below 1; each draw skips the largest g <= n with
+    u < T[g] unflipped qubits (0 if none) and flips the next one, until the position passes n.
+    A zero probability consumes one draw and flips nothing."""
+    two32 = 4294967296.0
+    T, pw = [], 1.0
+    for g in range(n + 1):
+        t = pw * two32
+        T.append(0xFFFFFFFF if (g == 0 or t >= two32) else (0 if t < 1.0 else int(t)))
+        pw *= (1.0 - q)
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    flips, pos, d = [], 0, 0
+    while True:
+        u = I.philox4x32_10((d >> 2, shot & 0xFFFFFFFF, shot >> 32, 0x53414721), key)[d & 3]
+        d += 1
+        if q == 0.0:
+            break
+        pos += max([g for g in range(n + 1) if u < T[g]], default=0)
+        if pos >= n:
+            break
+        flips.append(pos)
+        pos += 1
+        if pos >= n:
+            break
+    return flips
+
+
+@pytest.mark.parametrize("q", [0.0, 0.02, 0.3, 0.9])
+def test_sampler_bits_equal_its_definition(q):
+    """Every flipped position of the C sampler, frame by frame, against the plain-Python
+    statement of its definition (the frames the tests and the on-device sampler share)."""
+    c = I.gb_code(63, 3)
+    seed, shot0, shots = 0x1234_5678_9ABC, 2**33 + 5, 25
+    err, _ = I.sample(c, q, shots, seed=seed, shot0=shot0)
+    bits = I.unpack_bits(err, c.n)
+    for k in range(shots):
+        assert np.nonzero(bits[k])[0].tolist() == _gap_sampler_by_definition(c.n, q, seed, shot0 + k), k
