@@ -162,3 +162,28 @@ def test_library_layering_property_on_small_irregular_codes():
         assert np.array_equal(layer, _first_fit(c)) and L == layer.max() + 1
 
     check()
+
+
+@pytest.mark.parametrize("lw", [(63, 3), (127, 4)])
+def test_layered_decode_is_invariant_under_relabelling_into_layer_order(lw):
+    """The oracle visits checks in first-fit layer order.  Relabel the checks so that their
+    index order is that order (layer by layer, by index within a layer, from the rule written
+    out on the dense matrix): first-fit then assigns every check the same layer, so the
+    layered decode must not change, bit for bit, in every round.  An oracle whose layers or
+    visiting order follow any other rule fails this on codes with several layers."""
+    c = I.gb_code(*lw)
+    layer = _first_fit(c)
+    assert layer.max() >= 3
+    order = np.lexsort((np.arange(c.m), layer))         # by (layer, index)
+    rows = [c.col_idx[c.row_ptr[i]:c.row_ptr[i + 1]] for i in order]
+    rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    c2 = I.Code(m=c.m, n=c.n, row_ptr=rp, col_idx=np.concatenate(rows).astype(np.int32))
+    assert np.array_equal(_first_fit(c2), layer[order])
+    _, syn, L0, _ = I.workload(c, [0.05], 40, seed=lw[0])
+    bits = I.unpack_bits(syn, c.m)[:, order]
+    syn2 = I.pack_bits(bits)
+    kw = dict(mode=oracle.MS, max_iter=12, trace=True, flags=LAYERED | oracle.FLAG_NO_EARLY_STOP)
+    a = oracle.decode_code(c, syn, L0, **kw)
+    b = oracle.decode_code(c2, syn2, L0, **kw)
+    assert np.array_equal(a["err"], b["err"]) and np.array_equal(a["iters"], b["iters"])
+    assert np.array_equal(np.nan_to_num(a["trace"], nan=7.0), np.nan_to_num(b["trace"], nan=7.0))

@@ -76,6 +76,14 @@ MUTANTS = {
     # Corollary 1: the automatic ceiling without its clamp to [alpha_min, 1/eta]
     "auto-ceiling-no-upper-clamp": ("if (a > 1.0 / eta_unsat) a = 1.0 / eta_unsat;", "", AUTO_PINS),
     "auto-ceiling-no-lower-clamp": ("if (!(a >= alpha_min)) a = alpha_min;", "", AUTO_PINS),
+    # layered schedule: checks visited in index order, not layer order
+    "layered-index-order": ("                if (layer[i] == l) order[o++] = i;",
+                            "                if (layer[i] == l) order[o++] = o;", LAYERED_PINS),
+    # layered schedule: a check's input includes its own old message
+    "layered-vn-not-extrinsic": ("                            if (vn_edges[u] != e) {",
+                                 "                            if (1) {", LAYERED_PINS),
+    # layered schedule: layers that are valid but not first-fit (odd checks one layer up)
+    "layered-not-first-fit": ("while (stamp[l]) ++l;", "while (stamp[l]) ++l; l = (i % 2) ? l + 1 : l;", LAYERED_PINS),
 }
 
 
