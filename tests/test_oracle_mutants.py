@@ -78,7 +78,7 @@ MUTANTS = {
     "auto-ceiling-no-lower-clamp": ("if (!(a >= alpha_min)) a = alpha_min;", "", AUTO_PINS),
     # layered schedule: checks visited in index order, not layer order
     "layered-index-order": ("                if (layer[i] == l) order[o++] = i;",
-                            "                if (layer[i] == l) order[o++] = o;", LAYERED_PINS),
+                            "                if (layer[i] == l) { order[o] = o; ++o; }", LAYERED_PINS),
     # layered schedule: a check's input includes its own old message
     "layered-vn-not-extrinsic": ("                            if (vn_edges[u] != e) {",
                                  "                            if (1) {", LAYERED_PINS),
