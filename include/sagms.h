@@ -400,7 +400,8 @@ int sagms_mc_set_logicals(sagms_code* code, int32_t k, const uint32_t* logicals)
  * 2^32 - 1; the run is the largest g <= n with u < T[g]).  This is, bit for bit, the
  * generator the tests use to build inputs.  Writes d_err [shots][ceil(n/32)],
  * d_syn [shots][ceil(m/32)] = H e, and d_L0 [shots] = L0 (the decoder's prior for the
- * level; any of the three may be NULL).  Asynchronous on `stream`.
+ * level; any of the three may be NULL; those given must be 4-byte aligned, else ERR_ARG
+ * before anything is launched).  Asynchronous on `stream`.
  */
 int sagms_mc_sample(const sagms_code* code, uint64_t seed, double q, float L0, int64_t shot0, int64_t shots,
                     uint32_t* d_err, uint32_t* d_syn, float* d_L0, void* stream);
@@ -409,7 +410,9 @@ int sagms_mc_sample(const sagms_code* code, uint64_t seed, double q, float L0, i
  * Logical check of decoded frames against their true errors (device arrays as produced by
  * sagms_mc_sample and sagms_decode): per frame a flag (0 success, 1 not converged,
  * 2 converged to a nontrivial logical) in d_fail (may be NULL), and the counts added to
- * *d_counts (device memory; shots included).  Needs attached logicals.  Asynchronous.
+ * *d_counts (device memory; shots included).  Needs attached logicals.  d_err, d_err_hat
+ * and d_iters must be 4-byte aligned and d_counts 8-byte aligned (64-bit atomics), else
+ * ERR_ARG before anything is launched.  Asynchronous.
  */
 int sagms_mc_check(const sagms_code* code, int64_t shots, const uint32_t* d_err, const uint32_t* d_err_hat,
                    const uint8_t* d_conv, const int32_t* d_iters, uint8_t* d_fail, sagms_mc_counts* d_counts,
