@@ -1281,7 +1281,11 @@ int sagms_decode_multi(const sagms_job* jobs, int32_t njobs, void* stream_v) {
     std::vector<cudaEvent_t> ev(used + 1, nullptr);
     for (auto& e : ev) {
         ce = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
-        if (ce != cudaSuccess) return cuda_fail(ce, "cudaEventCreate");
+        if (ce != cudaSuccess) {
+            for (cudaEvent_t x : ev)
+                if (x) cudaEventDestroy(x);
+            return cuda_fail(ce, "cudaEventCreate");
+        }
     }
     int rc = SAGMS_OK;
     ce = cudaEventRecord(ev[0], stream);
