@@ -1214,10 +1214,13 @@ int sagms_autotune(const sagms_code* code, const sagms_params* params, int64_t s
             }
         }
     }
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
     ce = cudaEventCreate(&e0);
     if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
-    if (ce != cudaSuccess) return cuda_fail(ce, "cudaEventCreate");
+    if (ce != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(ce, "cudaEventCreate");
+    }
     float best_ms = 0.0f;
     Plan best;
     bool have = false;
