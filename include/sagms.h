@@ -305,6 +305,18 @@ int sagms_autotune(const sagms_code* code, const sagms_params* params, int64_t s
 int sagms_set_plan(sagms_code* code, int32_t plan);   /* 0 restores the defaults */
 
 /*
+ * Largest number of shots one kernel launch of a continuous-batching decode of `code` takes
+ * (not part of the method).  A batch is always split into launches of at most
+ * (2^31 - 1) / W shots (W = max(ceil(m/32), ceil(n/32)) words per pattern, the kernels'
+ * 32-bit shot indexing); a positive `shots` lowers that bound for later decodes of this
+ * code, 0 restores it.  Smaller launches bound how long one launch holds the GPU; results do
+ * not depend on the split.  sagms_decode_noalloc uses one fixed counter per launch, so its
+ * size limit (SAGMS_NOALLOC_COUNTERS launches) follows this bound.
+ * Errors: SAGMS_ERR_ARG for a NULL code or shots < 0.
+ */
+int sagms_set_launch_limit(sagms_code* code, int64_t shots);
+
+/*
  * Serving loop (continuous batching; not part of the method).  A server accepts decode
  * requests -- a registered code, a batch of syndromes and priors in host memory, host output
  * buffers -- at any time from any host thread and runs them on the current device:

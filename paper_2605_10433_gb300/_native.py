@@ -77,6 +77,7 @@ def _load_library():
         "sagms_autotune": (ctypes.c_int, [vp, P(sagms_params), i64, vp, vp, vp, vp, vp, P(i32),
                                           P(ctypes.c_float), vp]),
         "sagms_set_plan": (ctypes.c_int, [vp, i32]),
+        "sagms_set_launch_limit": (ctypes.c_int, [vp, i64]),
         "sagms_server_create": (ctypes.c_int, [ctypes.c_size_t, i32, i32, i32, P(vp)]),
         "sagms_server_add_code": (ctypes.c_int, [vp, vp, P(sagms_params), P(i32)]),
         "sagms_server_submit": (ctypes.c_int, [vp, i32, i64, vp, vp, vp, vp, vp, P(ctypes.c_uint64)]),
@@ -239,6 +240,10 @@ def sagms_autotune(handle, params, shots, syn_ptr, L0_ptr, err_ptr, conv_ptr, it
 
 def sagms_set_plan(handle, plan):
     _check(_lib.sagms_set_plan(handle, int(plan)))
+
+
+def sagms_set_launch_limit(handle, shots):
+    _check(_lib.sagms_set_launch_limit(handle, int(shots)))
 
 
 def sagms_alpha_star(L0: float, dc: int) -> float:

@@ -388,8 +388,23 @@ struct sagms_code {
     // bits 8-15 CTAs per SM (0 = occupancy limit), bits 16-19 log2 shots per claimed chunk
     // (0 = automatic).
     mutable std::atomic<uint32_t> plan;
+    // Largest launch of a continuous-batching kernel set by sagms_set_launch_limit (0: only the
+    // 32-bit indexing bound of max_slot_chunk applies).
+    std::atomic<long long> launch_limit{0};
     uint64_t shape_key;    // code fingerprint for the autotune cache
 };
+
+namespace {
+
+// Shots per launch of a continuous-batching kernel for this code: the 32-bit indexing bound,
+// lowered to the code's launch limit when one is set.
+long long launch_chunk(const sagms_code* code) {
+    const long long cap = max_slot_chunk(code->m, code->n);
+    const long long lim = code->launch_limit.load();
+    return lim > 0 ? std::min(cap, lim) : cap;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -961,7 +976,7 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     // split into launches of at most max_slot_chunk shots.  Each launch gets a zeroed shot
     // counter that its CTAs claim chunks of shots from: the plan's scratch when it has one,
     // else scratch from the stream-ordered pool.
-    const long long kMaxChunk = max_slot_chunk(code->m, code->n);
+    const long long kMaxChunk = launch_chunk(code);
     const long long nchunks = (shots + kMaxChunk - 1) / kMaxChunk;
     int* d_work = plan.work;
     const bool own_work = d_work == nullptr;
@@ -1158,7 +1173,7 @@ int sagms_decode_noalloc(const sagms_code* code, const sagms_params* p, int64_t 
     if (shots < 0) return fail(SAGMS_ERR_ARG, "shots < 0");
     if (shots == 0) return SAGMS_OK;
     if (!d_syn || !d_L0 || !d_err || !d_conv || !d_iters) return fail(SAGMS_ERR_ARG, "NULL device buffer");
-    const long long kMaxChunk = max_slot_chunk(code->m, code->n);
+    const long long kMaxChunk = launch_chunk(code);
     if (shots > kMaxChunk * kNoAllocCounters)
         return fail(SAGMS_ERR_SIZE, "sagms_decode_noalloc: %lld shots exceed the fixed scratch (%d counters of %lld shots)",
                     (long long)shots, kNoAllocCounters, kMaxChunk);
@@ -1246,6 +1261,13 @@ int sagms_autotune(const sagms_code* code, const sagms_params* params, int64_t s
     store_cached_plan(code->shape_key, packed);
     if (out_plan) *out_plan = (int32_t)packed;
     if (out_shots_per_s) *out_shots_per_s = (float)(3.0 * (double)shots / (best_ms * 1e-3));
+    return SAGMS_OK;
+}
+
+int sagms_set_launch_limit(sagms_code* code, int64_t shots) {
+    if (!code) return fail(SAGMS_ERR_ARG, "code is NULL");
+    if (shots < 0) return fail(SAGMS_ERR_ARG, "launch limit %lld < 0", (long long)shots);
+    code->launch_limit.store((long long)shots);
     return SAGMS_OK;
 }
 

@@ -9,6 +9,9 @@ check that it returns exactly what sagms_decode returns, on two calls in a row (
 array keeps the previous call's counters, so the second call checks that each call
 resets what it uses).
 
+A launch limit (sagms_set_launch_limit) splits a call into several launches, so the
+fixed counters beyond the first are exercised as well.
+
 This file is collected last so that a run stopping at the first failure has already run
 every other test."""
 import ctypes
@@ -58,6 +61,35 @@ def test_noalloc_matches_decode_on_two_calls(lw, mode):
             assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("lw,mode", [((1023, 5), "sagms"), ((255, 5), "sms")])
+def test_noalloc_split_over_several_counters(lw, mode):
+    """A launch limit below the batch splits each call into several launches, so the call
+    uses fixed counters 0..k (one per launch), each reset before its launch: the results
+    must still equal sagms_decode's single launch, on two calls in a row."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_10433_gb300 import _native
+    code = I.gb_code(*lw)
+    dcode = S.DeviceCode.from_code(code)
+    shots = 20011
+    _, syn, L0, _ = I.workload(code, [0.01, 0.02], shots, seed=777 + lw[0])
+    d_syn = torch.from_numpy(syn.view(np.int32)).cuda()
+    d_L0 = torch.from_numpy(L0).cuda()
+    params = S.Params(mode=mode, max_iter=100)
+    stream = torch.cuda.current_stream()
+    ref = S.decode(dcode, d_syn, d_L0, params, stream=stream)   # one launch
+    torch.cuda.synchronize()
+    try:
+        _native.sagms_set_launch_limit(dcode.handle, 5003)          # four launches: counters 0..3
+        for _ in range(2):
+            out = _noalloc(_native, dcode, params.to_c(), d_syn, d_L0, shots, stream)
+            torch.cuda.synchronize()
+            for a, b in zip(out, ref):
+                assert torch.equal(a, b)
+    finally:
+        _native.sagms_set_launch_limit(dcode.handle, 0)
+
+
 def test_noalloc_rejects_batches_beyond_the_fixed_scratch():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -67,7 +99,9 @@ def test_noalloc_rejects_batches_beyond_the_fixed_scratch():
     params = S.Params(mode="sagms").to_c()
     too_many = 64 * (2 ** 31 - 1) + 1
     dummy = torch.zeros(16, dtype=torch.int32, device="cuda")
+    # d_err is deliberately misaligned: should the size check ever stop refusing first, the
+    # launcher's host-side alignment check still refuses the call before any launch.
     rc = _native.lib().sagms_decode_noalloc(dcode.handle, ctypes.byref(params), too_many, dummy.data_ptr(),
-                                            dummy.data_ptr(), dummy.data_ptr(), dummy.data_ptr(),
+                                            dummy.data_ptr(), dummy.data_ptr() + 2, dummy.data_ptr(),
                                             dummy.data_ptr(), None)
     assert rc == -9 and "fixed scratch" in _native.sagms_last_error_string()
