@@ -15,6 +15,9 @@ Parity status per function:
   first-fit layering on a hand-drawn graph, single-layer codes, information speed on
   a chain).
 * ``alpha_star`` / ``alpha_star_approx``: pinned to the values the paper prints (Sec. V).
+* ``shadow`` (acceptance machinery, not the method): pinned by ``tests/test_shadow.py`` -- the
+  oracle's own trajectories replay with zero deviation, a plain binary32 decoder written in
+  the test passes its bound, and planted mistakes in that decoder (Eqs. 1-8) exceed it.
 * The pins themselves are checked by ``tests/test_oracle_mutants.py``: mistakes planted in a
   copy of ``oracle.c`` (one per case, across Eqs. 1-8, Algorithm 1, the readings, the
   automatic ceiling and the layered schedule) must each make a pin fail.
@@ -75,6 +78,11 @@ def _load():
                                       P(ctypes.c_uint8), P(ctypes.c_int32), P(ctypes.c_double),
                                       P(ctypes.c_double), P(ctypes.c_int64)]
         lib.oracle_decode.restype = ctypes.c_int
+        lib.oracle_shadow.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_int32), P(ctypes.c_int32), ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_uint, P(ctypes.c_uint32), P(ctypes.c_double), ctypes.c_int,
+                                      P(ctypes.c_float), P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_int32)]
+        lib.oracle_shadow.restype = ctypes.c_int
         lib.oracle_alpha_star.argtypes = [ctypes.c_double, ctypes.c_int]
         lib.oracle_alpha_star.restype = ctypes.c_double
         lib.oracle_alpha_star_approx.argtypes = [ctypes.c_double, ctypes.c_int]
@@ -146,6 +154,36 @@ def decode(m, n, row_ptr, col_idx, syn, L0, mode=SAGMS, alpha=0.75, alpha_min=0.
 
 def decode_code(code, syn, L0, **kw):
     return decode(code.m, code.n, code.row_ptr, code.col_idx, syn, L0, **kw)
+
+
+def shadow(m, n, row_ptr, col_idx, syn, L0, G, rounds, mode=SAGMS, alpha=0.75, alpha_min=0.30, alpha_max=0.50,
+           eta_unsat=1.10, flags=0):
+    """Replay one shot's flooding rounds from another implementation's binary32 posterior
+    trace ``G`` [>= rounds+1][n] (rows 0..rounds) and bound its rounding (oracle.c,
+    ``oracle_shadow``; test acceptance only).  ``syn``: one packed row; ``L0``: the shot's prior
+    (one value) or [n] with FLAG_L0_PER_QUBIT.  Returns (dev, bnd, flips): dev[l][j] =
+    G_l(j) minus the FP64 step applied to G_{l-1}, bnd the binary32 rounding bound on |dev|,
+    flips[l] the qubits whose G_l sign differs from that step's sign."""
+    lib = _load()
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+    syn = np.ascontiguousarray(syn, dtype=np.uint32).reshape(-1)
+    L0 = np.ascontiguousarray(L0, dtype=np.float64).reshape(-1)
+    G = np.ascontiguousarray(np.asarray(G, dtype=np.float32)[:rounds + 1]).reshape(rounds + 1, n)
+    dev = np.zeros((rounds + 1, n), dtype=np.float64)
+    bnd = np.zeros((rounds + 1, n), dtype=np.float64)
+    flips = np.zeros(rounds + 1, dtype=np.int32)
+    rc = lib.oracle_shadow(m, n, _p(row_ptr, ctypes.c_int32), _p(col_idx, ctypes.c_int32), mode, alpha, alpha_min,
+                           alpha_max, eta_unsat, flags, _p(syn, ctypes.c_uint32), _p(L0, ctypes.c_double), rounds,
+                           _p(G, ctypes.c_float), _p(dev, ctypes.c_double), _p(bnd, ctypes.c_double),
+                           _p(flips, ctypes.c_int32))
+    if rc != 0:
+        raise RuntimeError("oracle_shadow: bad arguments")
+    return dev, bnd, flips
+
+
+def shadow_code(code, syn, L0, G, rounds, **kw):
+    return shadow(code.m, code.n, code.row_ptr, code.col_idx, syn, L0, G, rounds, **kw)
 
 
 def alpha_star(L0: float, dc: int) -> float:

@@ -24,18 +24,18 @@ AUTO_PINS = [os.path.join(ROOT, "tests", "test_auto_ceiling.py")]
 # name: (text in oracle.c, replacement, pin files that must catch it)
 MUTANTS = {
     # Eq. 7: the eta boost on the input syndrome bit instead of the residual bit
-    "eta-on-input-bit": ("(sres[i] ? eta_unsat : 1.0)", "(bit_of(sy, i) ? eta_unsat : 1.0)", PINS),
+    "eta-on-input-bit": ("eta_unsat, gamma, sres[i]);", "eta_unsat, gamma, bit_of(sy, i));", PINS),
     # Eq. 6: the syndrome ratio over the qubits instead of the checks
-    "gamma-over-n": ("(double)unsat / (double)m", "(double)unsat / (double)n", PINS),
+    "gamma-over-n": ("syndrome_ratio(unsat, m)", "syndrome_ratio(unsat, n)", PINS),
     # Eq. 7: the gain schedule inverted (rising with the unsatisfied fraction)
     "gain-schedule-inverted": ("(amax - (amax - alpha_min) * gamma)", "(alpha_min + (amax - alpha_min) * gamma)",
                                PINS),
     # Eqs. 3, 4, 8: the (-1)^{s_i} factor dropped
-    "syndrome-sign-dropped": ("int neg = s_i;", "int neg = 0;", PINS),
+    "syndrome-sign-dropped": ("int sg = s_i;", "int sg = 0;", PINS),
     # Eqs. 4, 8: the check's own edge kept in the minimum (not extrinsic)
     "cn-not-extrinsic": ("if (f == e) continue;", "if (0) continue;", PINS),
     # Eq. 3: tanh(|q|) instead of tanh(|q| / 2)
-    "bp-tanh-argument": ("prod *= tanh(0.5 * a);", "prod *= tanh(a);", PINS),
+    "bp-tanh-argument": ("pr *= tanh(0.5 * a);", "pr *= tanh(a);", PINS),
     # Eq. 3: atanh without its factor 2
     "bp-atanh-factor": ("2.0 * atanh(prod)", "atanh(prod)", PINS),
     # Eq. 2: the VN->CN message includes the receiving check's own message (not extrinsic)
@@ -68,7 +68,7 @@ MUTANTS = {
     # reading 10: a non-finite prior decoded instead of marking the shot invalid
     "invalid-prior-ignored": ("if (!isfinite(per_qubit ? L0[j] : L0[s])) bad = 1;", "", PINS),
     # per-qubit priors read from the wrong qubit
-    "per-qubit-index": ("double l0 = per_qubit ? L0[j] : L0[s];", "double l0 = per_qubit ? L0[0] : L0[s];", PINS),
+    "per-qubit-index": ("prior_in_units(per_qubit ? L0[j] : L0[s],", "prior_in_units(per_qubit ? L0[0] : L0[s],", PINS),
     # Algorithm 1: early stop taken although SAGMS_FLAG_NO_EARLY_STOP is set
     "no-early-stop-ignored": ("if (unsat == 0 && early_stop)", "if (unsat == 0)", PINS),
     # Algorithm 1: a zero residual at the last round reported as not converged
@@ -77,8 +77,8 @@ MUTANTS = {
     "auto-ceiling-no-upper-clamp": ("if (a > 1.0 / eta_unsat) a = 1.0 / eta_unsat;", "", AUTO_PINS),
     "auto-ceiling-no-lower-clamp": ("if (!(a >= alpha_min)) a = alpha_min;", "", AUTO_PINS),
     # layered schedule: checks visited in index order, not layer order
-    "layered-index-order": ("                if (layer[i] == l) order[o++] = i;",
-                            "                if (layer[i] == l) { order[o] = o; ++o; }", LAYERED_PINS),
+    "layered-index-order": ("            if (layer[i] == l) order[o++] = i;",
+                            "            if (layer[i] == l) { order[o] = o; ++o; }", LAYERED_PINS),
     # layered schedule: a check's input includes its own old message
     "layered-vn-not-extrinsic": ("                            if (vn_edges[u] != e) {",
                                  "                            if (1) {", LAYERED_PINS),

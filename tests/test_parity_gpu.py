@@ -43,8 +43,8 @@ def test_config1_n126_per_shot_parity(codes, mode):
     c, dc = codes[(63, 3)]
     _, syn, L0, _ = I.workload(c, [0.05], 10000, seed=101)
     r = G.compare(c, dc, syn, L0, _p(mode, max_iter=50))
-    print(f"config1 {mode}: mismatches {r['mismatch']}/{r['shots']} (near-tie {r['near_tie']}, ill-conditioned "
-          f"{r['ill_conditioned']}) FER gpu {r['fer_gpu']:.4f} oracle {r['fer_oracle']:.4f}")
+    print(f"config1 {mode}: mismatches {r['mismatch']}/{r['shots']} (near-tie {r['near_tie']}, amplified "
+          f"{r['amplified']}) FER gpu {r['fer_gpu']:.4f} oracle {r['fer_oracle']:.4f}")
     if mode == "ms":
         assert r["mismatch"] == 0   # MS is integer-valued in L0 units: exact on both sides
 
@@ -71,7 +71,7 @@ def test_config2_n254_fer_parity(codes, mode, p_dep):
     fails_o = int(round(r["fer_oracle"] * r["shots"]))
     lo, hi = wilson_interval(fails_o, r["shots"])
     assert lo - 1e-12 <= r["fer_gpu"] <= hi + 1e-12
-    print(f"config2 {mode} p={p_dep}: mismatches {r['mismatch']} (near-tie {r['near_tie']}, ill {r['ill_conditioned']}) FER gpu {r['fer_gpu']:.4f} oracle {r['fer_oracle']:.4f} [{lo:.4f},{hi:.4f}]")
+    print(f"config2 {mode} p={p_dep}: mismatches {r['mismatch']} (near-tie {r['near_tie']}, amplified {r['amplified']}) FER gpu {r['fer_gpu']:.4f} oracle {r['fer_oracle']:.4f} [{lo:.4f},{hi:.4f}]")
 
 
 @pytest.mark.parametrize("mode", ["sms", "sagms", "bp"])
@@ -121,10 +121,12 @@ def test_config4_full_launch_properties(codes):
     assert np.array_equal(ok, g1["conv"].astype(bool))
     assert g1["iters"].min() >= 0 and g1["iters"].max() <= 100
     assert (g1["iters"][g1["conv"] == 0] == 100).all()
-    idx = np.arange(0, shots, 997)
-    o = G.oracle_decode(c, syn[idx], L0[idx], p)
-    same = (g1["err"][idx] == o["err"]).all(axis=1) & (g1["iters"][idx] == o["iters"])
-    assert same.mean() >= 0.995
+    # a strided sample of this launch's outputs against the oracle, under the full acceptance
+    idx = np.arange(0, shots, 97)
+    r = G.compare(c, dc, syn[idx], L0[idx], p, gpu={k: g1[k][idx] for k in ("err", "conv", "iters")},
+                  max_amplified=1e-3)
+    print(f"config4 full launch, {len(idx)} sampled shots: mismatches {r['mismatch']} (near-tie {r['near_tie']}, "
+          f"amplified {r['amplified']})")
 
 
 # --------------------------------------------------------------------------- edge cases

@@ -95,3 +95,7 @@ def test_sorted_and_term_ordered_rows_decode_alike():
     ra, rb = G.gpu_decode(a, syn, L0, PARAMS["sagms"]), G.gpu_decode(b, syn, L0, PARAMS["sagms"])
     same = (ra["err"] == rb["err"]).all(axis=1) & (ra["iters"] == rb["iters"])
     assert same.mean() > 0.995
+    # each order on its own against the oracle, under the full acceptance
+    sb = _sorted_gb(1023, 5)
+    G.compare(g, a, syn, L0, PARAMS["sagms"], max_amplified=1e-3, gpu=ra)
+    G.compare(sb, b, syn, L0, PARAMS["sagms"], max_amplified=1e-3, gpu=rb)
