@@ -18,9 +18,11 @@ def pytest_sessionstart(session):
     from paper_2605_10433_gb300 import build as B
     from paper_2605_10433_gb300 import inputs
     import oracle
+    from oracle import gf4
     B.build()
     inputs.build_lib()
     oracle.build_lib()
+    gf4.build_lib()
 
 
 @pytest.fixture(scope="session")
