@@ -170,10 +170,22 @@ def trace_outcome_ok(code, syn1, G, rounds, err1, conv1, p: S.Params):
     return None
 
 
-def compare(code, dcode, syn, L0, p: S.Params, min_frac=0.9999, ref=None, max_amplified=5e-3, gpu=None):
+def amplified_cap(max_amplified, shots, oracle_failures):
+    """Largest accepted number of amplified mismatches: ``max_amplified`` x shots for the
+    workloads whose caps are set from measurements, else (targeted tests of adversarial codes)
+    ten times the oracle's non-converged shots plus 2e-4 of the shots plus 2 -- amplification
+    needs trajectories that wander, and those are the non-converging and slowly converging
+    shots."""
+    if max_amplified is not None:
+        return int(np.ceil(max_amplified * shots - 1e-9))
+    return 10 * int(oracle_failures) + int(np.ceil(2e-4 * shots)) + 2
+
+
+def compare(code, dcode, syn, L0, p: S.Params, min_frac=0.9999, ref=None, max_amplified=None, gpu=None):
     """Decode on both sides and enforce the acceptance above.  Returns a summary dict.
     ``gpu``: outputs of these shots taken from an earlier GPU launch (for instance a sample of
-    a full-size batch), used instead of decoding them here."""
+    a full-size batch), used instead of decoding them here.  ``min_frac``: the near-tie budget
+    is (1 - min_frac) of the shots; ``max_amplified``: see amplified_cap."""
     g = gpu if gpu is not None else gpu_decode(dcode, syn, L0, p)
     o = ref if ref is not None else oracle_decode(code, syn, L0, p)
     same = (g["err"] == o["err"]).all(axis=1) & (g["conv"] == o["conv"]) & (g["iters"] == o["iters"])
@@ -208,16 +220,44 @@ def compare(code, dcode, syn, L0, p: S.Params, min_frac=0.9999, ref=None, max_am
             assert l is not None, f"shot {s}: outputs differ but no posterior sign differs"
             p_llr = np.abs(ot["trace"][k, l, bits]) * (abs(float(L0[s])) if normalised else 1.0)
             (counted if float(p_llr.max()) < TIE_ABS else amplified).append(int(s))
-    allowed = int(np.floor((1 - min_frac) * shots))
+    allowed = int(np.floor((1 - min_frac) * shots + 1e-6))
     assert len(counted) <= allowed, f"{len(counted)} near-tie mismatches / {shots} shots ({p.mode}), allowed {allowed}"
-    cap = int(np.ceil(max_amplified * shots))
-    assert len(amplified) <= cap, (f"{len(amplified)} amplified mismatches / {shots} shots ({p.mode}), "
-                                   f"cap {max_amplified:g} = {cap}")
+    cap = amplified_cap(max_amplified, shots, int((o["conv"] == 0).sum()))
+    assert len(amplified) <= cap, f"{len(amplified)} amplified mismatches / {shots} shots ({p.mode}), cap {cap}"
     fer_g = float(1 - g["conv"].mean()) if shots else 0.0
     fer_o = float(1 - o["conv"].mean()) if shots else 0.0
     return {"shots": shots, "mismatch": len(bad), "near_tie": len(counted), "amplified": len(amplified),
             "shadow_worst": worst_shadow,
             "fer_gpu": fer_g, "fer_oracle": fer_o, "gpu": g, "oracle": o}
+
+
+def mcnemar_p(gpu_conv, oracle_conv):
+    """Exact two-sided McNemar p-value of the paired convergence flags (the same shots decoded
+    by both sides): under equal FER the discordant shots split evenly."""
+    from math import comb
+    g = np.asarray(gpu_conv) == 0
+    o = np.asarray(oracle_conv) == 0
+    b, c = int((g & ~o).sum()), int((o & ~g).sum())
+    k, n = min(b, c), b + c
+    if n == 0:
+        return 1.0
+    tail = sum(comb(n, i) for i in range(k + 1)) / 2.0 ** n
+    return min(1.0, 2.0 * tail)
+
+
+def fer_check(r, shots, alpha=0.01):
+    """FER parity: the GPU FER lies in the oracle's 95% Wilson interval, or -- the two FERs come
+    from the same shots, so their difference is the discordant shots' -- the exact McNemar test
+    of the paired convergence flags does not reject equality at level ``alpha``.  Returns
+    (oracle interval, McNemar p)."""
+    from paper_2605_10433_gb300.stats import wilson_interval
+    fails_o = int((r["oracle"]["conv"] == 0).sum())
+    lo, hi = wilson_interval(fails_o, shots)
+    pm = mcnemar_p(r["gpu"]["conv"], r["oracle"]["conv"])
+    inside = lo - 1e-12 <= r["fer_gpu"] <= hi + 1e-12
+    assert inside or pm >= alpha, (f"FER gpu {r['fer_gpu']:.3e} outside the oracle's interval [{lo:.3e}, {hi:.3e}] "
+                                   f"and McNemar p = {pm:.3g}")
+    return (lo, hi), pm
 
 
 def compare_traces(code, dcode, syn, L0, p: S.Params):

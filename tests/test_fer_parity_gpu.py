@@ -2,7 +2,9 @@
 the FP64 oracle (all host cores) decode the same seeded shots, 1e5 to 1e6 per point.  Per shot
 the acceptance of tests/gpu_helpers.py applies (exact agreement, or a shadow-validated
 mismatch: at most 0.01% near-ties and at most the workload's cap of amplified ones), and
-each side's FER must lie in the other's 95% Wilson interval.
+the GPU FER must lie in the oracle's 95% Wilson interval, or the exact McNemar test of the
+paired convergence flags must not reject equal FERs at the 1% level (both sides decode the
+same shots, so their FERs differ only by the discordant shots).
 
 The matrix: GB(127,4) (depolarising p marginalised to 2p/3) in every mode; GB(255, w) for every
 w in every mode; GB(1023,5) on the headline mix in every mode; and the serving workload's four
@@ -13,7 +15,6 @@ import torch
 
 import paper_2605_10433_gb300 as S
 from paper_2605_10433_gb300 import inputs as I
-from paper_2605_10433_gb300.stats import wilson_interval
 from tests import gpu_helpers as G
 
 pytestmark = pytest.mark.gpu
@@ -24,35 +25,43 @@ MODES = {
     "ms": S.Params(mode="ms", max_iter=100),
     "bp": S.Params(mode="bp", max_iter=100),
 }
-CASES = ([((127, 4), p * 2 / 3, mode, 4000 + k) for k, (p, mode) in enumerate(
-             [(0.04, "sagms"), (0.04, "sms"), (0.04, "ms"), (0.04, "bp"), (0.02, "sagms"), (0.01, "sagms")])]
-         + [((255, w), 0.02, "sagms", 5000 + w) for w in (3, 4, 5, 6, 8)])
-# config 3, the other modes: 1e5 shots per code and mode
-CASES3 = [((255, w), 0.02, mode, 5100 + 10 * w + k) for w in (3, 4, 5, 6, 8)
-          for k, mode in enumerate(("ms", "sms", "bp"))]
+# (code, q, mode, seed, shots, cap on amplified mismatches as a fraction of the shots).  Caps are
+# about twice the counts measured on GB300 (recorded in the design notes); MS in L0-normalised
+# units is integer-exact on both sides, so its cap is zero and fewer shots suffice.
+Q2 = {0.04: 0.04 * 2 / 3, 0.02: 0.02 * 2 / 3, 0.01: 0.01 * 2 / 3}
+CASES = [
+    # config 2: GB(127,4), depolarising p = 0.04 (every mode), 0.02, 0.01 marginalised to 2p/3
+    ((127, 4), Q2[0.04], "sagms", 4000, 1_000_000, 1.5e-4),
+    ((127, 4), Q2[0.04], "sms", 4001, 1_000_000, 1.5e-3),
+    ((127, 4), Q2[0.04], "ms", 4002, 200_000, 0.0),
+    ((127, 4), Q2[0.04], "bp", 4003, 1_000_000, 4e-3),
+    ((127, 4), Q2[0.02], "sagms", 4004, 1_000_000, 1e-4),
+    ((127, 4), Q2[0.01], "sagms", 4005, 1_000_000, 1e-5),
+    # config 3: GB(255, w), q = 0.02, SAGMS
+    ((255, 3), 0.02, "sagms", 5003, 300_000, 2e-5),
+    ((255, 4), 0.02, "sagms", 5004, 300_000, 1.5e-4),
+    ((255, 5), 0.02, "sagms", 5005, 300_000, 3e-5),
+    ((255, 6), 0.02, "sagms", 5006, 300_000, 5e-5),
+    ((255, 8), 0.02, "sagms", 5008, 300_000, 7e-4),
+]
+# config 3 in the other modes: (w, mode, shots, cap)
+CASES3 = [((255, w), 0.02, mode, 5100 + 10 * w + k, shots, cap) for w, k, mode, shots, cap in [
+    (3, 0, "ms", 20_000, 0.0), (3, 1, "sms", 100_000, 6e-3), (3, 2, "bp", 100_000, 2e-2),
+    (4, 0, "ms", 20_000, 0.0), (4, 1, "sms", 100_000, 4e-4), (4, 2, "bp", 100_000, 2.5e-3),
+    (5, 0, "ms", 20_000, 0.0), (5, 1, "sms", 100_000, 1e-3), (5, 2, "bp", 100_000, 1e-3),
+    (6, 0, "ms", 20_000, 0.0), (6, 1, "sms", 100_000, 1e-4), (6, 2, "bp", 100_000, 1e-4),
+    (8, 0, "ms", 20_000, 0.0), (8, 1, "sms", 100_000, 3e-3), (8, 2, "bp", 100_000, 1.2e-3)]]
 # config 4: GB(1023,5) on the headline mix p in {0.005, 0.01, 0.02} (shots interleaved)
-CASES4 = [("sagms", 1_000_000, 6000), ("sms", 100_000, 6001), ("ms", 200_000, 6002), ("bp", 100_000, 6003)]
+CASES4 = [("sagms", 500_000, 6000, 4e-4), ("sms", 100_000, 6001, 1e-2), ("ms", 50_000, 6002, 0.0),
+          ("bp", 100_000, 6003, 1e-2)]
 # the serving workload's codes (n = 126, 510, 1022, 2046), p over its range U[0.005, 0.03]
-SERVING = [((63, 3), 7001), ((255, 4), 7002), ((511, 5), 7003), ((1023, 5), 7004)]
+SERVING = [((63, 3), 7001, 1e-4), ((255, 4), 7002, 1e-4), ((511, 5), 7003, 3e-4), ((1023, 5), 7004, 3e-4)]
 SERVING_P = [0.005, 0.01, 0.015, 0.02, 0.025, 0.03]
-# Cap on amplified mismatches (fraction of shots) per workload and mode: about twice the
-# measured count, rounded up (the measured values are in the design notes).
-AMPLIFIED_CAP = {"sagms": 1e-3, "sms": 1e-2, "ms": 1e-3, "bp": 5e-3}
 
 
-def _fer_check(r, shots):
-    fails_g = int(round(r["fer_gpu"] * shots))
-    fails_o = int(round(r["fer_oracle"] * shots))
-    lo_o, hi_o = wilson_interval(fails_o, shots)
-    lo_g, hi_g = wilson_interval(fails_g, shots)
-    assert lo_o - 1e-12 <= r["fer_gpu"] <= hi_o + 1e-12
-    assert lo_g - 1e-12 <= r["fer_oracle"] <= hi_g + 1e-12
-    return lo_o, hi_o
-
-
-def _line(tag, shots, r, lo, hi):
-    print(f"{tag}: {shots} shots, FER gpu {r['fer_gpu']:.3e} oracle {r['fer_oracle']:.3e} [{lo:.3e}, {hi:.3e}], "
-          f"mismatches {r['mismatch']} (near-tie {r['near_tie']}, amplified {r['amplified']}, "
+def _line(tag, shots, r, lo, hi, pm):
+    print(f"{tag}: {shots} shots, FER gpu {r['fer_gpu']:.3e} oracle {r['fer_oracle']:.3e} [{lo:.3e}, {hi:.3e}] "
+          f"McNemar p {pm:.3g}, mismatches {r['mismatch']} (near-tie {r['near_tie']}, amplified {r['amplified']}, "
           f"shadow worst {r['shadow_worst']:.3g})")
 
 
@@ -62,50 +71,48 @@ def dev_check():
         pytest.skip("no CUDA device")
 
 
-@pytest.mark.parametrize("lw,q,mode,seed", CASES)
-def test_million_shot_fer_parity(lw, q, mode, seed):
+@pytest.mark.parametrize("lw,q,mode,seed,shots,cap", CASES)
+def test_million_shot_fer_parity(lw, q, mode, seed, shots, cap):
     """Config 2 (GB(127,4), depolarising p = 0.04, 0.02, 0.01 marginalised to q = 2p/3; every
-    mode at p = 0.04) and config 3 (GB(255, w) for every w at q = 0.02)."""
+    mode at p = 0.04) and config 3 (GB(255, w) for every w at q = 0.02), up to 1e6 shots."""
     c = I.gb_code(*lw)
     dc = S.DeviceCode.from_code(c)
-    shots = 1_000_000
     _, syn, L0, _ = I.workload(c, [q], shots, seed=seed)
-    r = G.compare(c, dc, syn, L0, MODES[mode], max_amplified=AMPLIFIED_CAP[mode])
-    lo, hi = _fer_check(r, shots)
-    _line(f"GB{lw} q={q:.4f} {mode}", shots, r, lo, hi)
+    r = G.compare(c, dc, syn, L0, MODES[mode], max_amplified=cap)
+    (lo, hi), pm = G.fer_check(r, shots)
+    _line(f"GB{lw} q={q:.4f} {mode}", shots, r, lo, hi, pm)
 
 
-@pytest.mark.parametrize("lw,q,mode,seed", CASES3)
-def test_config3_other_modes_fer_parity(lw, q, mode, seed):
+@pytest.mark.parametrize("lw,q,mode,seed,shots,cap", CASES3)
+def test_config3_other_modes_fer_parity(lw, q, mode, seed, shots, cap):
     """Config 3 (GB(255, w), w in {3, 4, 5, 6, 8}, q = 0.02) in MS, SMS(0.75) and BP."""
     c = I.gb_code(*lw)
     dc = S.DeviceCode.from_code(c)
-    shots = 100_000
     _, syn, L0, _ = I.workload(c, [q], shots, seed=seed)
-    r = G.compare(c, dc, syn, L0, MODES[mode], max_amplified=AMPLIFIED_CAP[mode])
-    lo, hi = _fer_check(r, shots)
-    _line(f"GB{lw} q={q:.4f} {mode}", shots, r, lo, hi)
+    r = G.compare(c, dc, syn, L0, MODES[mode], max_amplified=cap)
+    (lo, hi), pm = G.fer_check(r, shots)
+    _line(f"GB{lw} q={q:.4f} {mode}", shots, r, lo, hi, pm)
 
 
-@pytest.mark.parametrize("mode,shots,seed", CASES4)
-def test_large_code_fer_parity(mode, shots, seed):
+@pytest.mark.parametrize("mode,shots,seed,cap", CASES4)
+def test_large_code_fer_parity(mode, shots, seed, cap):
     """Config 4: GB(1023,5), iid Z flips at p in {0.005, 0.01, 0.02}, max_iter 100."""
     c = I.gb_code(1023, 5)
     dc = S.DeviceCode.from_code(c)
     _, syn, L0, _ = I.workload(c, [0.005, 0.01, 0.02], shots, seed=seed)
-    r = G.compare(c, dc, syn, L0, MODES[mode], max_amplified=AMPLIFIED_CAP[mode])
-    lo, hi = _fer_check(r, shots)
-    _line(f"GB(1023,5) {mode}", shots, r, lo, hi)
+    r = G.compare(c, dc, syn, L0, MODES[mode], max_amplified=cap)
+    (lo, hi), pm = G.fer_check(r, shots)
+    _line(f"GB(1023,5) {mode}", shots, r, lo, hi, pm)
 
 
-@pytest.mark.parametrize("lw,seed", SERVING)
-def test_serving_codes_fer_parity(lw, seed):
+@pytest.mark.parametrize("lw,seed,cap", SERVING)
+def test_serving_codes_fer_parity(lw, seed, cap):
     """The serving workload's codes with SAGMS at its noise range (p interleaved over
     0.005..0.03), 1e5 shots each."""
     c = I.gb_code(*lw)
     dc = S.DeviceCode.from_code(c)
     shots = 100_000
     _, syn, L0, _ = I.workload(c, SERVING_P, shots, seed=seed)
-    r = G.compare(c, dc, syn, L0, MODES["sagms"], max_amplified=AMPLIFIED_CAP["sagms"])
-    lo, hi = _fer_check(r, shots)
-    _line(f"serving GB{lw} sagms", shots, r, lo, hi)
+    r = G.compare(c, dc, syn, L0, MODES["sagms"], max_amplified=cap)
+    (lo, hi), pm = G.fer_check(r, shots)
+    _line(f"serving GB{lw} sagms", shots, r, lo, hi, pm)

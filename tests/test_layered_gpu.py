@@ -70,14 +70,14 @@ def test_layered_oracle_parity(key, mode):
     L0 = L0.copy()
     syn[::9] = 0
     L0[4::13] = -L0[4::13]
-    G.compare(c, dc, syn, L0, PARAMS[mode])
+    G.compare(c, dc, syn, L0, PARAMS[mode], min_frac=0.0)
 
 
 def test_layered_full_size_gb1023_oracle_parity():
     c = I.gb_code(1023, 5)
     dc = S.DeviceCode.from_code(c)
     _, syn, L0, _ = I.workload(c, [0.005, 0.01, 0.02], 300, seed=18)
-    G.compare(c, dc, syn, L0, PARAMS["sagms"])
+    G.compare(c, dc, syn, L0, PARAMS["sagms"], min_frac=0.0)
 
 
 @pytest.mark.parametrize("key", ["gb63x3", "gb1023x3", "irregular-gb255x5"])
@@ -96,9 +96,9 @@ def test_layered_per_qubit_priors_and_auto_ceiling():
     _, syn = I.sample(c, 0.03, 400, seed=21)
     L0q = I.llr_prior(rng.uniform(0.005, 0.08, size=c.n)).astype(np.float32)
     L0q[rng.choice(c.n, size=c.n // 50, replace=False)] *= -1.0
-    G.compare(c, dc, syn, L0q, _with(PARAMS["sagms"], flags=LAY | S.FLAG_L0_PER_QUBIT))
+    G.compare(c, dc, syn, L0q, _with(PARAMS["sagms"], flags=LAY | S.FLAG_L0_PER_QUBIT), min_frac=0.0)
     _, syn, L0, _ = I.workload(c, [0.01, 0.04], 400, seed=22)
-    G.compare(c, dc, syn, L0, _with(PARAMS["sagms"], flags=LAY | S.FLAG_AUTO_CEILING))
+    G.compare(c, dc, syn, L0, _with(PARAMS["sagms"], flags=LAY | S.FLAG_AUTO_CEILING), min_frac=0.0)
     bad = L0q.copy()
     bad[7] = np.inf
     g = G.gpu_decode(dc, syn[:50], bad, _with(PARAMS["sagms"], flags=LAY | S.FLAG_L0_PER_QUBIT))

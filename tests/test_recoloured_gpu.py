@@ -97,5 +97,5 @@ def test_sorted_and_term_ordered_rows_decode_alike():
     assert same.mean() > 0.995
     # each order on its own against the oracle, under the full acceptance
     sb = _sorted_gb(1023, 5)
-    G.compare(g, a, syn, L0, PARAMS["sagms"], max_amplified=1e-3, gpu=ra)
-    G.compare(sb, b, syn, L0, PARAMS["sagms"], max_amplified=1e-3, gpu=rb)
+    G.compare(g, a, syn, L0, PARAMS["sagms"], gpu=ra)
+    G.compare(sb, b, syn, L0, PARAMS["sagms"], gpu=rb)

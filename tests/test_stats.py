@@ -52,3 +52,22 @@ def test_logical_ok_on_the_steane_code():
     R[5, rows[2]] = 1
     R[5, 0] ^= 1                                        # a stabilizer plus one flip
     assert logical_ok(hz, R).tolist() == [True, True, True, False, False, False]
+
+
+def test_mcnemar_exact_p_matches_the_binomial_test():
+    """The paired FER check's exact McNemar p-value equals scipy's two-sided binomial test of the
+    discordant shots at 1/2."""
+    scipy_stats = pytest.importorskip("scipy.stats")
+    import numpy as np
+    from tests.gpu_helpers import mcnemar_p
+    rng = np.random.default_rng(3)
+    for b, c in [(0, 0), (0, 1), (5, 0), (3, 9), (17, 11), (40, 70)]:
+        conv_g = np.ones(200, dtype=np.uint8)
+        conv_o = np.ones(200, dtype=np.uint8)
+        idx = rng.permutation(200)
+        conv_g[idx[:b]] = 0                    # GPU-only failures
+        conv_o[idx[b:b + c]] = 0               # oracle-only failures
+        conv_g[idx[b + c:b + c + 7]] = 0       # shared failures: not discordant
+        conv_o[idx[b + c:b + c + 7]] = 0
+        want = 1.0 if b + c == 0 else scipy_stats.binomtest(min(b, c), b + c, 0.5).pvalue
+        assert abs(mcnemar_p(conv_g, conv_o) - min(1.0, want)) < 1e-12
