@@ -42,7 +42,7 @@ MAX_ITER = 100
 NOISE_SEED = 20260513
 PROFILE = os.path.join(ROOT, "profiles", "qc_kernel_gb1023_sagms.md")
 KERNEL_SRC = [os.path.join(ROOT, "paper_2605_10433_gb300", "csrc", f)
-              for f in ("decode_qc.cuh", "decode_groups.cuh", "decode_slots.cuh", "decode_kernel.cuh")]
+              for f in ("decode_qc.cuh", "decode_groups.cuh", "decode_slots.cuh", "decode_kernel.cuh", "tmem.cuh")]
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -221,7 +221,8 @@ def bench_serving(S, I, nreq=3000, load=0.6, seed=5):
     (w = 3/4/5/5), batch size floor(exp U[ln 1, ln 4096]), p ~ U[0.005, 0.03], SAGMS
     max_iter=100.  Plain per-request launches (one stream, one request at a time) give the
     capacity; the same arrival schedule at `load` x that capacity is then replayed through the
-    continuous-batching server and through plain launches.  Latency = completion - submit,
+    continuous-batching server and through plain launches.  A sweep replays it at 30, 60, 80 and
+    95% of the continuous mode's own capacity (all requests at once) in both modes.  Latency = completion - submit,
     measured by the server's clock, host copies included."""
     import torch
     rng = np.random.default_rng(seed)
@@ -267,17 +268,120 @@ def bench_serving(S, I, nreq=3000, load=0.6, seed=5):
     burst = np.zeros(nreq, dtype=np.int64)
     run("plain", burst)   # warm-up
     cap = run("plain", burst)["shots_per_s"]
-    rate_req = load * cap / shots.mean()
-    arrival = np.cumsum(rng.exponential(1.0 / rate_req, size=nreq)) * 1e9
-    arrival = (arrival - arrival[0]).astype(np.int64)
+    run("continuous", burst)   # warm-up
+    cap_cont = run("continuous", burst)["shots_per_s"]
+    gaps = rng.exponential(1.0, size=nreq)   # one Poisson schedule, rescaled to each offered rate
+
+    def schedule(rate_shots):
+        rate_req = rate_shots / shots.mean()
+        arrival = np.cumsum(gaps / rate_req) * 1e9
+        return (arrival - arrival[0]).astype(np.int64)
+
+    arrival = schedule(load * cap)
     cont = run("continuous", arrival)
     plain = run("plain", arrival)
+    # the same schedule at fractions of the continuous mode's own capacity, both modes
+    sweep = []
+    for f in (0.3, 0.6, 0.8, 0.95):
+        arr = schedule(f * cap_cont)
+        c, pl = run("continuous", arr), run("plain", arr)
+        sweep.append({"load_of_continuous_capacity": f, "offered_shots_per_s": f * cap_cont,
+                      "continuous": c, "plain": pl, "p99_speedup_vs_plain": pl["p99_us"] / c["p99_us"]})
     return {"workload": f"{nreq} Poisson requests, GB n in {{126,510,1022,2046}}, batch floor(exp U[ln1,ln4096]) "
                         f"(mean {shots.mean():.0f} shots), p~U[0.005,0.03], SAGMS max_iter=100, "
                         f"offered load {load:.0%} of plain-launch capacity",
-            "plain_capacity_shots_per_s": cap, "offered_shots_per_s": rate_req * shots.mean(),
+            "plain_capacity_shots_per_s": cap, "continuous_capacity_shots_per_s": cap_cont,
+            "offered_shots_per_s": load * cap,
             "continuous": cont, "plain": plain,
-            "p99_speedup_vs_plain": plain["p99_us"] / cont["p99_us"]}
+            "p99_speedup_vs_plain": plain["p99_us"] / cont["p99_us"], "sweep": sweep}
+
+
+def bench_gf4(S, I, steps, shots=1_000_000):
+    """The paper's own decoding setting (Sec. II, Sec. V): GF(4) decoding of the overcomplete CSS
+    matrix of a GB code with l = 63, w = 5 (m = 126 rows, check and qubit degree 10) under
+    depolarising noise at eps = 0.01; SAGMS (0.30, 0.50, 1.10), SMS(0.5) and BP4 with the matched
+    prior (eps0 = eps) and SAGMS / BP4 with the mismatched one (eps0 = 0.1): shots/s and FER."""
+    import torch
+    from paper_2605_10433_gb300.inputs import gf4 as I4
+    g = I4.css_code(I.gb_code(63, 5))
+    dc = S.Gf4DeviceCode(g)
+    eps = 0.01
+    _, _, syn = I4.depolarizing(g, eps, shots, seed=NOISE_SEED + 4)
+    d_syn = torch.from_numpy(syn.view(np.int32)).cuda()
+    out = {"workload": f"CSS stack of GB l=63 w=5 ([[126,{g.k}]], m=126, d_c=d_v=10), depolarising eps={eps}, "
+                       f"{shots:.0e} shots, max_iter={MAX_ITER}, GF(4) scalar messages"}
+    runs = [("sagms", S.Params(mode="sagms", max_iter=MAX_ITER, **SAGMS_KW), eps),
+            ("sms", S.Params(mode="sms", alpha=0.5, max_iter=MAX_ITER), eps),
+            ("bp4", S.Params(mode="bp", max_iter=MAX_ITER), eps),
+            ("sagms_mismatch", S.Params(mode="sagms", max_iter=MAX_ITER, **SAGMS_KW), 0.1),
+            ("bp4_mismatch", S.Params(mode="bp", max_iter=MAX_ITER), 0.1)]
+    stream = torch.cuda.current_stream()
+    for name, p, eps0 in runs:
+        d_L0 = torch.full((shots,), float(I4.prior(eps0)), dtype=torch.float32, device="cuda")
+        S.gf4_decode(dc, d_syn, d_L0, p, stream=stream)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            _, conv, iters = S.gf4_decode(dc, d_syn, d_L0, p, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"eps0": eps0, "shots_per_s": shots / (ms / 1e3), "fer_syn": float((conv == 0).float().mean()),
+                     "mean_iters": float(iters.float().mean())}
+    dc.close()
+    return out
+
+
+def classify_mismatches(S, code, dcode, syn, L0, params, g_err, g_conv, g_it, o):
+    """Per-shot decision parity of the GPU batch against the FP64 oracle on the same shots,
+    with the acceptance of the parity tests: every mismatching shot is re-decoded on the GPU
+    with its posterior trace and replayed by the oracle's shadow check (each round re-done in
+    FP64 from the GPU's own previous posteriors must land within the binary32 rounding bound);
+    it is a near-tie when the first differing decision has an oracle posterior |LLR| < 1e-4,
+    else amplified.  Returns the counts."""
+    import oracle
+    import torch
+    mode = {"ms": oracle.MS, "sms": oracle.SMS, "sagms": oracle.SAGMS, "bp": oracle.BP}[params.mode]
+    kw = dict(mode=mode, alpha=params.alpha, alpha_min=params.alpha_min, alpha_max=params.alpha_max,
+              eta_unsat=params.eta_unsat, flags=params.flags)
+    same = (g_err == o["err"]).all(axis=1) & (g_conv == o["conv"]) & (g_it == o["iters"])
+    bad = np.nonzero(~same)[0]
+    near, amp, shadow_fail, worst = 0, 0, 0, 0.0
+    n = code.n
+    for c0 in range(0, len(bad), 64):
+        idx = bad[c0:c0 + 64]
+        d_syn = torch.from_numpy(np.ascontiguousarray(syn[idx]).view(np.int32)).cuda()
+        d_L0 = torch.from_numpy(np.ascontiguousarray(L0[idx])).cuda()
+        _, _, it_t, tr = S.decode(dcode, d_syn, d_L0, params, trace=True)
+        torch.cuda.synchronize()
+        it_t, tr = it_t.cpu().numpy(), tr.cpu().numpy()
+        ot = oracle.decode_code(code, syn[idx], L0[idx].astype(np.float64), max_iter=params.max_iter, trace=True,
+                                threads=os.cpu_count() or 1, **{k: v for k, v in kw.items()})
+        for k, s in enumerate(idx):
+            rounds = int(it_t[k])
+            dev, bnd, _ = oracle.shadow_code(code, syn[s], L0[s:s + 1], tr[k], rounds, **kw)
+            with np.errstate(divide="ignore", invalid="ignore"):
+                ratio = float(np.max(np.where(dev == 0.0, 0.0, np.abs(dev) / bnd)))
+            worst = max(worst, ratio)
+            if ratio > 1.0 or rounds != int(g_it[s]):
+                shadow_fail += 1
+                continue
+            last = min(rounds, int(ot["iters"][k]))
+            for l in range(last + 1):
+                diff = np.signbit(tr[k, l, :n]) != (ot["trace"][k, l, :n] < 0)
+                if diff.any():
+                    scale = abs(float(L0[s])) if params.mode != "bp" else 1.0
+                    if float(np.abs(ot["trace"][k, l, :n][diff]).max()) * scale < 1e-4:
+                        near += 1
+                    else:
+                        amp += 1
+                    break
+    shots = len(same)
+    return {"shots": shots, "identical": int(same.sum()), "identical_frac": float(same.mean()),
+            "near_tie": near, "near_tie_frac": near / shots, "amplified": amp, "amplified_frac": amp / shots,
+            "shadow_failures": shadow_fail, "shadow_worst": worst}
 
 
 def cpu_oracle_sample(code, syn, L0, shots, threads):
@@ -330,7 +434,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--shots", type=int, default=10_000_000)
     ap.add_argument("--ref-sample", type=int, default=40000)
-    ap.add_argument("--cpu-sample", type=int, default=40000)
+    ap.add_argument("--cpu-sample", type=int, default=100000)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--mode-steps", type=int, default=3)
     ap.add_argument("--no-extras", action="store_true",
@@ -428,12 +532,14 @@ def main():
                      f"{roofline.hbm_bytes_per_shot(code.m, code.n)} B/shot at "
                      f"{peaks.get('hbm_gbs', 'n/a')} GB/s is "
                      f"{(peaks.get('hbm_gbs', 6793.1) * 1e9 / roofline.hbm_bytes_per_shot(code.m, code.n)):.3g} shots/s")}
-    smem_b = roofline.smem_bytes(it_host, code.nnz, code.n)
+    tmem = "qc_tmem=1" in S._native.sagms_version() and args.mode != "bp" and not args.layered
+    smem_b = roofline.smem_bytes(it_host, code.nnz, code.n, old_in_smem=not tmem)
     smem_peak = roofline.smem_peak_bytes(props.multi_processor_count, sm_max)
     roof_smem = {"bound": "smem", "achieved": smem_b / (ms_step / 1e3) / 1e9, "peak": smem_peak / 1e9, "unit": "GB/s",
                  "frac": smem_b / (ms_step / 1e3) / smem_peak,
-                 "note": ("diagnostic roof: on-chip bytes of the flooding schedule (16E r - 4E + 4n r per shot of r "
-                          "iterations) over SMs x 128 B x clock (derived)")}
+                 "note": ("diagnostic roof: shared-memory bytes of the flooding schedule per shot of r iterations "
+                          + ("(12E r + 4n r: old messages in tensor memory)" if tmem else "(16E r - 4E + 4n r)")
+                          + " over SMs x 128 B x clock (derived)")}
 
     fer = {}
     for k, p in enumerate(P_VALUES):
@@ -483,8 +589,13 @@ def main():
                                                    max_iter=MAX_ITER, flags=S.FLAG_LAYERED))):
             m_ms, _ = timed(p, 1, args.mode_steps)
             cv = conv.cpu().numpy()
+            it_m = iters.cpu().numpy()
+            ops_m = roofline.ops_per_iteration(p.mode, code.row_ptr, code.col_idx, code.n)
+            t_m = m_ms / 1e3 / args.mode_steps
             modes[name] = {"shots_per_s": shots * world * args.mode_steps / (m_ms / 1e3),
-                           "mean_iters": float(iters.cpu().numpy().mean()), "fer_syn": float((cv == 0).mean())}
+                           "mean_iters": float(it_m.mean()), "fer_syn": float((cv == 0).mean()),
+                           "roofline_frac": float(it_m.astype(np.int64).sum()) * ops_m / t_m / peak,
+                           "ops_per_iteration": ops_m}
         out["modes"] = modes
         step(sagms)
         torch.cuda.synchronize()
@@ -518,16 +629,18 @@ def main():
             out["config3_mixed_degree"] = bench_mixed_degree(S, I, args.mode_steps)
             out["serving"] = bench_serving(S, I)
             out["monte_carlo"] = bench_mc(S, I)
+            out["gf4"] = bench_gf4(S, I, args.mode_steps)
 
     if rank == 0 and world == 1 and not args.no_extras:
         threads = os.cpu_count() or 1
         r, dt = cpu_oracle_sample(code, syn, L0, args.cpu_sample, threads)
-        g_err = err.cpu().numpy().view(np.uint32)[:args.cpu_sample]
-        same = ((g_err == r["err"]).all(axis=1) & (it_host[:args.cpu_sample] == r["iters"])).mean()
-        out["cpu_baseline"] = {"value": args.cpu_sample / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-                               "sample": f"first {args.cpu_sample} shots of the same batch (FP64 C oracle, "
-                                         f"{threads} threads)",
-                               "oracle_fer_syn": float((r["conv"] == 0).mean()), "gpu_oracle_identical": same}
+        cs = args.cpu_sample
+        parity = classify_mismatches(S, code, dcode, syn[:cs], L0[:cs], sagms, err.cpu().numpy().view(np.uint32)[:cs],
+                                     conv_host[:cs], it_host[:cs], r)
+        out["cpu_baseline"] = {"value": cs / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+                               "sample": f"first {cs} shots of the same batch (FP64 C oracle, {threads} threads)",
+                               "oracle_fer_syn": float((r["conv"] == 0).mean()),
+                               "gpu_oracle_identical": parity["identical_frac"], "decision_parity": parity}
         one = max(1, args.cpu_sample // 16)
         _, dt1 = cpu_oracle_sample(code, syn, L0, one, 1)
         out["cpu_baseline"]["single_thread"] = {"value": one / dt1, "unit": UNIT, "cores": 1,

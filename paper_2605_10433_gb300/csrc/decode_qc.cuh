@@ -32,6 +32,11 @@
 #pragma once
 
 #include "decode_groups.cuh"
+#include "tmem.cuh"
+
+#ifndef SAGMS_QC_TMEM
+#define SAGMS_QC_TMEM 1
+#endif
 
 namespace sagms {
 
@@ -54,6 +59,11 @@ struct QcShape {
     static constexpr size_t PQS = SMEM;
     static constexpr size_t NEGW = PQS + (size_t)(NP + 4) * 4;
     static constexpr size_t SMEM_PQ = NEGW + (size_t)(NP / 32) * 4;
+    // Check threads keep their outgoing messages in tensor memory too (tmem.cuh): the shapes
+    // with four checks of ten slots per thread in 256-thread groups, one CTA per SM (40 of the
+    // 64 columns a warp's lane row gets; 4 warps per lane quadrant, 256 columns per CTA).
+    static constexpr bool TM = SAGMS_QC_TMEM != 0 && DC == 10 && K == 4 && T == 256;
+    static constexpr uint32_t TM_COLS = 256, TM_WARP_COLS = 64;
     static_assert(DC == 2 * DV && (K == 2 || K == 4) && NG * T == kQcThreads, "shape");
     static_assert(NP % (2 * T) == 0 && MC <= 1024 && (T == 32 || NG <= 15), "layout");
 };
@@ -74,10 +84,17 @@ __device__ __forceinline__ uint32_t qc_byte(uint32_t x, int k) { return (x >> (8
 // group address an immediate), or -1 (one copy for all groups, g at run time).  PQ: one prior
 // per qubit shared by all shots (SAGMS_FLAG_L0_PER_QUBIT; LLR units), pq_ok = all finite.
 // BPK: the BP rule of Eq. 3 (per-shot priors in LLR units) instead of the MS family.
+// tm: the thread's tensor-memory address (its lane, its warp's columns) when S::TM and !BPK: the
+// check thread's outgoing messages are kept there as well as in C_g, and the next round reads its
+// old messages from there.  Checks 2p and 2p + 1 share columns 2p DC .. 2p DC + 2 DC - 1, slot j
+// of check 2p + h at column 2p DC + 2j + h, so each loaded pair lands in adjacent registers as
+// the FP32x2 operand of the input sums.
 template <class S, bool AUTO, bool PQ, int GC, bool BPK>
 __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* smem, const int tg, const int g_rt,
-                                         const uint32_t (&off)[S::K][S::DC], const uint32_t degs, const bool pq_ok) {
+                                         const uint32_t (&off)[S::K][S::DC], const uint32_t degs, const bool pq_ok,
+                                         const uint32_t tm) {
     constexpr int DC = S::DC, DV = S::DV, K = S::K, T = S::T, NP = S::NP;
+    constexpr bool TM = S::TM && !BPK;
     const int g = GC >= 0 ? GC : g_rt;
     const size_t PO = (size_t)g * S::GROUP;
     const bool early = (a.flags & kFlagNoEarlyStop) == 0;
@@ -292,6 +309,7 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
                 // edge, and every real edge gets the second-minimum output (|v_j| = m1).
                 const uint32_t sgn = __float_as_uint(prior) & kSign;
                 const float ms = fabsf(prior);
+                uint32_t dk[K];
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
                     const uint32_t deg = qc_byte(degs, k);
@@ -301,6 +319,10 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
                     const float d = __uint_as_float(__float_as_uint(o2) ^ (~__float_as_uint(prior) & kSign));
 #pragma unroll
                     for (int j = 0; j < DC; ++j) Cat(j, off[k][j]) = d;
+                    if constexpr (TM) {
+                        dk[k] = __float_as_uint(d);
+                        if (k & 1) tmem_st20_alt(tm + (uint32_t)((k - 1) * DC), dk[k - 1], dk[k]);
+                    }
                 }
             } else {
                 if (PQ && fresh) {
@@ -315,9 +337,18 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
                     // A3 check-node update for checks 2p and 2p + 1 (C holds negated
                     // messages: P - L = P + D; a fresh shot has no old messages)
                     if (!(PQ && fresh)) {
+                        if constexpr (TM) {
+                            uint32_t o[2 * DC];
+                            __syncwarp();
+                            tmem_ld20(tm + (uint32_t)(2 * p * DC), o);
 #pragma unroll
-                        for (int j = 0; j < DC; ++j)
-                            v[p][j] = add2(v[p][j], make_float2(Cat(j, off[2 * p][j]), Cat(j, off[2 * p + 1][j])));
+                            for (int j = 0; j < DC; ++j)
+                                v[p][j] = add2(v[p][j], make_float2(__uint_as_float(o[2 * j]), __uint_as_float(o[2 * j + 1])));
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < DC; ++j)
+                                v[p][j] = add2(v[p][j], make_float2(Cat(j, off[2 * p][j]), Cat(j, off[2 * p + 1][j])));
+                        }
                     }
                     uint32_t par0 = ((sbits >> (2 * p)) & 1u) << 31, par1 = ((sbits >> (2 * p + 1)) & 1u) << 31;
 #pragma unroll
@@ -365,6 +396,7 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
                         // compare and select per edge and a short dependency chain.  (Shapes
                         // where the values do not fit the register budget keep the selection.)
                         constexpr int NPR = DC / 2;
+                        uint32_t wvp[2][DC];   // both checks' outputs, for the interleaved store
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             const uint32_t par = h ? par1 : par0;
@@ -378,6 +410,7 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
 #pragma unroll
                             for (int i = NPR - 2; i >= 0; --i) sp[i] = min(sp[i + 1], pm[i + 1]);
                             uint32_t pre = 0u;
+                            uint32_t wv[DC];
 #pragma unroll
                             for (int i = 0; i < NPR; ++i) {
                                 const uint32_t o0 = i ? __vimin3_u32(x[2 * i + 1], pre, sp[i]) : min(x[1], sp[0]);
@@ -385,9 +418,19 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
                                 pre = i ? min(pre, pm[i]) : pm[0];
                                 const uint32_t b0 = __float_as_uint(h ? v[p][2 * i].y : v[p][2 * i].x);
                                 const uint32_t b1 = __float_as_uint(h ? v[p][2 * i + 1].y : v[p][2 * i + 1].x);
-                                Cat(2 * i, off[2 * p + h][2 * i]) = __uint_as_float(o0 ^ (~b0 & kSign));
-                                Cat(2 * i + 1, off[2 * p + h][2 * i + 1]) = __uint_as_float(o1 ^ (~b1 & kSign));
+                                wv[2 * i] = o0 ^ (~b0 & kSign);
+                                wv[2 * i + 1] = o1 ^ (~b1 & kSign);
+                                Cat(2 * i, off[2 * p + h][2 * i]) = __uint_as_float(wv[2 * i]);
+                                Cat(2 * i + 1, off[2 * p + h][2 * i + 1]) = __uint_as_float(wv[2 * i + 1]);
                             }
+#pragma unroll
+                            for (int j = 0; j < DC; ++j) wvp[h][j] = wv[j];
+                        }
+                        if constexpr (TM) {
+                            uint32_t il[2 * DC];
+#pragma unroll
+                            for (int j = 0; j < DC; ++j) { il[2 * j] = wvp[0][j]; il[2 * j + 1] = wvp[1][j]; }
+                            tmem_st20(tm + (uint32_t)(2 * p * DC), il);
                         }
                     } else {
                         // Smallest and second smallest |v|, two edges at a time:
@@ -418,6 +461,7 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
                     }
                 }
             }
+            if constexpr (TM) tmem_wait_st();   // this round's stores land before the next reads
         }
         qc_sync<T, GC>(g);
 
@@ -459,9 +503,17 @@ __global__ void __launch_bounds__(kQcThreads, S::K * S::DC <= 12 ? 2 : 1)
 qc_kernel(const DecodeArgs a, const uint32_t* __restrict__ colQ) {
     constexpr int DC = S::DC, K = S::K, T = S::T;
     extern __shared__ __align__(16) unsigned char smem[];
+    constexpr bool TMK = S::TM && !BPK;
+    __shared__ uint32_t tm_slot;
     const int t = threadIdx.x;
     const int g = t / T;
     const int tg = t % T;
+    // Tensor memory for the check threads' messages: warp 0 allocates the CTA's columns; the
+    // barrier after the zeroing below publishes the base (fenced on both sides).
+    if constexpr (TMK) {
+        if (t < 32) tmem_alloc(&tm_slot, S::TM_COLS);
+        tmem_fence_before();
+    }
     const float inf = __uint_as_float(0x7f800000u);
     uint32_t off[K][DC];
     uint32_t degs = 0;
@@ -523,11 +575,25 @@ qc_kernel(const DecodeArgs a, const uint32_t* __restrict__ colQ) {
         }
     }
     pq_ok = __syncthreads_and(pq_ok);
+    uint32_t tm = 0;
+    if constexpr (TMK) {
+        tmem_fence_after();
+        const int w = t >> 5;
+        tm = tm_slot + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(w >> 2) * S::TM_WARP_COLS;
+    }
     if constexpr (S::NG == 2) {
-        if (g == 0) qc_group<S, AUTO, PQ, 0, BPK>(a, smem, tg, g, off, degs, pq_ok != 0);
-        else qc_group<S, AUTO, PQ, 1, BPK>(a, smem, tg, g, off, degs, pq_ok != 0);
+        if (g == 0) qc_group<S, AUTO, PQ, 0, BPK>(a, smem, tg, g, off, degs, pq_ok != 0, tm);
+        else qc_group<S, AUTO, PQ, 1, BPK>(a, smem, tg, g, off, degs, pq_ok != 0, tm);
     } else {
-        qc_group<S, AUTO, PQ, -1, BPK>(a, smem, tg, g, off, degs, pq_ok != 0);
+        qc_group<S, AUTO, PQ, -1, BPK>(a, smem, tg, g, off, degs, pq_ok != 0, tm);
+    }
+    if constexpr (TMK) {
+        // every tensor-memory access of the CTA has completed (each load and each round's
+        // stores were waited for); warp 0 releases the columns
+        tmem_fence_before();
+        __syncthreads();
+        tmem_fence_after();
+        if (t < 32) tmem_dealloc(tm_slot, S::TM_COLS);
     }
 }
 

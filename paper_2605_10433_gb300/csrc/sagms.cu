@@ -415,8 +415,9 @@ const char* sagms_version(void) {
     static std::once_flag once;
     std::call_once(once, [] {
         snprintf(buf, sizeof(buf),
-                 "libsagms 0.1 sm_103a; msfam_clip=%g bp_clip=%g max_dc=%d max_dv=%d max_m=%d",
-                 (double)kMsFamClip, (double)kBpClip, SAGMS_MAX_DC, SAGMS_MAX_DV, SAGMS_MAX_M);
+                 "libsagms 0.1 sm_103a; msfam_clip=%g bp_clip=%g max_dc=%d max_dv=%d max_m=%d qc_tmem=%d",
+                 (double)kMsFamClip, (double)kBpClip, SAGMS_MAX_DC, SAGMS_MAX_DV, SAGMS_MAX_M,
+                 sagms::QcShape<10, 5, 4, 256, 2048>::TM ? 1 : 0);
     });
     return buf;
 }

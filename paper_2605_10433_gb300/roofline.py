@@ -43,15 +43,19 @@ def alu_peak_ops(sms: int, sm_mhz: float) -> float:
 SMEM_BYTES_PER_SM_CLK = 128  # shared-memory pipe: one 128-byte wavefront per clock per SM
 
 
-def smem_bytes(iters, edges: int, n: int) -> float:
-    """On-chip bytes of the flooding schedule with messages held in shared memory, summed
-    over shots.  A shot with r >= 1 iterations reads P_j for each of its r residual checks
-    (4E per check; rounds 2..r take their check-node inputs from the same read), reads
-    L_old (4E) in rounds 2..r (round 1 starts from zero messages), writes L_new (4E) and
-    reads it back in the variable-node sum (4E) in every round, and writes P (4n) in every
-    round: 16E r - 4E + 4n r bytes.  A shot stopped at its first check (r = 0) moves none."""
+def smem_bytes(iters, edges: int, n: int, old_in_smem: bool = True) -> float:
+    """Shared-memory bytes of the flooding schedule, summed over shots.  A shot with r >= 1
+    iterations reads P_j for each of its r residual checks (4E per check; rounds 2..r take
+    their check-node inputs from the same read), writes L_new (4E) and reads it back in the
+    variable-node sum (4E) in every round, and writes P (4n) in every round.  With the check
+    threads' old messages in shared memory it also reads L_old (4E) in rounds 2..r (round 1
+    starts from zero messages): 16E r - 4E + 4n r bytes; with them in tensor memory (the
+    headline kernel shape) that read leaves shared memory: 12E r + 4n r.  A shot stopped at its
+    first check (r = 0) moves none."""
     r = np.asarray(iters, dtype=np.int64)
     r = r[r > 0]
+    if not old_in_smem:
+        return float((12 * edges + 4 * n) * r.sum())
     return float((16 * edges + 4 * n) * r.sum() - 4 * edges * r.size)
 
 
