@@ -443,6 +443,46 @@ int sagms_mc_run(const sagms_code* code, const sagms_params* params, uint64_t se
                  int64_t target_failures, int64_t max_shots, int64_t batch, sagms_mc_counts* counts);
 
 /* Message of the last failure on the calling thread ("" if none). */
+/*
+ * Quaternary (GF(4)) decoding (Sec. II; Fig. 2b, Fig. 3 experiments): BP4 and the Min-Sum family
+ * on a stabilizer matrix H in GF(4)^{m x n} whose entries are Paulis, with scalar messages
+ * (the scalarisation the paper takes from its ref. [Lai_2021]).
+ *   - Each qubit holds per-Pauli LLRs Lambda(W) = ln P(I)/P(W), W in {X, Z, Y}, starting at the
+ *     prior L0 = ln((1 - eps0) / (eps0/3)); a CN message counts toward Lambda(W) exactly when W
+ *     anticommutes with the edge's entry (Eq. 2 read per Pauli).
+ *   - The VN->CN message of an edge with entry T is the LLR that the qubit's error commutes with
+ *     T: ln(1 + e^{-Lambda'(T)}) - ln(e^{-Lambda'(T')} + e^{-Lambda'(T'')}) over the extrinsic
+ *     Lambda' (T', T'' the Paulis anticommuting with T).
+ *   - The CN update is the binary rule of Eq. 3 (BP4) or Eqs. 4 / 8 (MS, SMS, SAGMS, gains of
+ *     Eqs. 6-7 from the residual of Eq. 1 over GF(4)); decision (Algorithm 1): the argmin of
+ *     (0, Lambda(X), Lambda(Z), Lambda(Y)), ties to I, X, Z, Y.  LLR units; clips as sagms_decode.
+ *
+ * sagms_gf4_load_code: H in CSR (host arrays, copied): row_ptr[m+1], col_idx[nnz], pauli[nnz]
+ * with 1 = X, 2 = Z, 3 = Y (the symplectic bits x | z << 1 of Sec. II's map phi_s).
+ * 1 <= m <= 512 (one thread per check, 512 per CTA), n <= 16382, check and qubit degree <= 16, no
+ * duplicate column in a row.
+ * Errors: SAGMS_ERR_ARG, SAGMS_ERR_CSR (bad CSR or Pauli), SAGMS_ERR_DEGREE, SAGMS_ERR_CUDA.
+ *
+ * sagms_gf4_decode: d_syn [shots][ceil(m/32)] u32 packed syndrome bits s_i = <E, H_i> (trace
+ * inner product); d_L0 [shots] f32 one prior LLR per shot (the same for X, Z, Y); outputs
+ * d_err [shots][2][ceil(n/32)] u32 (the x bits, then the z bits of e_hat: X = x, Z = z, Y = both),
+ * d_conv [shots] u8, d_iters [shots] i32 as sagms_decode.  Parameters as sagms_decode; flags: only
+ * SAGMS_FLAG_NO_EARLY_STOP.  Device buffers caller-owned, 4-byte aligned; asynchronous on
+ * `stream`.  sagms_gf4_decode_trace also writes d_trace [shots][max_iter+1][n][3] f32: Lambda(X),
+ * Lambda(Z), Lambda(Y) of every qubit at every checked round.
+ * Errors: as sagms_decode, plus SAGMS_ERR_PARAM for other flags and SAGMS_ERR_SIZE when the code's
+ * state does not fit a CTA's shared memory.
+ */
+typedef struct sagms_gf4_code sagms_gf4_code;
+int sagms_gf4_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+                        const uint8_t* pauli, sagms_gf4_code** out);
+void sagms_gf4_free_code(sagms_gf4_code* code);
+int sagms_gf4_decode(const sagms_gf4_code* code, const sagms_params* params, int64_t shots, const uint32_t* d_syn,
+                     const float* d_L0, uint32_t* d_err, uint8_t* d_conv, int32_t* d_iters, void* stream);
+int sagms_gf4_decode_trace(const sagms_gf4_code* code, const sagms_params* params, int64_t shots,
+                           const uint32_t* d_syn, const float* d_L0, uint32_t* d_err, uint8_t* d_conv,
+                           int32_t* d_iters, float* d_trace, void* stream);
+
 const char* sagms_last_error_string(void);
 
 /* Library version and build constants (clip levels, limits), human-readable. */

@@ -81,6 +81,69 @@ class DeviceCode:
             pass
 
 
+class Gf4DeviceCode:
+    """A stabilizer matrix with Pauli entries (GF(4), Sec. II) loaded on the current CUDA device
+    for the quaternary decoder (owns the C handle).  ``gcode``: inputs.gf4.Gf4Code or any
+    object with m, n, row_ptr, col_idx and pauli (1 X, 2 Z, 3 Y)."""
+
+    def __init__(self, gcode):
+        from . import _native
+        import torch
+        self._native = _native
+        self.m, self.n = int(gcode.m), int(gcode.n)
+        self.device = torch.cuda.current_device()
+        self.handle = _native.sagms_gf4_load_code(self.m, self.n, gcode.row_ptr, gcode.col_idx, gcode.pauli)
+
+    @property
+    def mw(self):
+        return (self.m + 31) // 32
+
+    @property
+    def nw(self):
+        return (self.n + 31) // 32
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._native.sagms_gf4_free_code(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gf4_decode(code: Gf4DeviceCode, syn, L0, params: Params | None = None, stream=None, trace=False):
+    """Decode on the GPU with the quaternary decoder.  ``syn``: int32 CUDA tensor [shots, mw];
+    ``L0``: float32 CUDA tensor [shots] (one prior LLR per shot, ln((1 - eps0)/(eps0/3))).
+    Returns (err [shots, 2, nw] int32: x bits then z bits of e_hat, conv [shots] uint8,
+    iters [shots] int32[, trace [shots, max_iter+1, n, 3] float32: Lambda(X, Z, Y)])."""
+    import torch
+    from . import _native
+    p = params or Params()
+    if p.flags & ~FLAG_NO_EARLY_STOP:
+        raise ValueError("the GF(4) decoder takes one prior per shot and no flag but FLAG_NO_EARLY_STOP")
+    dev = f"cuda:{code.device}"
+    for name, a, dt in (("syn", syn, (torch.int32, torch.uint32) if hasattr(torch, "uint32") else (torch.int32,)),
+                        ("L0", L0, (torch.float32,))):
+        if not hasattr(a, "data_ptr") or str(a.device) != dev or a.dtype not in dt or not a.is_contiguous():
+            raise ValueError(f"{name}: need a contiguous {dt[0]} tensor on {dev}")
+    if syn.dim() != 2 or syn.shape[1] != code.mw:
+        raise ValueError(f"syn: shape {list(syn.shape)}, need [shots, {code.mw}]")
+    shots = int(syn.shape[0])
+    if tuple(L0.shape) != (shots,):
+        raise ValueError(f"L0: shape {list(L0.shape)}, need [{shots}]")
+    err = torch.empty((shots, 2, code.nw), dtype=torch.int32, device=dev)
+    conv = torch.empty((shots,), dtype=torch.uint8, device=dev)
+    iters = torch.empty((shots,), dtype=torch.int32, device=dev)
+    tr = torch.empty((shots, p.max_iter + 1, code.n, 3), dtype=torch.float32, device=dev) if trace else None
+    _native.sagms_gf4_decode(code.handle, p.to_c(), shots, syn.data_ptr(), L0.data_ptr(), err.data_ptr(),
+                             conv.data_ptr(), iters.data_ptr(), _stream_ptr(stream),
+                             tr.data_ptr() if tr is not None else None)
+    return (err, conv, iters, tr) if trace else (err, conv, iters)
+
+
 def _stream_ptr(stream):
     import torch
     if stream is None:

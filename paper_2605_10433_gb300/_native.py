@@ -78,6 +78,10 @@ def _load_library():
                                           P(ctypes.c_float), vp]),
         "sagms_set_plan": (ctypes.c_int, [vp, i32]),
         "sagms_set_launch_limit": (ctypes.c_int, [vp, i64]),
+        "sagms_gf4_load_code": (ctypes.c_int, [i32, i32, i64, P(i32), P(i32), P(ctypes.c_uint8), P(vp)]),
+        "sagms_gf4_free_code": (None, [vp]),
+        "sagms_gf4_decode": (ctypes.c_int, [vp, P(sagms_params), i64, vp, vp, vp, vp, vp, vp]),
+        "sagms_gf4_decode_trace": (ctypes.c_int, [vp, P(sagms_params), i64, vp, vp, vp, vp, vp, vp, vp]),
         "sagms_server_create": (ctypes.c_int, [ctypes.c_size_t, i32, i32, i32, P(vp)]),
         "sagms_server_add_code": (ctypes.c_int, [vp, vp, P(sagms_params), P(i32)]),
         "sagms_server_submit": (ctypes.c_int, [vp, i32, i64, vp, vp, vp, vp, vp, P(ctypes.c_uint64)]),
@@ -244,6 +248,34 @@ def sagms_set_plan(handle, plan):
 
 def sagms_set_launch_limit(handle, shots):
     _check(_lib.sagms_set_launch_limit(handle, int(shots)))
+
+
+def sagms_gf4_load_code(m, n, row_ptr, col_idx, pauli):
+    """Returns an opaque handle (int).  Host arrays: row_ptr int32, col_idx int32, pauli uint8."""
+    import numpy as np
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    pa = np.ascontiguousarray(pauli, dtype=np.uint8)
+    if rp.shape != (int(m) + 1,) or ci.shape != pa.shape or ci.shape[0] != int(rp[-1]):
+        raise ValueError("sagms_gf4_load_code: row_ptr must have m + 1 entries and col_idx / pauli nnz each")
+    out = ctypes.c_void_p()
+    _check(_lib.sagms_gf4_load_code(int(m), int(n), int(rp[-1]), rp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                    ci.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                    pa.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), ctypes.byref(out)))
+    return out.value
+
+
+def sagms_gf4_free_code(handle):
+    _lib.sagms_gf4_free_code(handle)
+
+
+def sagms_gf4_decode(handle, params, shots, syn_ptr, L0_ptr, err_ptr, conv_ptr, iters_ptr, stream_ptr, trace_ptr=None):
+    if trace_ptr is None:
+        _check(_lib.sagms_gf4_decode(handle, ctypes.byref(params), shots, syn_ptr, L0_ptr, err_ptr, conv_ptr, iters_ptr,
+                                     stream_ptr))
+    else:
+        _check(_lib.sagms_gf4_decode_trace(handle, ctypes.byref(params), shots, syn_ptr, L0_ptr, err_ptr, conv_ptr,
+                                           iters_ptr, trace_ptr, stream_ptr))
 
 
 def sagms_alpha_star(L0: float, dc: int) -> float:

@@ -16,7 +16,7 @@ LIB = os.path.join(HERE, "libsagms.so")
 SOURCES = [os.path.join(HERE, "csrc", f)
            for f in ("kernels_qc_large.cu", "kernels_qc_small.cu", "kernels_slots.cu", "kernels_generic.cu",
                      "kernels_layered.cu", "sagms.cu",
-                     "server.cu", "mc.cu")]
+                     "server.cu", "mc.cu", "gf4.cu")]
 DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in os.listdir(os.path.join(HERE, "csrc"))] + \
     [os.path.join(ROOT, "include", "sagms.h")]
 
