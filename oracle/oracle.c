@@ -132,17 +132,18 @@ static double pert_sign(uint64_t item, uint64_t round) {
 }
 
 /* The leave-one-out set M(i)\j of edge e of check i (Eqs. 3, 4, 8): the sign parity
- * (-1)^{s_i} prod sgn(q) (1 = negative), min |q| and prod tanh(|q|/2) over the other edges. */
-static void cn_extrinsic(int i, int e, const int32_t* row_ptr, int s_i, const double* q, int* neg, double* mn,
-                         double* prod) {
+ * (-1)^{s_i} prod sgn(q) (1 = negative) and, over the other edges, min |q| (MS family) or
+ * prod tanh(|q|/2) (BP). */
+static void cn_extrinsic(int i, int e, const int32_t* row_ptr, int s_i, int msfam, const double* q, int* neg,
+                         double* mn, double* prod) {
     int sg = s_i;
     double lo = INFINITY, pr = 1.0;
     for (int f = row_ptr[i]; f < row_ptr[i + 1]; ++f) {
         if (f == e) continue;
         if (q[f] < 0.0) sg ^= 1;
         const double a = fabs(q[f]);
-        if (a < lo) lo = a;
-        pr *= tanh(0.5 * a);
+        if (msfam) { if (a < lo) lo = a; }
+        else pr *= tanh(0.5 * a);
     }
     *neg = sg;
     *mn = lo;
@@ -170,7 +171,7 @@ static void cn_update(int i, const int32_t* row_ptr, int s_i, int msfam, double 
     for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
         int neg;
         double mn, prod;
-        cn_extrinsic(i, e, row_ptr, s_i, q, &neg, &mn, &prod);
+        cn_extrinsic(i, e, row_ptr, s_i, msfam, q, &neg, &mn, &prod);
         const double mag = cn_magnitude(msfam, g, mn, prod, nclip);
         r[e] = neg ? -mag : mag;
     }
@@ -534,7 +535,7 @@ int oracle_shadow(int m, int n, const int32_t* row_ptr, const int32_t* col_idx, 
                 for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
                     int neg;
                     double mn, prod;
-                    cn_extrinsic(i, e, row_ptr, s_i, q, &neg, &mn, &prod);
+                    cn_extrinsic(i, e, row_ptr, s_i, msfam, q, &neg, &mn, &prod);
                     const double mag = cn_magnitude(msfam, g, mn, prod, &nclip);
                     /* bound: the largest input bound, whether an input's sign is uncertain,
                      * and (MS family) the largest bound among inputs that could be the minimum */
