@@ -443,10 +443,22 @@ def main():
                     help="time the layered schedule (SAGMS_FLAG_LAYERED) instead of Algorithm 1's flooding one")
     ap.add_argument("--mode", default="sagms", choices=["sagms", "sms", "ms", "bp"],
                     help="decoder timed (default SAGMS, the headline; the others for profiling)")
+    ap.add_argument("--only", default=None, choices=["gf4", "mc", "serving", "mixed"],
+                    help="run one secondary workload alone and print its JSON (profiling)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        import torch
+        import paper_2605_10433_gb300 as S
+        from paper_2605_10433_gb300 import inputs as I
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        fn = {"gf4": lambda: bench_gf4(S, I, args.mode_steps, shots=min(args.shots, 1_000_000)),
+              "mc": lambda: bench_mc(S, I), "serving": lambda: bench_serving(S, I),
+              "mixed": lambda: bench_mixed_degree(S, I, args.mode_steps)}[args.only]
+        print(json.dumps(fn()))
+        return 0
 
     import torch
     import paper_2605_10433_gb300 as S

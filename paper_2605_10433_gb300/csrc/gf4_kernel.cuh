@@ -23,7 +23,10 @@
 //       (Eq. 2 per Pauli), decision D = argmin(0, Lambda(X), Lambda(Z), Lambda(Y)) (ties to
 //       I, X, Z, Y), and for every edge of Pauli T the extrinsic scalar message
 //       lambda_T = ln(1 + e^{-Lambda'(T)}) - ln(e^{-Lambda'(T')} + e^{-Lambda'(T'')}), Lambda' =
-//       Lambda minus the edge's own message on the Paulis it anticommutes with.
+//       Lambda minus the edge's own message on the Paulis it anticommutes with.  Since that
+//       message enters T' and T'' alike, lambda_T(Lambda') = lambda_T(Lambda) - message: one
+//       lambda per Pauli and qubit, then one subtraction per edge (as q = P - r in the
+//       binary kernels).
 // LLR units throughout (lambda_T is not homogeneous).  Outputs: e_hat as x bits then z bits
 // ([shots][2][nw]), conv, iters; the trace holds Lambda(X, Z, Y) of every checked round.
 #pragma once
@@ -217,17 +220,18 @@ __global__ void __launch_bounds__(512) gf4_kernel(const DecodeArgs a, const Gf4L
                 if (lz < best) { best = lz; d = 2; }
                 if (ly < best) { best = ly; d = 3; }
                 D[c] = d;
+                // lambda_T of the totals, once per Pauli: an edge's own message r enters exactly
+                // the two Paulis anticommuting with its entry T, so removing it multiplies
+                // e^{-Lambda(T')} + e^{-Lambda(T'')} by e^{r} and leaves Lambda(T): the
+                // extrinsic message is lambda_T(Lambda) - r.
+                const float lamX = gf4_softplus_neg(lx) - gf4_lse_neg(lz, ly);
+                const float lamZ = gf4_softplus_neg(lz) - gf4_lse_neg(lx, ly);
+                const float lamY = gf4_softplus_neg(ly) - gf4_lse_neg(lx, lz);
 #pragma unroll
                 for (int q = 0; q < DV; ++q) {
                     if (pt[q] == 0u) continue;
-                    const float ex = gf4_anti(1u, pt[q]) ? lx - r[q] : lx;
-                    const float ez = gf4_anti(2u, pt[q]) ? lz - r[q] : lz;
-                    const float ey = gf4_anti(3u, pt[q]) ? ly - r[q] : ly;
-                    // commuting Pauli of the entry, then the two anticommuting ones
-                    const float own = (pt[q] == 1u) ? ex : ((pt[q] == 2u) ? ez : ey);
-                    const float o1 = (pt[q] == 1u) ? ez : ex;
-                    const float o2 = (pt[q] == 3u) ? ez : ey;
-                    Lam[vneT[q * Np + c] & 0xffffu] = gf4_softplus_neg(own) - gf4_lse_neg(o1, o2);
+                    const float lam = (pt[q] == 1u) ? lamX : ((pt[q] == 2u) ? lamZ : lamY);
+                    Lam[vneT[q * Np + c] & 0xffffu] = lam - r[q];
                 }
             }
             __syncthreads();

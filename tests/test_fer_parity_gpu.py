@@ -39,7 +39,7 @@ CASES = [
     ((127, 4), Q2[0.01], "sagms", 4005, 1_000_000, 1e-5),
     # config 3: GB(255, w), q = 0.02, SAGMS
     ((255, 3), 0.02, "sagms", 5003, 300_000, 2e-5),
-    ((255, 4), 0.02, "sagms", 5004, 300_000, 1.5e-4),
+    ((255, 4), 0.02, "sagms", 5004, 300_000, 8e-5),
     ((255, 5), 0.02, "sagms", 5005, 300_000, 3e-5),
     ((255, 6), 0.02, "sagms", 5006, 300_000, 5e-5),
     ((255, 8), 0.02, "sagms", 5008, 300_000, 7e-4),
@@ -48,14 +48,14 @@ CASES = [
 CASES3 = [((255, w), 0.02, mode, 5100 + 10 * w + k, shots, cap) for w, k, mode, shots, cap in [
     (3, 0, "ms", 20_000, 0.0), (3, 1, "sms", 100_000, 6e-3), (3, 2, "bp", 100_000, 2e-2),
     (4, 0, "ms", 20_000, 0.0), (4, 1, "sms", 100_000, 4e-4), (4, 2, "bp", 100_000, 2.5e-3),
-    (5, 0, "ms", 20_000, 0.0), (5, 1, "sms", 100_000, 1e-3), (5, 2, "bp", 100_000, 1e-3),
+    (5, 0, "ms", 20_000, 0.0), (5, 1, "sms", 100_000, 3e-4), (5, 2, "bp", 100_000, 1e-3),
     (6, 0, "ms", 20_000, 0.0), (6, 1, "sms", 100_000, 1e-4), (6, 2, "bp", 100_000, 1e-4),
     (8, 0, "ms", 20_000, 0.0), (8, 1, "sms", 100_000, 3e-3), (8, 2, "bp", 100_000, 1.2e-3)]]
 # config 4: GB(1023,5) on the headline mix p in {0.005, 0.01, 0.02} (shots interleaved)
 CASES4 = [("sagms", 500_000, 6000, 4e-4), ("sms", 100_000, 6001, 1e-2), ("ms", 50_000, 6002, 0.0),
-          ("bp", 100_000, 6003, 1e-2)]
+          ("bp", 100_000, 6003, 2e-3)]
 # the serving workload's codes (n = 126, 510, 1022, 2046), p over its range U[0.005, 0.03]
-SERVING = [((63, 3), 7001, 1e-4), ((255, 4), 7002, 1e-4), ((511, 5), 7003, 3e-4), ((1023, 5), 7004, 3e-4)]
+SERVING = [((63, 3), 7001, 1e-4), ((255, 4), 7002, 1e-4), ((511, 5), 7003, 3e-4), ((1023, 5), 7004, 1.2e-3)]
 SERVING_P = [0.005, 0.01, 0.015, 0.02, 0.025, 0.03]
 
 
