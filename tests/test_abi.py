@@ -182,3 +182,35 @@ def test_op_count_model_matches_eq15_and_table1():
     assert roofline.smem_bytes([1], E, n) == 12 * E + 4 * n
     assert roofline.smem_bytes([1, 3, 0], E, n) == (12 * E + 4 * n) + (12 * E + 4 * n + 2 * (16 * E + 4 * n))
     assert roofline.smem_peak_bytes(152, 2070) == 152 * 128 * 2070e6
+
+
+@pytest.mark.parametrize("rows,pauli,n,err", [
+    ([[0, 1], [1, 2]], [1, 2, 3, 4], 3, "SAGMS_ERR_CSR"),        # Pauli code 4
+    ([[0, 1], [1, 2]], [1, 0, 3, 1], 3, "SAGMS_ERR_CSR"),        # Pauli code 0 (identity entry)
+    ([[0, 0], [1, 2]], [1, 1, 2, 2], 3, "SAGMS_ERR_CSR"),        # duplicate column
+    ([[0, 5]], [1, 2], 3, "SAGMS_ERR_CSR"),                      # column out of range
+    ([list(range(17))], [1] * 17, 20, "SAGMS_ERR_DEGREE"),       # check degree 17
+])
+def test_gf4_loader_refuses_bad_matrices_before_any_cuda_call(native, rows, pauli, n, err):
+    rp = np.cumsum([0] + [len(r) for r in rows]).astype(np.int32)
+    ci = np.array([c for r in rows for c in r], dtype=np.int32)
+    pa = np.array(pauli, dtype=np.uint8)
+    out = ctypes.c_void_p()
+    rc = native.lib().sagms_gf4_load_code(len(rows), n, int(rp[-1]), rp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                          ci.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                          pa.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), ctypes.byref(out))
+    code = {v: k for k, v in native.ERRORS.items()}[err.replace("SAGMS_", "")]
+    assert rc == code and not out.value, native.sagms_last_error_string()
+
+
+def test_gf4_decode_refuses_before_any_launch(native):
+    p = native.sagms_params(2, 0.75, 0.3, 0.5, 1.1, 10, 0)
+    lib = native.lib()
+    err_arg = -1
+    assert lib.sagms_gf4_decode(None, ctypes.byref(p), 10, 16, 16, 16, 16, 16, None) == err_arg
+    assert lib.sagms_gf4_load_code(600, 10, 0, None, None, None, None) == err_arg   # out is NULL
+    out = ctypes.c_void_p()
+    rp = np.zeros(601, dtype=np.int32)
+    rc = lib.sagms_gf4_load_code(600, 10, 0, rp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), None, None,
+                                 ctypes.byref(out))
+    assert rc == err_arg and "512" in native.sagms_last_error_string()
