@@ -542,8 +542,9 @@ def main():
                      f"decision, residual XOR, popcount); peak = {props.multi_processor_count} SMs x 128 lanes x "
                      f"{sm_max:.0f} MHz (derived from unit counts and clock); HBM bound "
                      f"{roofline.hbm_bytes_per_shot(code.m, code.n)} B/shot at "
-                     f"{peaks.get('hbm_gbs', 'n/a')} GB/s is "
-                     f"{(peaks.get('hbm_gbs', 6793.1) * 1e9 / roofline.hbm_bytes_per_shot(code.m, code.n)):.3g} shots/s")}
+                     + (f"{peaks['hbm_gbs']} GB/s (of measured)" if "hbm_gbs" in peaks else "6800 GB/s (of fallback)")
+                     + f" is {(peaks.get('hbm_gbs', 6800.0) * 1e9 / roofline.hbm_bytes_per_shot(code.m, code.n)):.3g} "
+                     "shots/s")}
     tmem = "qc_tmem=1" in S._native.sagms_version() and args.mode != "bp" and not args.layered
     smem_b = roofline.smem_bytes(it_host, code.nnz, code.n, old_in_smem=not tmem)
     smem_peak = roofline.smem_peak_bytes(props.multi_processor_count, sm_max)
