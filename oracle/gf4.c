@@ -216,3 +216,174 @@ done:
     free(vn_ptr); free(vn_edges); free(fill); free(lam_in); free(r); free(post); free(prior); free(ehat); free(sres);
     return rc;
 }
+
+/*
+ * oracle_gf4_shadow (test acceptance only, not part of the method): the GF(4) counterpart of
+ * oracle_shadow in oracle.c.  It replays one shot's flooding rounds with the per-Pauli
+ * posteriors of each check taken from a supplied binary32 trace G (another implementation's
+ * Lambda(X, Z, Y) per qubit, rows 0..rounds) and bounds, to first order in u = 2^-24, how far
+ * that implementation's rounding may move its next posteriors from the FP64 step.  Round l:
+ *   - decisions from G_l: the argmin of (0, Lambda(X), Lambda(Z), Lambda(Y)) with the
+ *     comparisons in the order X, Z, Y on the binary32 values as given, residual (Eq. 1),
+ *     gamma (Eq. 6), gains (Eq. 7);
+ *   - CN inputs: lambda_T(G_l(j)) - r(i,j), the extrinsic scalar message of reading 19 with
+ *     the totals replaced by G_l (removing an edge's own message from the two Paulis that
+ *     anticommute with its entry T subtracts it from lambda_T);
+ *   - CN update (Eqs. 3, 4, 8) as in gf4_decode; Lambda_{l+1}(W) = L0 + the messages of the
+ *     edges anticommuting with W (Eq. 2 per Pauli).
+ * The bound per edge grows as in oracle_shadow (input difference, gain, product, 1-Lipschitz
+ * minimum and BP rule, uncertain signs), with the binary32 evaluation of lambda_T adding
+ * 8 u (|Lambda(T)| + |min(Lambda(T'), Lambda(T''))| + 1); lambda_T is 1-Lipschitz in the
+ * largest change of its three arguments (its partial derivatives are -s(T), s(T'), s(T'') with
+ * s(T) <= 1 and s(T') + s(T'') <= 1).  The posterior bound is the sum of the bounds of the
+ * messages it adds plus d_v u (|L0| + their magnitudes), doubled for second-order terms.
+ *   rounds, G [rounds+1][n][3] (float): as oracle_shadow; dev, bnd [rounds+1][n][3] (out):
+ *   G minus the FP64 step and its bound (row 0: G_0 - L0, bound 0); flips [rounds+1] (out):
+ *   qubits whose Pauli decision of G differs from that of the FP64 step.
+ * Returns 0, or -1 on bad arguments / allocation failure.
+ */
+int oracle_gf4_shadow(int m, int n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* pauli,
+                      int mode, double alpha, double alpha_min, double alpha_max, double eta_unsat, unsigned flags,
+                      const uint32_t* syn, const double* L0, int rounds, const float* G, double* dev, double* bnd,
+                      int32_t* flips) {
+    if (m < 0 || n <= 0 || rounds < 0 || !row_ptr || !col_idx || !pauli || !syn || !L0 || !G || !dev || !bnd ||
+        !flips || mode < 0 || mode > 3)
+        return -1;
+    const double u = 0x1p-24;
+    const int nnz = row_ptr[m];
+    int* vn_ptr = (int*)calloc((size_t)n + 1, sizeof(int));
+    int* vn_edges = (int*)malloc(sizeof(int) * (size_t)(nnz > 0 ? nnz : 1));
+    int* fill = (int*)calloc((size_t)n + 1, sizeof(int));
+    double* q = (double*)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+    double* bq = (double*)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+    double* r = (double*)calloc((size_t)(nnz > 0 ? nnz : 1), sizeof(double));
+    double* br = (double*)calloc((size_t)(nnz > 0 ? nnz : 1), sizeof(double));
+    double* prior = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    int* dec = (int*)malloc(sizeof(int) * (size_t)n);
+    int* sres = (int*)malloc(sizeof(int) * (size_t)(m > 0 ? m : 1));
+    int rc = 0;
+    if (!vn_ptr || !vn_edges || !fill || !q || !bq || !r || !br || !prior || !dec || !sres) { rc = -1; goto done; }
+    for (int e = 0; e < nnz; ++e) {
+        if (col_idx[e] < 0 || col_idx[e] >= n || pauli[e] < 1 || pauli[e] > 3) { rc = -1; goto done; }
+        vn_ptr[col_idx[e] + 1]++;
+    }
+    for (int j = 0; j < n; ++j) vn_ptr[j + 1] += vn_ptr[j];
+    for (int e = 0; e < nnz; ++e) vn_edges[vn_ptr[col_idx[e]] + fill[col_idx[e]]++] = e;
+    {
+        static const int paulis[3] = {1, 2, 3};   /* X, Z, Y */
+        const int msfam = (mode != GF4_MODE_BP);
+        const int per_qubit = (flags & GF4_FLAG_L0_PER_QUBIT) != 0;
+        int dv_max = 1;
+        for (int j = 0; j < n; ++j)
+            if (vn_ptr[j + 1] - vn_ptr[j] > dv_max) dv_max = vn_ptr[j + 1] - vn_ptr[j];
+        const double gtop = (mode == GF4_MODE_SAGMS) ? alpha_max * eta_unsat : (mode == GF4_MODE_SMS ? alpha : 1.0);
+        const double dgain = (mode == GF4_MODE_MS || mode == GF4_MODE_BP) ? 0.0 : 8.0 * u * gtop;
+        for (int j = 0; j < n; ++j)
+            for (int w = 0; w < 3; ++w) prior[3 * j + w] = per_qubit ? L0[3 * j + w] : L0[0];
+        for (int k = 0; k < 3 * n; ++k) {
+            dev[k] = (double)G[k] - prior[k];
+            bnd[k] = 0.0;
+        }
+        flips[0] = 0;
+        for (int l = 0; l < rounds; ++l) {
+            const float* Gl = G + (size_t)l * n * 3;
+            /* (i) decisions of the supplied posteriors (their own comparisons), residual, gamma */
+            for (int j = 0; j < n; ++j) {
+                float best = 0.0f;
+                int arg = 0;
+                for (int w = 0; w < 3; ++w)
+                    if (Gl[3 * j + w] < best) { best = Gl[3 * j + w]; arg = paulis[w]; }
+                dec[j] = arg;
+            }
+            int n_unsat = 0;
+            for (int i = 0; i < m; ++i) {
+                int x = gbit(syn, i);
+                for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) x ^= anticommute(dec[col_idx[e]], pauli[e]);
+                sres[i] = x;
+                n_unsat += x;
+            }
+            const double gamma = (m > 0) ? (double)n_unsat / (double)m : 0.0;
+            /* inputs: lambda_T of the supplied totals minus the edge's own message */
+            for (int e = 0; e < nnz; ++e) {
+                const int j = col_idx[e], T = pauli[e];
+                double lam[3];
+                for (int w = 0; w < 3; ++w) lam[w] = (double)Gl[3 * j + w];
+                const int t = (T == 1) ? 0 : (T == 2 ? 1 : 2);
+                const double lo = (lam[(t + 1) % 3] < lam[(t + 2) % 3]) ? lam[(t + 1) % 3] : lam[(t + 2) % 3];
+                const double c = commute_llr(lam, T);
+                q[e] = c - r[e];
+                bq[e] = br[e] + 8.0 * u * (fabs(lam[t]) + fabs(lo) + 1.0) + u * (fabs(q[e]) + br[e]);
+            }
+            /* CN update with the bound (as oracle_shadow) */
+            for (int i = 0; i < m; ++i) {
+                const int res_i = sres[i];
+                double g = 1.0;
+                if (mode == GF4_MODE_SMS) g = alpha;
+                else if (mode == GF4_MODE_SAGMS) g = (alpha_max - (alpha_max - alpha_min) * gamma) * (res_i ? eta_unsat : 1.0);
+                const int deg = row_ptr[i + 1] - row_ptr[i];
+                for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+                    int neg = gbit(syn, i), unsure = 0;
+                    double mn = INFINITY, prod = 1.0, bmax = 0.0, bm = 0.0;
+                    for (int f = row_ptr[i]; f < row_ptr[i + 1]; ++f)
+                        if (f != e) {
+                            if (q[f] < 0.0) neg ^= 1;
+                            if (fabs(q[f]) <= bq[f]) unsure = 1;
+                            if (bq[f] > bmax) bmax = bq[f];
+                            if (msfam) { if (fabs(q[f]) < mn) mn = fabs(q[f]); }
+                            else prod *= tanh(0.5 * fabs(q[f]));
+                        }
+                    double mag, b;
+                    if (msfam) {
+                        for (int f = row_ptr[i]; f < row_ptr[i + 1]; ++f)
+                            if (f != e && fabs(q[f]) - bq[f] <= mn + bmax && bq[f] > bm) bm = bq[f];
+                        mag = g * mn;
+                        if (mag > GF4_MSFAM_CLIP) mag = GF4_MSFAM_CLIP;
+                        b = (mn < INFINITY) ? g * bm + dgain * (mn + bm) + u * fabs(mag) : 0.0;
+                        if (mag >= GF4_MSFAM_CLIP && (g - dgain) * (mn - bm) > GF4_MSFAM_CLIP) b = 0.0;
+                        if (unsure) b += 2.0 * (g + dgain) * (mn + bm);
+                    } else {
+                        mag = (prod >= 1.0) ? INFINITY : 2.0 * atanh(prod);
+                        if (mag > GF4_BP_CLIP) mag = GF4_BP_CLIP;
+                        b = bmax + (double)(deg + 6) * u + 3.0 * u * mag;
+                        if (mag >= GF4_BP_CLIP) b += u * GF4_BP_CLIP;
+                        if (unsure) b += 2.0 * (mag + bmax);
+                    }
+                    r[e] = neg ? -mag : mag;
+                    br[e] = b;
+                }
+            }
+            /* (v) per-Pauli posteriors of the replay and their bound */
+            double* dl = dev + (size_t)(l + 1) * n * 3;
+            double* bl = bnd + (size_t)(l + 1) * n * 3;
+            const float* Gn = G + (size_t)(l + 1) * n * 3;
+            int fl = 0;
+            for (int j = 0; j < n; ++j) {
+                double sbest = 0.0;
+                int sarg = 0;
+                float gbest = 0.0f;
+                int garg = 0;
+                for (int w = 0; w < 3; ++w) {
+                    double acc = prior[3 * j + w], mag = fabs(prior[3 * j + w]), bsum = 0.0;
+                    for (int t2 = vn_ptr[j]; t2 < vn_ptr[j + 1]; ++t2) {
+                        const int e = vn_edges[t2];
+                        if (anticommute(paulis[w], pauli[e])) {
+                            acc += r[e];
+                            mag += fabs(r[e]);
+                            bsum += br[e];
+                        }
+                    }
+                    dl[3 * j + w] = (double)Gn[3 * j + w] - acc;
+                    bl[3 * j + w] = 2.0 * (bsum + (double)dv_max * u * mag);
+                    if (acc < sbest) { sbest = acc; sarg = paulis[w]; }
+                    if (Gn[3 * j + w] < gbest) { gbest = Gn[3 * j + w]; garg = paulis[w]; }
+                }
+                fl += (sarg != garg);
+            }
+            flips[l + 1] = fl;
+        }
+    }
+done:
+    free(vn_ptr); free(vn_edges); free(fill); free(q); free(bq); free(r); free(br); free(prior); free(dec);
+    free(sres);
+    return rc;
+}

@@ -5,7 +5,8 @@ Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.
 this module.  Parity status: pinned by ``tests/test_gf4_oracle.py`` -- BP4 on tree-structured
 stabilizer matrices equals brute-force Pauli marginals over all 4^n errors, a matrix of
 X-type checks with priors that forbid X and Y reduces it exactly to the binary oracle (itself
-pinned), and the mode reductions and zero-syndrome case hold bit for bit.
+pinned), and the mode reductions and zero-syndrome case hold bit for bit.  ``shadow`` (the
+acceptance replay of GPU traces, not the method) is pinned in ``tests/test_gf4_shadow.py``.
 """
 from __future__ import annotations
 
@@ -52,6 +53,12 @@ def _load():
                                           P(ctypes.c_uint32), P(ctypes.c_uint8), P(ctypes.c_int32),
                                           P(ctypes.c_double)]
         lib.oracle_gf4_decode.restype = ctypes.c_int
+        lib.oracle_gf4_shadow.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_int32), P(ctypes.c_int32),
+                                          P(ctypes.c_uint8), ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_uint, P(ctypes.c_uint32),
+                                          P(ctypes.c_double), ctypes.c_int, P(ctypes.c_float), P(ctypes.c_double),
+                                          P(ctypes.c_double), P(ctypes.c_int32)]
+        lib.oracle_gf4_shadow.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -112,3 +119,28 @@ def decode(gcode, syn, L0, mode=SAGMS, alpha=0.75, alpha_min=0.30, alpha_max=0.5
     if tr is not None:
         out["trace"] = tr
     return out
+
+
+def shadow(gcode, syn_row, L0, G, rounds, mode=SAGMS, alpha=0.75, alpha_min=0.30, alpha_max=0.50, eta_unsat=1.10,
+           flags=0):
+    """Replay one shot's rounds from another implementation's binary32 per-Pauli posterior trace
+    ``G`` [>= rounds+1][n][3] and bound its rounding (``oracle_gf4_shadow``; test acceptance
+    only).  Returns (dev, bnd, flips) with dev, bnd [rounds+1][n][3]."""
+    lib = _load()
+    n = gcode.n
+    row_ptr = np.ascontiguousarray(gcode.row_ptr, dtype=np.int32)
+    col_idx = np.ascontiguousarray(gcode.col_idx, dtype=np.int32)
+    pauli = np.ascontiguousarray(gcode.pauli, dtype=np.uint8)
+    syn_row = np.ascontiguousarray(syn_row, dtype=np.uint32).reshape(-1)
+    L0 = np.ascontiguousarray(L0, dtype=np.float64).reshape(-1)
+    G = np.ascontiguousarray(np.asarray(G, dtype=np.float32)[:rounds + 1]).reshape(rounds + 1, n, 3)
+    dev = np.zeros((rounds + 1, n, 3))
+    bnd = np.zeros((rounds + 1, n, 3))
+    flips = np.zeros(rounds + 1, dtype=np.int32)
+    rc = lib.oracle_gf4_shadow(gcode.m, n, _p(row_ptr, ctypes.c_int32), _p(col_idx, ctypes.c_int32),
+                               _p(pauli, ctypes.c_uint8), mode, alpha, alpha_min, alpha_max, eta_unsat, flags,
+                               _p(syn_row, ctypes.c_uint32), _p(L0, ctypes.c_double), rounds, _p(G, ctypes.c_float),
+                               _p(dev, ctypes.c_double), _p(bnd, ctypes.c_double), _p(flips, ctypes.c_int32))
+    if rc != 0:
+        raise RuntimeError("oracle_gf4_shadow: bad arguments")
+    return dev, bnd, flips

@@ -4,10 +4,14 @@ w = 5 (X-type rows of H_X over Z-type rows of H_Z: m = 126 rows, check and qubit
 depolarising noise at eps, prior L0 = ln((1 - eps0)/(eps0/3)) with eps0 = eps (matched) or
 eps0 = 0.1 (the mismatch of Fig. 2b / Fig. 3).  Modes: BP4, SMS(0.5), SAGMS(0.30, 0.50, 1.10).
 
-Per point: each side's FER lies in the other's 95% Wilson interval; per-shot outputs
-(x bits, z bits, conv, iters) are identical except for a capped fraction of shots, each traced
-to its first differing decision; posterior traces agree to 1e-5 (normwise, LLR units) at every
-check before the first differing decision within the first rounds.
+Per point: the GPU FER lies in the oracle's 95% Wilson interval (or the paired McNemar test
+does not reject equal FERs at 1%, as in tests/gpu_helpers.py); per-shot outputs
+(x bits, z bits, conv, iters) are identical except for a capped fraction of shots, each of
+which must pass the GF(4) shadow replay (every round re-done in FP64 from the GPU's own
+per-Pauli posteriors lands within the binary32 rounding bound, pinned in
+tests/test_gf4_shadow.py) and is classified at its first differing decision (near-ties at most
+0.01% of the shots); posterior traces agree to 1e-5 (normwise, LLR units) at every check
+before the first differing decision within the first rounds.
 """
 import numpy as np
 import pytest
@@ -19,6 +23,7 @@ from oracle import gf4 as O4
 from paper_2605_10433_gb300 import inputs as I
 from paper_2605_10433_gb300.inputs import gf4 as I4
 from paper_2605_10433_gb300.stats import wilson_interval
+from tests import gpu_helpers as G
 
 pytestmark = pytest.mark.gpu
 
@@ -58,6 +63,50 @@ def _same(a, b):
             & (a["iters"] == b["iters"]))
 
 
+def _decisions(Lam):
+    """Pauli decisions (0 I, 1 X, 2 Z, 3 Y) of per-Pauli LLRs [..., 3] (X, Z, Y), ties to I, X, Z, Y."""
+    full = np.concatenate([np.zeros(Lam.shape[:-1] + (1,)), Lam], axis=-1)
+    return np.array([0, 1, 2, 3])[np.argmin(full, axis=-1)]
+
+
+def _check_mismatches(g, dc, syn, L0, p, mo, gr, o):
+    """Every shot whose outputs differ: the traced GPU run reproduces the batch run and its outputs
+    are the ones its trace implies; the GF(4) shadow replay (oracle.gf4.shadow) accepts the trace
+    at every round; the first differing decision is classified as a near-tie (the oracle's two
+    smallest Pauli LLRs, the identity's 0 included, within 1e-4) or amplified.  Returns
+    (near-ties, amplified, worst shadow ratio)."""
+    bad = np.nonzero(~_same(gr, o))[0]
+    near, amp, worst = 0, 0, 0.0
+    kw = dict(mode=mo, alpha=p.alpha, alpha_min=p.alpha_min, alpha_max=p.alpha_max, eta_unsat=p.eta_unsat)
+    for c0 in range(0, len(bad), 64):
+        idx = bad[c0:c0 + 64]
+        gt, ot = _run(g, dc, syn[idx], L0[idx], p, mo, trace=True)
+        for k, s in enumerate(idx):
+            for key in ("ex", "ez", "conv", "iters"):
+                assert np.array_equal(gt[key][k], gr[key][s]), f"shot {s}: traced run differs ({key})"
+            rounds = int(gt["iters"][k])
+            last = _decisions(gt["trace"][k, rounds].astype(np.float64))
+            want = I.unpack_bits(gr["ex"][s:s + 1], g.n)[0] + 2 * I.unpack_bits(gr["ez"][s:s + 1], g.n)[0]
+            assert np.array_equal(last, want), f"shot {s}: e_hat differs from its last traced decisions"
+            dev, bnd, _ = O4.shadow(g, syn[s], L0[s:s + 1].astype(np.float64), gt["trace"][k], rounds, **kw)
+            with np.errstate(divide="ignore", invalid="ignore"):
+                ratio = float(np.max(np.where(dev == 0.0, 0.0, np.abs(dev) / bnd)))
+            worst = max(worst, ratio)
+            assert ratio <= 1.0, f"shot {s}: GPU posteriors at {ratio:.3g} of the binary32 rounding bound"
+            for l in range(min(rounds, int(ot["iters"][k])) + 1):
+                da = _decisions(gt["trace"][k, l].astype(np.float64))
+                db = _decisions(ot["trace"][k, l])
+                if (da != db).any():
+                    b = np.concatenate([np.zeros((g.n, 1)), ot["trace"][k, l]], axis=1)[da != db]
+                    srt = np.sort(b, axis=1)
+                    if float((srt[:, 1] - srt[:, 0]).max()) < 1e-4:
+                        near += 1
+                    else:
+                        amp += 1
+                    break
+    return near, amp, worst
+
+
 @pytest.mark.parametrize("eps,eps0", [(0.01, 0.01), (0.02, 0.02), (0.01, 0.1), (0.02, 0.1)])
 @pytest.mark.parametrize("mode", ["bp", "sms", "sagms"])
 def test_gf4_fer_parity(setting, mode, eps, eps0):
@@ -71,28 +120,14 @@ def test_gf4_fer_parity(setting, mode, eps, eps0):
     bad = np.nonzero(~same)[0]
     fer_g, fer_o = 1 - gr["conv"].mean(), 1 - o["conv"].mean()
     lo, hi = wilson_interval(int(round(fer_o * shots)), shots)
-    lo_g, hi_g = wilson_interval(int(round(fer_g * shots)), shots)
-    assert lo - 1e-12 <= fer_g <= hi + 1e-12
-    assert lo_g - 1e-12 <= fer_o <= hi_g + 1e-12
-    # classify the mismatches at their first differing decision (traced re-decode of both sides)
-    near = 0
-    for c0 in range(0, min(len(bad), 256), 64):
-        idx = bad[c0:c0 + 64]
-        gt, ot = _run(g, dc, syn[idx], L0[idx], p, mo, trace=True)
-        for k, s in enumerate(idx):
-            assert gt["iters"][k] == gr["iters"][s] and np.array_equal(gt["ex"][k], gr["ex"][s])
-            last = min(int(gt["iters"][k]), int(ot["iters"][k]))
-            for l in range(last + 1):
-                a = np.concatenate([np.zeros((g.n, 1)), gt["trace"][k, l]], axis=1)
-                b = np.concatenate([np.zeros((g.n, 1)), ot["trace"][k, l]], axis=1)
-                if (np.argmin(a, axis=1) != np.argmin(b, axis=1)).any():
-                    diff = np.argmin(a, axis=1) != np.argmin(b, axis=1)
-                    srt = np.sort(b[diff], axis=1)
-                    near += int(float((srt[:, 1] - srt[:, 0]).max()) < 1e-4)
-                    break
+    pm = G.mcnemar_p(gr["conv"], o["conv"])
+    assert (lo - 1e-12 <= fer_g <= hi + 1e-12) or pm >= 0.01
+    near, amp, worst = _check_mismatches(g, dc, syn, L0, p, mo, gr, o)
+    assert near <= int(1e-4 * shots + 1e-6), f"{near} near-ties of {shots}"
     assert len(bad) <= MISMATCH_CAP * shots, f"{len(bad)} mismatching shots of {shots}"
     print(f"gf4 GB(63,5) CSS eps={eps} eps0={eps0} {mode}: FER gpu {fer_g:.3e} oracle {fer_o:.3e} "
-          f"[{lo:.3e}, {hi:.3e}], mismatches {len(bad)} ({near} near-ties among the first 256), "
+          f"[{lo:.3e}, {hi:.3e}] McNemar p {pm:.3g}, mismatches {len(bad)} (near-tie {near}, amplified {amp}, "
+          f"shadow worst {worst:.3g}), "
           f"mean iters {gr['iters'].mean():.2f}")
 
 
@@ -135,3 +170,77 @@ def test_gf4_edge_cases(setting):
     e0, _, _ = S.gf4_decode(dc, torch.zeros((0, g.mw), dtype=torch.int32, device="cuda"),
                             torch.zeros((0,), dtype=torch.float32, device="cuda"), MODES["bp"][0])
     assert e0.shape[0] == 0
+
+
+def _random_pauli_code(m, n, seed, max_dc=8, max_dv=6):
+    """A random stabilizer-like matrix with X, Y and Z entries, irregular degrees (rows of 2..8
+    entries, qubit degree capped), m not a multiple of 32.  Not a commuting stabilizer group:
+    the decoder needs none, and the syndromes come from sampled errors."""
+    rng = np.random.default_rng(seed)
+    deg = np.zeros(n, dtype=int)
+    rows, paulis = [], []
+    for _ in range(m):
+        k = int(rng.integers(2, max_dc + 1))
+        free = np.nonzero(deg < max_dv)[0]
+        cols = sorted(rng.choice(free, size=min(k, len(free)), replace=False).tolist())
+        deg[cols] += 1
+        rows.append(cols)
+        paulis.append([int(rng.integers(1, 4)) for _ in cols])
+    row_ptr = np.cumsum([0] + [len(r) for r in rows]).astype(np.int32)
+    return I4.Gf4Code(m=m, n=n, row_ptr=row_ptr, col_idx=np.array([c for r in rows for c in r], dtype=np.int32),
+                      pauli=np.array([p for r in paulis for p in r], dtype=np.uint8), name=f"random-pauli{seed}")
+
+
+def _sample_paulis(g, eps, shots, seed):
+    """Depolarising errors on any Pauli matrix (numpy's Philox generator keyed by the seed) and
+    their syndromes as trace inner products."""
+    rng = np.random.Generator(np.random.Philox(key=seed))
+    hit = rng.random((shots, g.n)) < eps
+    kind = np.where(hit, rng.integers(1, 4, size=(shots, g.n)), 0)
+    x, z = kind & 1, kind >> 1
+    s = np.zeros((shots, g.m), dtype=np.uint8)
+    for i in range(g.m):
+        for e in range(g.row_ptr[i], g.row_ptr[i + 1]):
+            c, t = g.col_idx[e], int(g.pauli[e])
+            s[:, i] ^= ((x[:, c] & (t >> 1)) ^ (z[:, c] & (t & 1))).astype(np.uint8)
+    return I.pack_bits(s)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+@pytest.mark.parametrize("mode", ["bp", "sms", "sagms"])
+def test_gf4_general_pauli_matrices(mode, seed):
+    """Y entries, mixed entry types at a qubit, irregular degrees, m = 77 (not a multiple of 32):
+    every branch of the per-Pauli sums and of the commute LLR, against the oracle."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    g = _random_pauli_code(77, 90, seed)
+    dc = S.Gf4DeviceCode(g)
+    shots = 4000
+    syn = _sample_paulis(g, 0.01, shots, seed=100 + seed)
+    L0 = np.full(shots, I4.prior(0.01), dtype=np.float32)
+    p, mo = MODES[mode]
+    p = S.Params(**{**p.__dict__, "max_iter": 40})
+    gr, o = _run(g, dc, syn, L0, p, mo)
+    same = _same(gr, o)
+    fails_g, fails_o = int((gr["conv"] == 0).sum()), int((o["conv"] == 0).sum())
+    # these random matrices are poor codes (FER of a few percent): the non-converging shots
+    # wander, so mismatches are bounded relative to them, and the FERs are compared paired
+    assert int((~same).sum()) <= 2 * fails_o + int(0.002 * shots), f"{mode}: {int((~same).sum())} mismatches"
+    assert G.mcnemar_p(gr["conv"], o["conv"]) >= 0.01
+    _check_mismatches(g, dc, syn, L0, p, mo, gr, o)
+    gt, ot = _run(g, dc, syn[:32], L0[:32], p, mo, trace=True)
+    worst = 0.0
+    for s in range(32):
+        last = min(int(gt["iters"][s]), int(ot["iters"][s]), 3)
+        for l in range(last + 1):
+            a, b = gt["trace"][s, l].astype(np.float64), ot["trace"][s, l]
+            fin = np.isfinite(b)
+            e = float(np.max(np.abs(a[fin] - b[fin])) / max(float(np.max(np.abs(b[fin]))), 1.0))
+            worst = max(worst, e)
+            da = np.argmin(np.concatenate([np.zeros((g.n, 1)), a], axis=1), axis=1)
+            db = np.argmin(np.concatenate([np.zeros((g.n, 1)), b], axis=1), axis=1)
+            if (da != db).any():
+                break
+    assert worst <= 1e-5, worst
+    print(f"gf4 random Pauli matrix {seed} {mode}: {same.mean() * 100:.2f}% identical, FER gpu {fails_g / shots:.4f} "
+          f"oracle {fails_o / shots:.4f}, trace error {worst:.2e}")
