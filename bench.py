@@ -334,6 +334,50 @@ def bench_gf4(S, I, steps, shots=1_000_000):
     return out
 
 
+def bench_small_configs(S, I, steps, shots=1_000_000, cpu_shots=20000):
+    """Configs 1 and 2: SAGMS (and the other modes on config 2) on GB l=63 w=3 at iid Z flips
+    p = 0.05, and on GB l=127 w=4 at depolarising p in {0.01, 0.02, 0.04} marginalised to 2p/3;
+    GPU shots/s and FER, and the FP64 oracle's rate on the host cores on a bounded sample."""
+    import torch
+    import oracle
+    threads = os.cpu_count() or 1
+    out = {}
+    cases = [("config1 GB l=63 w=3 p=0.05", (63, 3), [0.05], 50, ["sagms", "sms", "ms", "bp"]),
+             ("config2 GB l=127 w=4 p_dep=0.01,0.02,0.04 (q=2p/3)", (127, 4), [0.01 * 2 / 3, 0.02 * 2 / 3, 0.04 * 2 / 3],
+              MAX_ITER, ["sagms", "sms", "ms", "bp"])]
+    stream = torch.cuda.current_stream()
+    for name, lw, qs, max_iter, modes in cases:
+        code = I.gb_code(*lw)
+        dc = S.DeviceCode.from_code(code)
+        _, syn, L0, _ = I.workload(code, qs, shots, seed=NOISE_SEED + lw[0])
+        d_syn = torch.from_numpy(syn.view(np.int32)).cuda()
+        d_L0 = torch.from_numpy(L0).cuda()
+        entry = {}
+        for mode in modes:
+            p = S.Params(mode=mode, alpha=SMS_ALPHA, max_iter=max_iter, **SAGMS_KW)
+            err, conv, iters = S.decode(dc, d_syn, d_L0, p, stream=stream)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                S.decode(dc, d_syn, d_L0, p, out=(err, conv, iters), stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            om = {"ms": oracle.MS, "sms": oracle.SMS, "sagms": oracle.SAGMS, "bp": oracle.BP}[mode]
+            t0 = time.perf_counter()
+            oracle.decode_code(code, syn[:cpu_shots], L0[:cpu_shots].astype(np.float64), mode=om, alpha=SMS_ALPHA,
+                               max_iter=max_iter, threads=threads, **SAGMS_KW)
+            cpu = cpu_shots / (time.perf_counter() - t0)
+            entry[mode] = {"shots_per_s": shots / (ms / 1e3), "fer_syn": float((conv == 0).float().mean()),
+                           "mean_iters": float(iters.float().mean()), "oracle_shots_per_s": cpu,
+                           "oracle_cores": threads, "oracle_sample": cpu_shots}
+        out[name] = entry
+        dc.close()
+    return out
+
+
 def classify_mismatches(S, code, dcode, syn, L0, params, g_err, g_conv, g_it, o):
     """Per-shot decision parity of the GPU batch against the FP64 oracle on the same shots,
     with the acceptance of the parity tests: every mismatching shot is re-decoded on the GPU
@@ -443,7 +487,7 @@ def main():
                     help="time the layered schedule (SAGMS_FLAG_LAYERED) instead of Algorithm 1's flooding one")
     ap.add_argument("--mode", default="sagms", choices=["sagms", "sms", "ms", "bp"],
                     help="decoder timed (default SAGMS, the headline; the others for profiling)")
-    ap.add_argument("--only", default=None, choices=["gf4", "mc", "serving", "mixed"],
+    ap.add_argument("--only", default=None, choices=["gf4", "mc", "serving", "mixed", "small"],
                     help="run one secondary workload alone and print its JSON (profiling)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -456,7 +500,8 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         fn = {"gf4": lambda: bench_gf4(S, I, args.mode_steps, shots=min(args.shots, 1_000_000)),
               "mc": lambda: bench_mc(S, I), "serving": lambda: bench_serving(S, I),
-              "mixed": lambda: bench_mixed_degree(S, I, args.mode_steps)}[args.only]
+              "mixed": lambda: bench_mixed_degree(S, I, args.mode_steps),
+              "small": lambda: bench_small_configs(S, I, args.mode_steps)}[args.only]
         print(json.dumps(fn()))
         return 0
 
