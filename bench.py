@@ -302,6 +302,7 @@ def bench_gf4(S, I, steps, shots=1_000_000):
     depolarising noise at eps = 0.01; SAGMS (0.30, 0.50, 1.10), SMS(0.5) and BP4 with the matched
     prior (eps0 = eps) and SAGMS / BP4 with the mismatched one (eps0 = 0.1): shots/s and FER."""
     import torch
+    from paper_2605_10433_gb300 import roofline
     from paper_2605_10433_gb300.inputs import gf4 as I4
     g = I4.css_code(I.gb_code(63, 5))
     dc = S.Gf4DeviceCode(g)
@@ -316,6 +317,8 @@ def bench_gf4(S, I, steps, shots=1_000_000):
             ("sagms_mismatch", S.Params(mode="sagms", max_iter=MAX_ITER, **SAGMS_KW), 0.1),
             ("bp4_mismatch", S.Params(mode="bp", max_iter=MAX_ITER), 0.1)]
     stream = torch.cuda.current_stream()
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    peak = roofline.alu_peak_ops(props.multi_processor_count, float(measured_peaks().get("sm_max_mhz") or 2070.0))
     for name, p, eps0 in runs:
         d_L0 = torch.full((shots,), float(I4.prior(eps0)), dtype=torch.float32, device="cuda")
         S.gf4_decode(dc, d_syn, d_L0, p, stream=stream)
@@ -328,8 +331,11 @@ def bench_gf4(S, I, steps, shots=1_000_000):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
+        ops = roofline.gf4_ops_per_iteration(p.mode, g.row_ptr, g.col_idx, g.n)
+        it_sum = float(iters.clamp(min=0).to(torch.int64).sum())
         out[name] = {"eps0": eps0, "shots_per_s": shots / (ms / 1e3), "fer_syn": float((conv == 0).float().mean()),
-                     "mean_iters": float(iters.float().mean())}
+                     "mean_iters": float(iters.float().mean()), "ops_per_iteration": ops,
+                     "roofline_frac": it_sum * ops / (ms / 1e3) / peak}
     dc.close()
     return out
 

@@ -88,7 +88,9 @@ __device__ __forceinline__ uint32_t qc_byte(uint32_t x, int k) { return (x >> (8
 // check thread's outgoing messages are kept there as well as in C_g, and the next round reads its
 // old messages from there.  Checks 2p and 2p + 1 share columns 2p DC .. 2p DC + 2 DC - 1, slot j
 // of check 2p + h at column 2p DC + 2j + h, so each loaded pair lands in adjacent registers as
-// the FP32x2 operand of the input sums.
+// the FP32x2 operand of the input sums.  The closed-form first round sends one value per check
+// on all its edges: it stores slot 0 of the pair only (2 columns), and the round after it
+// (flag `uni`) reads those two columns and adds them to every slot.
 template <class S, bool AUTO, bool PQ, int GC, bool BPK>
 __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* smem, const int tg, const int g_rt,
                                          const uint32_t (&off)[S::K][S::DC], const uint32_t degs, const bool pq_ok,
@@ -168,6 +170,7 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
     int pbuf = 0;
     int ph = 0;
     const bool tracing = a.trace != nullptr;
+    bool uni = false;   // the last round was the closed form (tensor memory holds slot 0 of each check)
 
     while (true) {
         // A5: gather the checks' posteriors, residual bits, unsatisfied count
@@ -320,8 +323,9 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
 #pragma unroll
                     for (int j = 0; j < DC; ++j) Cat(j, off[k][j]) = d;
                     if constexpr (TM) {
+                        // every edge of the check carries d: slot 0 of the pair stands for all
                         dk[k] = __float_as_uint(d);
-                        if (k & 1) tmem_st20_alt(tm + (uint32_t)((k - 1) * DC), dk[k - 1], dk[k]);
+                        if (k & 1) tmem_st2(tm + (uint32_t)((k - 1) * DC), dk[k - 1], dk[k]);
                     }
                 }
             } else {
@@ -338,12 +342,21 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
                     // messages: P - L = P + D; a fresh shot has no old messages)
                     if (!(PQ && fresh)) {
                         if constexpr (TM) {
-                            uint32_t o[2 * DC];
                             __syncwarp();
-                            tmem_ld20(tm + (uint32_t)(2 * p * DC), o);
+                            if (uni) {
+                                // the previous round was the closed form: one message per check
+                                uint32_t d0, d1;
+                                tmem_ld2(tm + (uint32_t)(2 * p * DC), d0, d1);
+                                const float2 d = make_float2(__uint_as_float(d0), __uint_as_float(d1));
 #pragma unroll
-                            for (int j = 0; j < DC; ++j)
-                                v[p][j] = add2(v[p][j], make_float2(__uint_as_float(o[2 * j]), __uint_as_float(o[2 * j + 1])));
+                                for (int j = 0; j < DC; ++j) v[p][j] = add2(v[p][j], d);
+                            } else {
+                                uint32_t o[2 * DC];
+                                tmem_ld20(tm + (uint32_t)(2 * p * DC), o);
+#pragma unroll
+                                for (int j = 0; j < DC; ++j)
+                                    v[p][j] = add2(v[p][j], make_float2(__uint_as_float(o[2 * j]), __uint_as_float(o[2 * j + 1])));
+                            }
                         } else {
 #pragma unroll
                             for (int j = 0; j < DC; ++j)
@@ -462,6 +475,7 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
                 }
             }
             if constexpr (TM) tmem_wait_st();   // this round's stores land before the next reads
+            uni = fresh && !PQ && !BPK;
         }
         qc_sync<T, GC>(g);
 

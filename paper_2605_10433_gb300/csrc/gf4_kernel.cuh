@@ -61,8 +61,11 @@ struct Gf4Layout {
     const uint32_t* vneT;   // [DV][Np]
 };
 
+// Up to d_c = 10 the kernel fits 64 registers without spilling, so two 512-thread CTAs (eight
+// of the 128 threads an m <= 128 code launches) share an SM; larger slot counts keep the
+// register budget of one 512-thread CTA.
 template <int DC, int DV, bool BP>
-__global__ void __launch_bounds__(512) gf4_kernel(const DecodeArgs a, const Gf4Layout lay) {
+__global__ void __launch_bounds__(512, DC <= 10 ? 2 : 1) gf4_kernel(const DecodeArgs a, const Gf4Layout lay) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int t = threadIdx.x;
     const int T = blockDim.x;   // == Mp

@@ -70,15 +70,15 @@ __device__ __forceinline__ void tmem_st20(uint32_t taddr, const uint32_t (&r)[20
                  : "memory");
 }
 
-// Store x, y, x, y, ... to 16 + 4 consecutive columns (two checks, each with equal outputs).
-__device__ __forceinline__ void tmem_st20_alt(uint32_t taddr, uint32_t x, uint32_t y) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %1, %2, %1, %2, %1, %2, %1, %2, %1, %2, %1, %2, %1, %2};" ::"r"(
-            taddr),
-        "r"(x), "r"(y)
-        : "memory");
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %1, %2};" ::"r"(taddr + 16u), "r"(x), "r"(y)
-                 : "memory");
+// Store x, y to 2 consecutive columns.
+__device__ __forceinline__ void tmem_st2(uint32_t taddr, uint32_t x, uint32_t y) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(taddr), "r"(x), "r"(y) : "memory");
+}
+
+// Load 2 consecutive columns of the thread's lane into x, y, then wait for them.
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t& x, uint32_t& y) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];" : "=r"(x), "=r"(y) : "r"(taddr) : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(x), "+r"(y) : : "memory");
 }
 
 }  // namespace sagms

@@ -35,6 +35,30 @@ def ops_per_iteration(mode: str, row_ptr, col_idx, n: int) -> int:
     return cn + vn + edges + len(dc)
 
 
+# Quaternary variable node (Sec. II, scalar messages): per qubit of degree d_v, the three Pauli
+# totals Lambda(X), Lambda(Z), Lambda(Y) take two additions per edge (an edge's message enters
+# the two Paulis that anticommute with its entry), the decision argmin(0, Lambda(X), Lambda(Z),
+# Lambda(Y)) three comparisons, and each of the three commute LLRs
+# lambda_T = ln(1 + e^{-Lambda(T)}) - ln(e^{-Lambda(T')} + e^{-Lambda(T'')}) two exponentials
+# and two logarithms (weight 10 each, as Eq. 15 weighs transcendentals) plus four simple
+# operations; every edge then takes one subtraction for its extrinsic message.
+GF4_LAMBDA_OPS = 4 * 10 + 4
+
+
+def gf4_ops_per_iteration(mode: str, row_ptr, col_idx, n: int) -> int:
+    """One iteration of the GF(4) decoder on a stabilizer matrix with Pauli entries: the check
+    rule of Eq. 15 / Table I per row (BP4 for mode "bp"), the quaternary variable node above
+    (3 d_v + 3 + 3 x 44 per qubit), one anticommutation test per edge for the residual
+    syndrome (Eq. 1 with the trace inner product) and one popcount step per check."""
+    row_ptr = np.asarray(row_ptr)
+    dc = np.diff(row_ptr)
+    dv = np.bincount(np.asarray(col_idx), minlength=n)
+    cn = int(sum(CN_OPS[mode](int(d)) for d in dc))
+    vn = int((3 * dv + 3 + 3 * GF4_LAMBDA_OPS).sum())
+    edges = int(row_ptr[-1])
+    return cn + vn + edges + len(dc)
+
+
 def alu_peak_ops(sms: int, sm_mhz: float) -> float:
     """Thread-instruction issue rate of the whole GPU: SMs x 128 lanes x clock."""
     return sms * THREAD_OPS_PER_SM_CLK * sm_mhz * 1e6

@@ -184,6 +184,23 @@ def test_op_count_model_matches_eq15_and_table1():
     assert roofline.smem_peak_bytes(152, 2070) == 152 * 128 * 2070e6
 
 
+def test_gf4_op_count_model():
+    """The GF(4) iteration count on the CSS stack of GB(63, 5): m = n = 126, every row and every
+    qubit of degree 10 (five X-type and five Z-type rows per qubit), E = 1260.  Per check the
+    Eq. 15 rule; per qubit 2 d_v Pauli-total additions, d_v extrinsic subtractions, 3 decision
+    comparisons and three commute LLRs of four transcendentals (weight 10) and four simple
+    operations each; one anticommutation test per edge and one popcount step per check."""
+    from paper_2605_10433_gb300 import roofline
+    from paper_2605_10433_gb300 import inputs as I
+    from paper_2605_10433_gb300.inputs import gf4 as I4
+    g = I4.css_code(I.gb_code(63, 5))
+    assert (g.m, g.n, g.nnz) == (126, 126, 1260)
+    vn = 126 * (2 * 10 + 10 + 3 + 3 * (4 * 10 + 4))
+    assert roofline.gf4_ops_per_iteration("sagms", g.row_ptr, g.col_idx, g.n) == 126 * 23 + vn + 1260 + 126
+    assert roofline.gf4_ops_per_iteration("bp", g.row_ptr, g.col_idx, g.n) == 126 * 207 + vn + 1260 + 126
+    assert roofline.gf4_ops_per_iteration("sms", g.row_ptr, g.col_idx, g.n) == 126 * 18 + vn + 1260 + 126
+
+
 @pytest.mark.parametrize("rows,pauli,n,err", [
     ([[0, 1], [1, 2]], [1, 2, 3, 4], 3, "SAGMS_ERR_CSR"),        # Pauli code 4
     ([[0, 1], [1, 2]], [1, 0, 3, 1], 3, "SAGMS_ERR_CSR"),        # Pauli code 0 (identity entry)
