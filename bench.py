@@ -310,12 +310,16 @@ def bench_gf4(S, I, steps, shots=1_000_000):
     _, _, syn = I4.depolarizing(g, eps, shots, seed=NOISE_SEED + 4)
     d_syn = torch.from_numpy(syn.view(np.int32)).cuda()
     out = {"workload": f"CSS stack of GB l=63 w=5 ([[126,{g.k}]], m=126, d_c=d_v=10), depolarising eps={eps}, "
-                       f"{shots:.0e} shots, max_iter={MAX_ITER}, GF(4) scalar messages"}
+                       f"{shots:.0e} shots, max_iter={MAX_ITER}, GF(4) scalar messages",
+           "kernel": "gf4_css_kernel<10,5> (column-indexed)" if dc.css_layout else "gf4_kernel<10,10>"}
     runs = [("sagms", S.Params(mode="sagms", max_iter=MAX_ITER, **SAGMS_KW), eps),
             ("sms", S.Params(mode="sms", alpha=0.5, max_iter=MAX_ITER), eps),
             ("bp4", S.Params(mode="bp", max_iter=MAX_ITER), eps),
             ("sagms_mismatch", S.Params(mode="sagms", max_iter=MAX_ITER, **SAGMS_KW), 0.1),
-            ("bp4_mismatch", S.Params(mode="bp", max_iter=MAX_ITER), 0.1)]
+            ("bp4_mismatch", S.Params(mode="bp", max_iter=MAX_ITER), 0.1),
+            # the same SAGMS decode on the generic (index-list) kernel, for comparison
+            ("sagms_generic_kernel", S.Params(mode="sagms", max_iter=MAX_ITER, flags=S.FLAG_GENERIC_KERNEL, **SAGMS_KW),
+             eps)]
     stream = torch.cuda.current_stream()
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     peak = roofline.alu_peak_ops(props.multi_processor_count, float(measured_peaks().get("sm_max_mhz") or 2070.0))

@@ -466,17 +466,28 @@ int sagms_mc_run(const sagms_code* code, const sagms_params* params, uint64_t se
  * sagms_gf4_decode: d_syn [shots][ceil(m/32)] u32 packed syndrome bits s_i = <E, H_i> (trace
  * inner product); d_L0 [shots] f32 one prior LLR per shot (the same for X, Z, Y); outputs
  * d_err [shots][2][ceil(n/32)] u32 (the x bits, then the z bits of e_hat: X = x, Z = z, Y = both),
- * d_conv [shots] u8, d_iters [shots] i32 as sagms_decode.  Parameters as sagms_decode; flags: only
- * SAGMS_FLAG_NO_EARLY_STOP.  Device buffers caller-owned, 4-byte aligned; asynchronous on
+ * d_conv [shots] u8, d_iters [shots] i32 as sagms_decode.  Parameters as sagms_decode; flags:
+ * SAGMS_FLAG_NO_EARLY_STOP and SAGMS_FLAG_GENERIC_KERNEL (below) only.  Device buffers caller-owned, 4-byte aligned; asynchronous on
  * `stream`.  sagms_gf4_decode_trace also writes d_trace [shots][max_iter+1][n][3] f32: Lambda(X),
  * Lambda(Z), Lambda(Y) of every qubit at every checked round.
  * Errors: as sagms_decode, plus SAGMS_ERR_PARAM for other flags and SAGMS_ERR_SIZE when the code's
  * state does not fit a CTA's shared memory.
+ *
+ * Kernels: a CSS matrix (every row all X or all Z, as the paper's stack of H_X over H_Z) whose
+ * rows of each type have a column-indexed slot assignment (sagms_column_slots with D = the
+ * largest per-type qubit degree rounded up to a compiled shape: 3, 4, 5, 6 or 8 message rows)
+ * is decoded by the column-indexed CSS kernel when its state fits a CTA's shared memory; any
+ * other matrix, or SAGMS_FLAG_GENERIC_KERNEL in params->flags, by the generic kernel.  The two
+ * run the same rounds and arithmetic per check and qubit and differ only in the order of each
+ * qubit's message sums.  sagms_gf4_layout returns 1 when a loaded code takes the CSS kernel,
+ * 0 when it takes the generic one, SAGMS_ERR_ARG for a NULL code (no paper counterpart: a
+ * property of this library's kernels).
  */
 typedef struct sagms_gf4_code sagms_gf4_code;
 int sagms_gf4_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
                         const uint8_t* pauli, sagms_gf4_code** out);
 void sagms_gf4_free_code(sagms_gf4_code* code);
+int sagms_gf4_layout(const sagms_gf4_code* code);
 int sagms_gf4_decode(const sagms_gf4_code* code, const sagms_params* params, int64_t shots, const uint32_t* d_syn,
                      const float* d_L0, uint32_t* d_err, uint8_t* d_conv, int32_t* d_iters, void* stream);
 int sagms_gf4_decode_trace(const sagms_gf4_code* code, const sagms_params* params, int64_t shots,

@@ -102,6 +102,12 @@ class Gf4DeviceCode:
     def nw(self):
         return (self.n + 31) // 32
 
+    @property
+    def css_layout(self) -> bool:
+        """True when the code takes the column-indexed CSS kernel (a CSS matrix with a slot
+        assignment per row type), False for the generic kernel."""
+        return self._native.sagms_gf4_layout(self.handle) == 1
+
     def close(self):
         if getattr(self, "handle", None):
             self._native.sagms_gf4_free_code(self.handle)
@@ -122,8 +128,9 @@ def gf4_decode(code: Gf4DeviceCode, syn, L0, params: Params | None = None, strea
     import torch
     from . import _native
     p = params or Params()
-    if p.flags & ~FLAG_NO_EARLY_STOP:
-        raise ValueError("the GF(4) decoder takes one prior per shot and no flag but FLAG_NO_EARLY_STOP")
+    if p.flags & ~(FLAG_NO_EARLY_STOP | FLAG_GENERIC_KERNEL):
+        raise ValueError("the GF(4) decoder takes one prior per shot and no flag but FLAG_NO_EARLY_STOP "
+                         "and FLAG_GENERIC_KERNEL")
     dev = f"cuda:{code.device}"
     for name, a, dt in (("syn", syn, (torch.int32, torch.uint32) if hasattr(torch, "uint32") else (torch.int32,)),
                         ("L0", L0, (torch.float32,))):

@@ -80,6 +80,7 @@ def _load_library():
         "sagms_set_launch_limit": (ctypes.c_int, [vp, i64]),
         "sagms_gf4_load_code": (ctypes.c_int, [i32, i32, i64, P(i32), P(i32), P(ctypes.c_uint8), P(vp)]),
         "sagms_gf4_free_code": (None, [vp]),
+        "sagms_gf4_layout": (ctypes.c_int, [vp]),
         "sagms_gf4_decode": (ctypes.c_int, [vp, P(sagms_params), i64, vp, vp, vp, vp, vp, vp]),
         "sagms_gf4_decode_trace": (ctypes.c_int, [vp, P(sagms_params), i64, vp, vp, vp, vp, vp, vp, vp]),
         "sagms_server_create": (ctypes.c_int, [ctypes.c_size_t, i32, i32, i32, P(vp)]),
@@ -263,6 +264,13 @@ def sagms_gf4_load_code(m, n, row_ptr, col_idx, pauli):
                                     ci.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                     pa.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), ctypes.byref(out)))
     return out.value
+
+
+def sagms_gf4_layout(handle):
+    """1 when the loaded GF(4) code takes the column-indexed CSS kernel, 0 for the generic one."""
+    rc = _lib.sagms_gf4_layout(handle)
+    _check(min(rc, 0))
+    return rc
 
 
 def sagms_gf4_free_code(handle):

@@ -1,4 +1,5 @@
-// Quaternary (GF(4)) decoding: code loading and launches of gf4_kernel (gf4_kernel.cuh).
+// Quaternary (GF(4)) decoding: code loading and launches of gf4_kernel (gf4_kernel.cuh, any
+// stabilizer matrix) and gf4_css_kernel (gf4_css_kernel.cuh, CSS matrices).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -6,8 +7,10 @@
 #include <cstring>
 #include <vector>
 
+#include "gf4_css_kernel.cuh"
 #include "gf4_kernel.cuh"
 #include "internal.h"
+#include "sagms.h"
 
 using sagms::DecodeArgs;
 using sagms::Gf4Layout;
@@ -29,13 +32,82 @@ const Gf4Variant kGf4Variants[] = {SAGMS_GF4(6, 6), SAGMS_GF4(8, 8), SAGMS_GF4(1
 #undef SAGMS_GF4
 constexpr int kNumGf4 = sizeof(kGf4Variants) / sizeof(kGf4Variants[0]);
 
+// Column-indexed CSS shapes: DC check slots, DH message rows per row type (DC = 2 DH); a code
+// takes the first that covers its check degree and its largest per-type qubit degree.
+struct Gf4CssVariant {
+    int dc, dh;
+    void (*fn[2])(const DecodeArgs, const uint32_t*);   // MS family, BP
+};
+#define SAGMS_GF4_CSS(DC, DH) \
+    Gf4CssVariant { DC, DH, {sagms::gf4_css_kernel<DC, DH, false>, sagms::gf4_css_kernel<DC, DH, true>} }
+const Gf4CssVariant kGf4CssVariants[] = {SAGMS_GF4_CSS(6, 3), SAGMS_GF4_CSS(8, 4), SAGMS_GF4_CSS(10, 5),
+                                         SAGMS_GF4_CSS(12, 6), SAGMS_GF4_CSS(16, 8)};
+#undef SAGMS_GF4_CSS
+constexpr int kNumGf4Css = sizeof(kGf4CssVariants) / sizeof(kGf4CssVariants[0]);
+
 }  // namespace
 
 struct sagms_gf4_code {
     int m, n, nnz, dc_max, dv_max, variant, Mp, Np, device;
+    uint32_t pauli_set;   // bit P: the matrix has an entry of Pauli P (1 X, 2 Z, 3 Y)
     uint16_t* d_colT;
     uint32_t* d_vneT;
+    int css_variant;      // column-indexed CSS shape, or -1 (not CSS, or no slot assignment)
+    uint32_t* d_colS;     // [DC][Mp] biased byte offsets of the CSS kernel
 };
+
+namespace {
+
+// The column-indexed layout of a CSS matrix (every row all X or all Z): per row type, slots from
+// sagms_column_slots on that type's rows (distinct mod DH among each qubit's edges of the type),
+// then the biased byte offsets colS[j][i] = 4 col + (type Z ? half : 0); padded slots and checks
+// past m point at the padding column n of the X half.  Returns the shape, or -1.
+int css_layout(int m, int n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* pauli, int dc_max,
+               int Mp, int Np, std::vector<uint32_t>& colS) {
+    std::vector<int> type(m, 0);
+    for (int i = 0; i < m; ++i) {
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            if (pauli[e] == 3 || (type[i] != 0 && type[i] != pauli[e])) return -1;
+            type[i] = pauli[e];
+        }
+    }
+    std::vector<int> dvt[2] = {std::vector<int>(n, 0), std::vector<int>(n, 0)};
+    for (int i = 0; i < m; ++i)
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) dvt[type[i] == 2][col_idx[e]]++;
+    int dh_need = 1;
+    for (int h = 0; h < 2; ++h) dh_need = std::max(dh_need, *std::max_element(dvt[h].begin(), dvt[h].end()));
+    int var = -1;
+    for (int v = 0; v < kNumGf4Css && var < 0; ++v)
+        if (kGf4CssVariants[v].dc >= dc_max && kGf4CssVariants[v].dh >= dh_need) var = v;
+    if (var < 0) return -1;
+    const int DC = kGf4CssVariants[var].dc, DH = kGf4CssVariants[var].dh;
+    const uint32_t half = (uint32_t)sagms::gf4_css_half_bytes(DH, Np);
+    colS.assign((size_t)DC * Mp, (uint32_t)n * 4u);
+    for (int h = 0; h < 2; ++h) {
+        // this type's rows as their own CSR (rows without edges count as X rows and stay padded)
+        std::vector<int> rows;
+        std::vector<int32_t> rp(1, 0), ci;
+        for (int i = 0; i < m; ++i) {
+            if ((type[i] == 2) != (h == 1)) continue;
+            rows.push_back(i);
+            for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) ci.push_back(col_idx[e]);
+            rp.push_back((int32_t)ci.size());
+        }
+        if (rows.empty()) continue;
+        std::vector<int32_t> slot(ci.size());
+        if (sagms_column_slots((int32_t)rows.size(), n, (int64_t)ci.size(), rp.data(), ci.data(), DH, slot.data()) !=
+            SAGMS_OK)
+            return -1;
+        for (size_t r = 0; r < rows.size(); ++r)
+            for (int e = rp[r]; e < rp[r + 1]; ++e) {
+                if (slot[e] < 0 || slot[e] >= DC) return -1;
+                colS[(size_t)slot[e] * Mp + rows[r]] = (uint32_t)ci[e] * 4u + (h ? half : 0u);
+            }
+    }
+    return var;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -48,6 +120,7 @@ int sagms_gf4_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_pt
     if (row_ptr[0] != 0 || row_ptr[m] != nnz) return gfail(SAGMS_ERR_CSR, "row_ptr must run from 0 to nnz");
     std::vector<int> dv(n, 0);
     int dc_max = 0;
+    uint32_t pauli_set = 0;
     for (int i = 0; i < m; ++i) {
         if (row_ptr[i + 1] < row_ptr[i]) return gfail(SAGMS_ERR_CSR, "row_ptr decreases");
         dc_max = std::max(dc_max, row_ptr[i + 1] - row_ptr[i]);
@@ -57,6 +130,7 @@ int sagms_gf4_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_pt
             for (int f = row_ptr[i]; f < e; ++f)
                 if (col_idx[f] == col_idx[e]) return gfail(SAGMS_ERR_CSR, "duplicate column in a row");
             dv[col_idx[e]]++;
+            pauli_set |= 1u << pauli[e];
         }
     }
     const int dv_max = *std::max_element(dv.begin(), dv.end());
@@ -79,19 +153,25 @@ int sagms_gf4_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_pt
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce != cudaSuccess) return sagms_internal::cuda_error(ce, "cudaGetDevice");
+    std::vector<uint32_t> colS;
+    const int css = css_layout(m, n, row_ptr, col_idx, pauli, dc_max, Mp, Np, colS);
     sagms_gf4_code* code = new sagms_gf4_code();
     code->m = m; code->n = n; code->nnz = (int)nnz; code->dc_max = dc_max; code->dv_max = dv_max;
-    code->variant = variant; code->Mp = Mp; code->Np = Np; code->device = dev;
-    code->d_colT = nullptr; code->d_vneT = nullptr;
+    code->variant = variant; code->Mp = Mp; code->Np = Np; code->device = dev; code->pauli_set = pauli_set;
+    code->d_colT = nullptr; code->d_vneT = nullptr; code->css_variant = css; code->d_colS = nullptr;
     ce = cudaMalloc(reinterpret_cast<void**>(&code->d_colT), colT.size() * sizeof(uint16_t));
     if (ce == cudaSuccess) ce = cudaMalloc(reinterpret_cast<void**>(&code->d_vneT), vneT.size() * sizeof(uint32_t));
+    if (ce == cudaSuccess && css >= 0) ce = cudaMalloc(reinterpret_cast<void**>(&code->d_colS), colS.size() * 4);
     if (ce == cudaSuccess)
         ce = cudaMemcpy(code->d_colT, colT.data(), colT.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
     if (ce == cudaSuccess)
         ce = cudaMemcpy(code->d_vneT, vneT.data(), vneT.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess && css >= 0)
+        ce = cudaMemcpy(code->d_colS, colS.data(), colS.size() * 4, cudaMemcpyHostToDevice);
     if (ce != cudaSuccess) {
         cudaFree(code->d_colT);
         cudaFree(code->d_vneT);
+        cudaFree(code->d_colS);
         delete code;
         return sagms_internal::cuda_error(ce, "sagms_gf4_load_code upload");
     }
@@ -103,6 +183,7 @@ void sagms_gf4_free_code(sagms_gf4_code* code) {
     if (!code) return;
     cudaFree(code->d_colT);
     cudaFree(code->d_vneT);
+    cudaFree(code->d_colS);
     delete code;
 }
 
@@ -113,8 +194,9 @@ int sagms_gf4_decode_trace(const sagms_gf4_code* code, const sagms_params* p, in
     if (!code) return gfail(SAGMS_ERR_ARG, "code is NULL");
     int rc = sagms_check_params(p);
     if (rc != SAGMS_OK) return rc;
-    if (p->flags & ~(uint32_t)SAGMS_FLAG_NO_EARLY_STOP)
-        return gfail(SAGMS_ERR_PARAM, "the GF(4) decoder takes one prior per shot and no flag but SAGMS_FLAG_NO_EARLY_STOP");
+    if (p->flags & ~(uint32_t)(SAGMS_FLAG_NO_EARLY_STOP | SAGMS_FLAG_GENERIC_KERNEL))
+        return gfail(SAGMS_ERR_PARAM, "the GF(4) decoder takes one prior per shot and no flag but "
+                                      "SAGMS_FLAG_NO_EARLY_STOP and SAGMS_FLAG_GENERIC_KERNEL");
     if (shots < 0) return gfail(SAGMS_ERR_ARG, "shots < 0");
     if (shots == 0) return SAGMS_OK;
     if (!d_syn || !d_L0 || !d_err || !d_conv || !d_iters) return gfail(SAGMS_ERR_ARG, "NULL device buffer");
@@ -136,16 +218,35 @@ int sagms_gf4_decode_trace(const sagms_gf4_code* code, const sagms_params* p, in
     a.inv_m = 1.0f / (float)code->m;
     a.dcmax = code->dc_max;
     a.max_iter = p->max_iter;
-    a.flags = p->flags;
+    a.flags = (p->flags & SAGMS_FLAG_NO_EARLY_STOP) | (code->pauli_set << sagms::kGf4PauliShift);
     a.shots = shots;
     a.syn = d_syn; a.L0 = d_L0; a.err = d_err; a.conv = d_conv; a.iters = d_iters; a.trace = d_trace;
-    const Gf4Variant& v = kGf4Variants[code->variant];
-    auto fn = v.fn[p->mode == SAGMS_BP ? 1 : 0];
-    const size_t smem = sagms::gf4_smem_bytes(v.dc, v.dv, code->Mp, code->Np);
     int smem_optin = 0, sms = 0;
     ce = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (ce != cudaSuccess) return sagms_internal::cuda_error(ce, "device attributes");
+    const int bp = p->mode == SAGMS_BP ? 1 : 0;
+    if (code->css_variant >= 0 && !(p->flags & SAGMS_FLAG_GENERIC_KERNEL)) {
+        // the column-indexed CSS kernel, when its two halves fit a CTA
+        const Gf4CssVariant& cv = kGf4CssVariants[code->css_variant];
+        const size_t smem = sagms::gf4_css_smem_bytes(cv.dh, code->Np);
+        if (smem <= (size_t)smem_optin) {
+            auto fn = cv.fn[bp];
+            ce = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (ce != cudaSuccess) return sagms_internal::cuda_error(ce, "cudaFuncSetAttribute");
+            int per_sm = 0;
+            ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, code->Mp, smem);
+            if (ce != cudaSuccess) return sagms_internal::cuda_error(ce, "occupancy query");
+            if (per_sm < 1) return gfail(SAGMS_ERR_SIZE, "kernel does not fit on an SM");
+            const long long grid = std::min<long long>(shots, (long long)per_sm * sms);
+            fn<<<(unsigned)grid, code->Mp, smem, static_cast<cudaStream_t>(stream_v)>>>(a, code->d_colS);
+            ce = cudaGetLastError();
+            return ce == cudaSuccess ? SAGMS_OK : sagms_internal::cuda_error(ce, "gf4 css decode launch");
+        }
+    }
+    const Gf4Variant& v = kGf4Variants[code->variant];
+    auto fn = v.fn[bp];
+    const size_t smem = sagms::gf4_smem_bytes(v.dc, v.dv, code->Mp, code->Np);
     if (smem > (size_t)smem_optin) return gfail(SAGMS_ERR_SIZE, "code needs more shared memory than a CTA has");
     ce = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (ce != cudaSuccess) return sagms_internal::cuda_error(ce, "cudaFuncSetAttribute");
@@ -158,6 +259,11 @@ int sagms_gf4_decode_trace(const sagms_gf4_code* code, const sagms_params* p, in
     fn<<<(unsigned)grid, code->Mp, smem, static_cast<cudaStream_t>(stream_v)>>>(a, lay);
     ce = cudaGetLastError();
     return ce == cudaSuccess ? SAGMS_OK : sagms_internal::cuda_error(ce, "gf4 decode launch");
+}
+
+int sagms_gf4_layout(const sagms_gf4_code* code) {
+    if (!code) return gfail(SAGMS_ERR_ARG, "code is NULL");
+    return code->css_variant >= 0 ? 1 : 0;
 }
 
 int sagms_gf4_decode(const sagms_gf4_code* code, const sagms_params* p, int64_t shots, const uint32_t* d_syn,

@@ -51,6 +51,10 @@ __device__ __forceinline__ float gf4_lse_neg(float b, float c) {
     return -lo + log1pf(expf(lo - hi));
 }
 
+// DecodeArgs::flags bits kGf4PauliShift + P, P = 1 (X), 2 (Z), 3 (Y): the matrix has an entry
+// of Pauli P.  Internal to the GF(4) launch, above every public flag bit.
+constexpr int kGf4PauliShift = 8;
+
 __host__ __device__ inline size_t gf4_smem_bytes(int DC, int DV, int Mp, int Np) {
     const size_t floats = 3 * (size_t)Np + 2 * ((size_t)DC * Mp + 4);
     return floats * 4 + (size_t)Np + (size_t)DC * Mp * 2 + (size_t)DV * Np * 4 + 64;
@@ -73,6 +77,8 @@ __global__ void __launch_bounds__(512, DC <= 10 ? 2 : 1) gf4_kernel(const Decode
     const int Mp = a.Mp, Np = a.Np, n = a.n, m = a.m;
     const int mw = (m + 31) >> 5, nw = (n + 31) >> 5;
     const bool early = (a.flags & kFlagNoEarlyStop) == 0;
+    // bit P (1 X, 2 Z, 3 Y): the matrix has an entry of Pauli P (set by the host)
+    const uint32_t pauli_set = (a.flags >> kGf4PauliShift) & 0xeu;
     float* LX = reinterpret_cast<float*>(smem);
     float* LZ = LX + Np;
     float* LY = LZ + Np;
@@ -94,8 +100,21 @@ __global__ void __launch_bounds__(512, DC <= 10 ? 2 : 1) gf4_kernel(const Decode
     if (t < 4) C[DC * Mp + t] = 0.0f;
     const float clip = BP ? kBpClip : kMsFamClip;
 
+    // The next shot's prior and syndrome word are loaded one shot ahead, so their latency
+    // overlaps the current shot's rounds.
+    float l0_next = 0.0f;
+    uint32_t sw_next = 0u;
+    if (blockIdx.x < a.shots) {
+        l0_next = __ldg(a.L0 + blockIdx.x);
+        sw_next = (t < m) ? __ldg(a.syn + (long long)blockIdx.x * mw + (t >> 5)) : 0u;
+    }
     for (long long shot = blockIdx.x; shot < a.shots; shot += gridDim.x) {
-        const float l0 = __ldg(a.L0 + shot);
+        const float l0 = l0_next;
+        const uint32_t sw = sw_next;
+        if (shot + gridDim.x < a.shots) {
+            l0_next = __ldg(a.L0 + shot + gridDim.x);
+            sw_next = (t < m) ? __ldg(a.syn + (shot + gridDim.x) * mw + (t >> 5)) : 0u;
+        }
         if (!isfinite(l0)) {
             for (int w = t; w < 2 * nw; w += T) a.err[shot * 2 * nw + w] = 0u;
             if (t == 0) { a.conv[shot] = 0; a.iters[shot] = -1; }
@@ -115,7 +134,7 @@ __global__ void __launch_bounds__(512, DC <= 10 ? 2 : 1) gf4_kernel(const Decode
             C[j * Mp + t] = 0.0f;
             if ((colT[j * Mp + t] & 0x3fffu) != (uint16_t)n) Lam[j * Mp + t] = lam0;
         }
-        const uint32_t s_bit = (t < m) ? ((__ldg(a.syn + shot * mw + (t >> 5)) >> (t & 31)) & 1u) : 0u;
+        const uint32_t s_bit = (t < m) ? ((sw >> (t & 31)) & 1u) : 0u;
         if (t == 0) { cnt_sh[0] = 0; cnt_sh[1] = 0; }
         __syncthreads();
 
@@ -227,9 +246,11 @@ __global__ void __launch_bounds__(512, DC <= 10 ? 2 : 1) gf4_kernel(const Decode
                 // the two Paulis anticommuting with its entry T, so removing it multiplies
                 // e^{-Lambda(T')} + e^{-Lambda(T'')} by e^{r} and leaves Lambda(T): the
                 // extrinsic message is lambda_T(Lambda) - r.
-                const float lamX = gf4_softplus_neg(lx) - gf4_lse_neg(lz, ly);
-                const float lamZ = gf4_softplus_neg(lz) - gf4_lse_neg(lx, ly);
-                const float lamY = gf4_softplus_neg(ly) - gf4_lse_neg(lx, lz);
+                // Only the Paulis the matrix has entries of need their lambda (a CSS stack has
+                // no Y entry, so lambda_Y is skipped there); the others are never selected.
+                const float lamX = (pauli_set & 2u) ? gf4_softplus_neg(lx) - gf4_lse_neg(lz, ly) : 0.0f;
+                const float lamZ = (pauli_set & 4u) ? gf4_softplus_neg(lz) - gf4_lse_neg(lx, ly) : 0.0f;
+                const float lamY = (pauli_set & 8u) ? gf4_softplus_neg(ly) - gf4_lse_neg(lx, lz) : 0.0f;
 #pragma unroll
                 for (int q = 0; q < DV; ++q) {
                     if (pt[q] == 0u) continue;

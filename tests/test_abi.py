@@ -225,6 +225,7 @@ def test_gf4_decode_refuses_before_any_launch(native):
     lib = native.lib()
     err_arg = -1
     assert lib.sagms_gf4_decode(None, ctypes.byref(p), 10, 16, 16, 16, 16, 16, None) == err_arg
+    assert lib.sagms_gf4_layout(None) == err_arg
     assert lib.sagms_gf4_load_code(600, 10, 0, None, None, None, None) == err_arg   # out is NULL
     out = ctypes.c_void_p()
     rp = np.zeros(601, dtype=np.int32)

@@ -33,6 +33,8 @@ MODES = {
     "sagms": (S.Params(mode="sagms", alpha_min=0.30, alpha_max=0.50, eta_unsat=1.10, max_iter=100), oracle.SAGMS),
 }
 MISMATCH_CAP = 2e-3
+# the column-indexed CSS kernel (the default for the CSS stack) and the generic kernel forced
+KERNELS = {"css": 0, "generic": S.FLAG_GENERIC_KERNEL}
 
 
 @pytest.fixture(scope="module")
@@ -40,7 +42,13 @@ def setting():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     g = I4.css_code(I.gb_code(63, 5))
-    return g, S.Gf4DeviceCode(g)
+    dc = S.Gf4DeviceCode(g)
+    assert dc.css_layout
+    return g, dc
+
+
+def _with_kernel(p, kernel):
+    return S.Params(**{**p.__dict__, "flags": p.flags | KERNELS[kernel]})
 
 
 def _run(g, dc, syn, L0, p, mode_o, trace=False, threads=16):
@@ -53,8 +61,8 @@ def _run(g, dc, syn, L0, p, mode_o, trace=False, threads=16):
     if trace:
         gres["trace"] = out[3].cpu().numpy()
     o = O4.decode(g, syn, L0.astype(np.float64), mode=mode_o, alpha=p.alpha, alpha_min=p.alpha_min,
-                  alpha_max=p.alpha_max, eta_unsat=p.eta_unsat, max_iter=p.max_iter, flags=p.flags, trace=trace,
-                  threads=threads)
+                  alpha_max=p.alpha_max, eta_unsat=p.eta_unsat, max_iter=p.max_iter,
+                  flags=p.flags & ~S.FLAG_GENERIC_KERNEL, trace=trace, threads=threads)
     return gres, o
 
 
@@ -107,14 +115,16 @@ def _check_mismatches(g, dc, syn, L0, p, mo, gr, o):
     return near, amp, worst
 
 
+@pytest.mark.parametrize("kernel", ["css", "generic"])
 @pytest.mark.parametrize("eps,eps0", [(0.01, 0.01), (0.02, 0.02), (0.01, 0.1), (0.02, 0.1)])
 @pytest.mark.parametrize("mode", ["bp", "sms", "sagms"])
-def test_gf4_fer_parity(setting, mode, eps, eps0):
+def test_gf4_fer_parity(setting, mode, eps, eps0, kernel):
     g, dc = setting
     shots = 100_000
     _, _, syn = I4.depolarizing(g, eps, shots, seed=int(9000 + 1000 * eps + 100 * eps0))
     L0 = np.full(shots, I4.prior(eps0), dtype=np.float32)
     p, mo = MODES[mode]
+    p = _with_kernel(p, kernel)
     gr, o = _run(g, dc, syn, L0, p, mo)
     same = _same(gr, o)
     bad = np.nonzero(~same)[0]
@@ -125,19 +135,20 @@ def test_gf4_fer_parity(setting, mode, eps, eps0):
     near, amp, worst = _check_mismatches(g, dc, syn, L0, p, mo, gr, o)
     assert near <= int(1e-4 * shots + 1e-6), f"{near} near-ties of {shots}"
     assert len(bad) <= MISMATCH_CAP * shots, f"{len(bad)} mismatching shots of {shots}"
-    print(f"gf4 GB(63,5) CSS eps={eps} eps0={eps0} {mode}: FER gpu {fer_g:.3e} oracle {fer_o:.3e} "
+    print(f"gf4 GB(63,5) CSS {kernel} kernel eps={eps} eps0={eps0} {mode}: FER gpu {fer_g:.3e} oracle {fer_o:.3e} "
           f"[{lo:.3e}, {hi:.3e}] McNemar p {pm:.3g}, mismatches {len(bad)} (near-tie {near}, amplified {amp}, "
           f"shadow worst {worst:.3g}), "
           f"mean iters {gr['iters'].mean():.2f}")
 
 
+@pytest.mark.parametrize("kernel", ["css", "generic"])
 @pytest.mark.parametrize("mode", ["bp", "sms", "sagms"])
-def test_gf4_posterior_traces(setting, mode):
+def test_gf4_posterior_traces(setting, mode, kernel):
     g, dc = setting
     _, _, syn = I4.depolarizing(g, 0.03, 64, seed=321)
     L0 = np.full(64, I4.prior(0.03), dtype=np.float32)
     p, mo = MODES[mode]
-    p = S.Params(**{**p.__dict__, "max_iter": 30})
+    p = _with_kernel(S.Params(**{**p.__dict__, "max_iter": 30}), kernel)
     gt, ot = _run(g, dc, syn, L0, p, mo, trace=True)
     worst = 0.0
     for s in range(64):
@@ -152,15 +163,16 @@ def test_gf4_posterior_traces(setting, mode):
             assert e <= 1e-5, f"shot {s} check {l}: normwise error {e:.3g}"
             if (da != db).any():
                 break
-    print(f"gf4 traces {mode}: normwise error {worst:.2e} over the first rounds")
+    print(f"gf4 traces {kernel} kernel {mode}: normwise error {worst:.2e} over the first rounds")
 
 
-def test_gf4_edge_cases(setting):
+@pytest.mark.parametrize("kernel", ["css", "generic"])
+def test_gf4_edge_cases(setting, kernel):
     g, dc = setting
     z = torch.zeros((50, g.mw), dtype=torch.int32, device="cuda")
     L0 = torch.full((50,), float(I4.prior(0.01)), dtype=torch.float32, device="cuda")
     L0[7] = float("nan")
-    err, conv, iters = S.gf4_decode(dc, z, L0, MODES["sagms"][0])
+    err, conv, iters = S.gf4_decode(dc, z, L0, _with_kernel(MODES["sagms"][0], kernel))
     torch.cuda.synchronize()
     assert not err.any()
     c, it = conv.cpu().numpy(), iters.cpu().numpy()
@@ -215,6 +227,7 @@ def test_gf4_general_pauli_matrices(mode, seed):
         pytest.skip("no CUDA device")
     g = _random_pauli_code(77, 90, seed)
     dc = S.Gf4DeviceCode(g)
+    assert not dc.css_layout
     shots = 4000
     syn = _sample_paulis(g, 0.01, shots, seed=100 + seed)
     L0 = np.full(shots, I4.prior(0.01), dtype=np.float32)
@@ -244,3 +257,60 @@ def test_gf4_general_pauli_matrices(mode, seed):
     assert worst <= 1e-5, worst
     print(f"gf4 random Pauli matrix {seed} {mode}: {same.mean() * 100:.2f}% identical, FER gpu {fails_g / shots:.4f} "
           f"oracle {fails_o / shots:.4f}, trace error {worst:.2e}")
+
+
+def _random_css_code(m, n, seed, max_dc=10, max_dv=4):
+    """A random CSS matrix: rows of one Pauli type each, X and Z rows interleaved at random, rows
+    of 2..max_dc entries, at most max_dv edges of each type per qubit, m not a multiple of 32.  The
+    CSR order rarely gives distinct slots, so the loader's edge colouring is exercised, and the
+    irregular degrees leave padded check slots and unused message rows."""
+    rng = np.random.default_rng(seed)
+    deg = np.zeros((2, n), dtype=int)
+    rows, paulis = [], []
+    for _ in range(m):
+        t = int(rng.integers(1, 3))
+        k = int(rng.integers(2, max_dc + 1))
+        free = np.nonzero(deg[t - 1] < max_dv)[0]
+        cols = sorted(rng.choice(free, size=min(k, len(free)), replace=False).tolist())
+        deg[t - 1][cols] += 1
+        rows.append(cols)
+        paulis.append([t] * len(cols))
+    row_ptr = np.cumsum([0] + [len(r) for r in rows]).astype(np.int32)
+    return I4.Gf4Code(m=m, n=n, row_ptr=row_ptr, col_idx=np.array([c for r in rows for c in r], dtype=np.int32),
+                      pauli=np.array([p for r in paulis for p in r], dtype=np.uint8), name=f"random-css{seed}")
+
+
+@pytest.mark.parametrize("seed", [11, 12])
+@pytest.mark.parametrize("mode", ["bp", "sms", "sagms"])
+def test_gf4_css_kernel_random_css_matrices(mode, seed):
+    """The CSS kernel on irregular CSS matrices (interleaved X and Z rows, coloured slots, padded
+    slots and message rows, m = 93): against the oracle as the general matrices are, and its
+    first-round posteriors against the generic kernel's (the priors bit for bit; after round 1 the
+    message sums differ only in their order)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    g = _random_css_code(93, 100, seed)
+    dc = S.Gf4DeviceCode(g)
+    assert dc.css_layout
+    shots = 4000
+    syn = _sample_paulis(g, 0.01, shots, seed=200 + seed)
+    L0 = np.full(shots, I4.prior(0.01), dtype=np.float32)
+    p, mo = MODES[mode]
+    p = S.Params(**{**p.__dict__, "max_iter": 40})
+    gr, o = _run(g, dc, syn, L0, p, mo)
+    same = _same(gr, o)
+    fails_o = int((o["conv"] == 0).sum())
+    assert int((~same).sum()) <= 2 * fails_o + int(0.002 * shots), f"{mode}: {int((~same).sum())} mismatches"
+    assert G.mcnemar_p(gr["conv"], o["conv"]) >= 0.01
+    _check_mismatches(g, dc, syn, L0, p, mo, gr, o)
+    gt, _ = _run(g, dc, syn[:32], L0[:32], p, mo, trace=True)
+    gg, _ = _run(g, dc, syn[:32], L0[:32], _with_kernel(p, "generic"), mo, trace=True)
+    assert np.array_equal(gt["trace"][:, 0], gg["trace"][:, 0])
+    ran = (gt["iters"] >= 1) & (gg["iters"] >= 1)   # rows past a shot's last check are not written
+    assert ran.sum() >= 16
+    # the same posteriors up to the order of each sum: normwise, as the traces against the oracle
+    # (a value near zero may come out of terms near +-L0, where a reordering moves a few ulp of L0)
+    a, b = gt["trace"][ran, 1].astype(np.float64), gg["trace"][ran, 1].astype(np.float64)
+    assert float(np.max(np.abs(a - b))) <= 1e-5 * max(float(np.max(np.abs(b))), 1.0)
+    print(f"gf4 random CSS matrix {seed} {mode}: {same.mean() * 100:.2f}% identical to the oracle, "
+          f"FER gpu {float((gr['conv'] == 0).mean()):.4f} oracle {fails_o / shots:.4f}")
