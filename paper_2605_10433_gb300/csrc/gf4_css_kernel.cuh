@@ -95,6 +95,10 @@ __global__ void __launch_bounds__(512, ((!BP && DC <= 10) || DC <= 6) ? 2 : 1) g
         l0_next = __ldg(a.L0 + blockIdx.x);
         sw_next = (t < m) ? __ldg(a.syn + (long long)blockIdx.x * mw + (t >> 5)) : 0u;
     }
+    // lambda_T(L0) of the last prior seen (the first-round input; the prior's bits as the key,
+    // and no finite prior has the bits of a NaN)
+    uint32_t prior_last = 0x7fffffffu;
+    float lam0 = 0.0f;
     for (long long shot = blockIdx.x; shot < a.shots; shot += gridDim.x) {
         const float l0 = l0_next;
         const uint32_t sw = sw_next;
@@ -110,7 +114,10 @@ __global__ void __launch_bounds__(512, ((!BP && DC <= 10) || DC <= 6) ? 2 : 1) g
         const float prior = l0 + 0.0f;
         // A0: no CN message yet; posteriors are the prior, scalar inputs lambda_T(prior), the
         // decision X when L0 < 0 (argmin(0, L0, L0, L0), ties to I): x bit set, z bit clear
-        const float lam0 = gf4_softplus_neg(prior) - gf4_lse_neg(prior, prior);
+        if (__float_as_uint(prior) != prior_last) {   // a batch-wide prior: once per CTA
+            lam0 = gf4_softplus_neg(prior) - gf4_lse_neg(prior, prior);
+            prior_last = __float_as_uint(prior);
+        }
         const uint32_t xb0 = (prior < 0.0f) ? kSign : 0u;
         for (int c = t; c < n; c += T) {
             LXh[c] = lam0;

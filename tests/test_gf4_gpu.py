@@ -314,3 +314,29 @@ def test_gf4_css_kernel_random_css_matrices(mode, seed):
     assert float(np.max(np.abs(a - b))) <= 1e-5 * max(float(np.max(np.abs(b))), 1.0)
     print(f"gf4 random CSS matrix {seed} {mode}: {same.mean() * 100:.2f}% identical to the oracle, "
           f"FER gpu {float((gr['conv'] == 0).mean()):.4f} oracle {fails_o / shots:.4f}")
+
+
+@pytest.mark.parametrize("lw,eps,shots", [((127, 4), 0.05, 4000), ((255, 5), 0.05, 2000)])
+@pytest.mark.parametrize("mode", ["bp", "sagms"])
+def test_gf4_css_kernel_larger_stacks(lw, eps, shots, mode):
+    """The CSS kernel's other shapes and sizes: the CSS stacks of GB(127, 4) (m = 254, d_c = 8,
+    four rows per type and qubit: the (8, 4) shape) and GB(255, 5) (m = 510, 512 threads per
+    CTA, the largest block), against the oracle under the same acceptance."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    g = I4.css_code(I.gb_code(*lw))
+    dc = S.Gf4DeviceCode(g)
+    assert dc.css_layout
+    _, _, syn = I4.depolarizing(g, eps, shots, seed=lw[0] + 31)
+    L0 = np.full(shots, I4.prior(eps), dtype=np.float32)
+    p, mo = MODES[mode]
+    p = S.Params(**{**p.__dict__, "max_iter": 50})
+    gr, o = _run(g, dc, syn, L0, p, mo)
+    same = _same(gr, o)
+    bad = int((~same).sum())
+    assert bad <= max(2, int(MISMATCH_CAP * shots)), f"{bad} mismatching shots of {shots}"
+    assert G.mcnemar_p(gr["conv"], o["conv"]) >= 0.01
+    near, amp, worst = _check_mismatches(g, dc, syn, L0, p, mo, gr, o)
+    assert near <= max(1, int(1e-4 * shots))
+    print(f"gf4 CSS stack GB{lw} (m={g.m}) {mode}: FER gpu {float((gr['conv'] == 0).mean()):.4f} "
+          f"oracle {float((o['conv'] == 0).mean()):.4f}, mismatches {bad} (near-tie {near}, amplified {amp})")
