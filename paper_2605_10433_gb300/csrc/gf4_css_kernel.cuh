@@ -45,10 +45,10 @@ __host__ __device__ inline size_t gf4_css_smem_bytes(int DH, int Np) { return 2 
 
 // colS: [DC][Mp] u32, byte offset of slot j's column of check i within the shared block,
 // 4 * column plus the half of the check's type (padded slots and checks past m: column n).
-// Two 512-thread CTAs' register budget (64) where the shape fits it without spilling: the MS
-// family up to DC = 10, BP at DC = 6.
+// Two 512-thread CTAs' register budget (64), eight 128-thread CTAs per SM for the m = 126
+// stack, for the shapes up to DC = 10 that fit it without spilling (all but BP at DC = 8).
 template <int DC, int DH, bool BP>
-__global__ void __launch_bounds__(512, ((!BP && DC <= 10) || DC <= 6) ? 2 : 1) gf4_css_kernel(const DecodeArgs a, const uint32_t* __restrict__ colS) {
+__global__ void __launch_bounds__(512, (DC <= 10 && !(BP && DC == 8)) ? 2 : 1) gf4_css_kernel(const DecodeArgs a, const uint32_t* __restrict__ colS) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int t = threadIdx.x;
     const int T = blockDim.x;   // == Mp
