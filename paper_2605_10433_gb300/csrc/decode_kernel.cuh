@@ -167,14 +167,32 @@ __global__ void __launch_bounds__(1024, 1) decode_kernel(const DecodeArgs a) {
 #pragma unroll
     for (int j = 0; j < DC; ++j) deg += (colT[j * Mp + t] != (uint16_t)n) ? 1 : 0;
 
+    // CN->VN messages start at zero once per launch: every slot is rewritten by its check in
+    // each round, and a shot's first round reads no old message, so no shot has to clear them.
+#pragma unroll
+    for (int j = 0; j < DC; ++j) C[j * Mp + t] = 0.0f;
+    // The next shot's prior and syndrome word are loaded one shot ahead, so their latency
+    // overlaps the current shot's rounds.
+    float l0_next = 0.0f;
+    uint32_t sw_next = 0u;
+    if (blockIdx.x < a.shots) {
+        if (!per_qubit) l0_next = __ldg(a.L0 + blockIdx.x);
+        sw_next = (t < m) ? __ldg(a.syn + (long long)blockIdx.x * mw + (t >> 5)) : 0u;
+    }
     for (long long shot = blockIdx.x; shot < a.shots; shot += gridDim.x) {
+        const float l0_cur = l0_next;
+        const uint32_t sw = sw_next;
+        if (shot + gridDim.x < a.shots) {
+            if (!per_qubit) l0_next = __ldg(a.L0 + shot + gridDim.x);
+            sw_next = (t < m) ? __ldg(a.syn + (shot + gridDim.x) * mw + (t >> 5)) : 0u;
+        }
         float prior = 0.0f;
         float amax = a.amax;
         bool valid;
         if (per_qubit) {
             valid = pq_ok != 0;
         } else {
-            const float l0 = __ldg(a.L0 + shot);
+            const float l0 = l0_cur;
             valid = isfinite(l0);
             if (BP) prior = l0 + 0.0f;
             else prior = (l0 > 0.0f) ? 1.0f : ((l0 < 0.0f) ? -1.0f : 0.0f);
@@ -185,11 +203,9 @@ __global__ void __launch_bounds__(1024, 1) decode_kernel(const DecodeArgs a) {
             if (t == 0) { a.conv[shot] = 0; a.iters[shot] = -1; }
             continue;
         }
-        // A0: P = L0, C = 0, load s_i
+        // A0: P = L0 (no CN message yet: round 1 reads none), s_i
         for (int c = t; c < n; c += T) P[c] = per_qubit ? PQ[c] : prior;
-#pragma unroll
-        for (int j = 0; j < DC; ++j) C[j * Mp + t] = 0.0f;
-        const uint32_t s_bit = (t < m) ? ((__ldg(a.syn + shot * mw + (t >> 5)) >> (t & 31)) & 1u) : 0u;
+        const uint32_t s_bit = (t < m) ? ((sw >> (t & 31)) & 1u) : 0u;
         if (t == 0) { cnt_sh[0] = 0; cnt_sh[1] = 0; }
         __syncthreads();
 
@@ -228,11 +244,12 @@ __global__ void __launch_bounds__(1024, 1) decode_kernel(const DecodeArgs a) {
 
             // A3: check-node update
             uint32_t par = s_bit << 31;
+            if (it > 0) {   // round 1 has no old message (v - 0 = v exactly)
 #pragma unroll
-            for (int j = 0; j < DC; ++j) {
-                v[j] = v[j] - C[j * Mp + t];
-                par ^= __float_as_uint(v[j]);
+                for (int j = 0; j < DC; ++j) v[j] = v[j] - C[j * Mp + t];
             }
+#pragma unroll
+            for (int j = 0; j < DC; ++j) par ^= __float_as_uint(v[j]);
             par &= kSign;
             if (!BP) {
                 float m1 = __uint_as_float(0x7f800000u), m2 = m1;
