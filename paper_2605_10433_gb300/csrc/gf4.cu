@@ -58,10 +58,11 @@ struct sagms_gf4_code {
 
 namespace {
 
-// The column-indexed layout of a CSS matrix (every row all X or all Z): per row type, slots from
-// sagms_column_slots on that type's rows (distinct mod DH among each qubit's edges of the type),
-// then the biased byte offsets colS[j][i] = 4 col + (type Z ? half : 0); padded slots and checks
-// past m point at the padding column n of the X half.  Returns the shape, or -1.
+// The column-indexed layout of a CSS matrix (every row all X or all Z): per row type, the slot
+// assignment sagms_column_slots would give that type's rows (distinct mod DH among each
+// qubit's edges of the type), then the biased byte offsets colS[j][i] = 4 col + (type Z ?
+// half : 0); padded slots and checks past m point at the padding column n of the X half.
+// Returns the shape, or -1 (the generic kernel then decodes the matrix).
 int css_layout(int m, int n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* pauli, int dc_max,
                int Mp, int Np, std::vector<uint32_t>& colS) {
     std::vector<int> type(m, 0);
@@ -94,10 +95,10 @@ int css_layout(int m, int n, const int32_t* row_ptr, const int32_t* col_idx, con
             rp.push_back((int32_t)ci.size());
         }
         if (rows.empty()) continue;
-        std::vector<int32_t> slot(ci.size());
-        if (sagms_column_slots((int32_t)rows.size(), n, (int64_t)ci.size(), rp.data(), ci.data(), DH, slot.data()) !=
-            SAGMS_OK)
-            return -1;
+        // degrees within the shape: qubit degree of this type <= DH, row degree <= DC = 2 DH
+        const std::vector<int> slot =
+            sagms_internal::column_slot_assignment((int)rows.size(), n, rp.data(), ci.data(), DH);
+        if (slot.size() != ci.size()) return -1;
         for (size_t r = 0; r < rows.size(); ++r)
             for (int e = rp[r]; e < rp[r + 1]; ++e) {
                 if (slot[e] < 0 || slot[e] >= DC) return -1;

@@ -5,6 +5,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
+#include <vector>
 
 #include "../../include/sagms.h"
 
@@ -47,6 +48,13 @@ struct CodeView {
 CodeView code_view(const sagms_code* code);
 // Attach logical operators (device copy owned by the code handle).
 int attach_logicals(sagms_code* code, int k, const uint32_t* h_logicals);
+
+// Column-indexed slot of every edge of a CSR matrix for D message rows (what
+// sagms_column_slots computes: the CSR order when it already gives each qubit distinct slots
+// mod D, else an edge colouring), or empty when there is none.  The caller guarantees a valid
+// CSR with qubit degrees <= D and row degrees <= 2 D.  Records no error, so a caller that only
+// probes whether a layout exists leaves the last-error string alone.
+std::vector<int> column_slot_assignment(int m, int n, const int32_t* row_ptr, const int32_t* col_idx, int D);
 
 // Record `msg` as the calling thread's last error and return `code`.
 int set_error(int code, const char* msg);

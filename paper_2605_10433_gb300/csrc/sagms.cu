@@ -1023,6 +1023,10 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
 
 namespace sagms_internal {
 
+std::vector<int> column_slot_assignment(int m, int n, const int32_t* row_ptr, const int32_t* col_idx, int D) {
+    return column_slots(m, n, row_ptr, col_idx, D);
+}
+
 CodeView code_view(const sagms_code* code) {
     return CodeView{code->m, code->n, code->dv_max, code->device, code->d_qchk, code->k_logicals, code->d_logicals};
 }
