@@ -161,10 +161,12 @@ def bench_mixed_degree(S, I, steps, shots_per_code=1_000_000):
     p=0.02, SAGMS max_iter=100, 1e6 shots per code in one CUDA-graph launch of a multi-code
     decode; each code's launch plan autotuned on a 1e5-shot sample first."""
     import torch
+    from paper_2605_10433_gb300 import roofline
     p = S.Params(mode="sagms", max_iter=MAX_ITER, **SAGMS_KW)
-    jobs, plans = [], {}
+    jobs, plans, ops = [], {}, []
     for w in (3, 4, 5, 6, 8):
         c = I.gb_code(255, w)
+        ops.append(roofline.ops_per_iteration("sagms", c.row_ptr, c.col_idx, c.n))
         _, syn, L0, _ = I.workload(c, [0.02], shots_per_code, seed=NOISE_SEED + w)
         dc = S.DeviceCode.from_code(c)
         d_syn = torch.from_numpy(syn.view(np.int32)).cuda()
@@ -188,11 +190,15 @@ def bench_mixed_degree(S, I, steps, shots_per_code=1_000_000):
     total = shots_per_code * len(jobs) * steps
     fer = {f"w={w}": float((j.conv == 0).float().mean().item()) for w, j in zip((3, 4, 5, 6, 8), jobs)}
     iters = {f"w={w}": float(j.iters.float().mean().item()) for w, j in zip((3, 4, 5, 6, 8), jobs)}
+    # issue roofline of the whole graph launch: every code's iterations x its ops per iteration
+    work = sum(float(j.iters.clamp(min=0).to(torch.int64).sum()) * o for j, o in zip(jobs, ops)) * steps
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    peak = roofline.alu_peak_ops(props.multi_processor_count, float(measured_peaks().get("sm_max_mhz") or 2070.0))
     g.close()
     return {"workload": "GB l=255 (n=510) w in {3,4,5,6,8}, 1e6 shots per code, p=0.02, SAGMS max_iter=100, "
                         "one CUDA-graph launch of sagms_decode_multi per step",
             "shots_per_s": total / (ms / 1e3), "ms_per_launch": ms / steps, "launches": steps,
-            "plans": plans, "fer_syn": fer, "mean_iters": iters}
+            "roofline_frac": work / (ms / 1e3) / peak, "plans": plans, "fer_syn": fer, "mean_iters": iters}
 
 
 def bench_mc(S, I, frames=10_000_000, q=0.01, seed=NOISE_SEED + 1):
@@ -355,6 +361,9 @@ def bench_small_configs(S, I, steps, shots=1_000_000, cpu_shots=20000):
     cases = [("config1 GB l=63 w=3 p=0.05", (63, 3), [0.05], 50, ["sagms", "sms", "ms", "bp"]),
              ("config2 GB l=127 w=4 p_dep=0.01,0.02,0.04 (q=2p/3)", (127, 4), [0.01 * 2 / 3, 0.02 * 2 / 3, 0.04 * 2 / 3],
               MAX_ITER, ["sagms", "sms", "ms", "bp"])]
+    from paper_2605_10433_gb300 import roofline
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    peak = roofline.alu_peak_ops(props.multi_processor_count, float(measured_peaks().get("sm_max_mhz") or 2070.0))
     stream = torch.cuda.current_stream()
     for name, lw, qs, max_iter, modes in cases:
         code = I.gb_code(*lw)
@@ -380,8 +389,11 @@ def bench_small_configs(S, I, steps, shots=1_000_000, cpu_shots=20000):
             oracle.decode_code(code, syn[:cpu_shots], L0[:cpu_shots].astype(np.float64), mode=om, alpha=SMS_ALPHA,
                                max_iter=max_iter, threads=threads, **SAGMS_KW)
             cpu = cpu_shots / (time.perf_counter() - t0)
+            ops = roofline.ops_per_iteration(mode, code.row_ptr, code.col_idx, code.n)
+            it_sum = float(iters.clamp(min=0).to(torch.int64).sum())
             entry[mode] = {"shots_per_s": shots / (ms / 1e3), "fer_syn": float((conv == 0).float().mean()),
-                           "mean_iters": float(iters.float().mean()), "oracle_shots_per_s": cpu,
+                           "mean_iters": float(iters.float().mean()), "ops_per_iteration": ops,
+                           "roofline_frac": it_sum * ops / (ms / 1e3) / peak, "oracle_shots_per_s": cpu,
                            "oracle_cores": threads, "oracle_sample": cpu_shots}
         out[name] = entry
         dc.close()
