@@ -340,3 +340,38 @@ def test_gf4_css_kernel_larger_stacks(lw, eps, shots, mode):
     assert near <= max(1, int(1e-4 * shots))
     print(f"gf4 CSS stack GB{lw} (m={g.m}) {mode}: FER gpu {float((gr['conv'] == 0).mean()):.4f} "
           f"oracle {float((o['conv'] == 0).mean()):.4f}, mismatches {bad} (near-tie {near}, amplified {amp})")
+
+
+@pytest.mark.parametrize("mode", ["bp", "sms", "sagms"])
+def test_gf4_css_kernel_degenerate_rows(mode):
+    """Rows the CSS layout must pad: two empty rows (typed as X rows, all slots padded), three
+    rows of a single entry (degree-1 checks: no second minimum, BP's sum over no other edge) and
+    a qubit in no row at all, among random CSS rows; both kernels against the oracle."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    base = _random_css_code(40, 50, 21, max_dc=6, max_dv=3)
+    rows = [list(base.col_idx[base.row_ptr[i]:base.row_ptr[i + 1]]) for i in range(base.m)]
+    paul = [list(base.pauli[base.row_ptr[i]:base.row_ptr[i + 1]]) for i in range(base.m)]
+    rows = [[c for c in r if c != 49] for r in rows]   # qubit 49 in no row
+    paul = [p[:len(r)] for p, r in zip(paul, rows)]
+    rows[3], paul[3] = [], []
+    rows[17], paul[17] = [], []
+    for i, (c, t) in zip((5, 11, 30), ((7, 1), (8, 2), (9, 1))):
+        rows[i], paul[i] = [c], [t]
+    row_ptr = np.cumsum([0] + [len(r) for r in rows]).astype(np.int32)
+    g = I4.Gf4Code(m=40, n=50, row_ptr=row_ptr, col_idx=np.array([c for r in rows for c in r], dtype=np.int32),
+                   pauli=np.array([p for r in paul for p in r], dtype=np.uint8), name="css-degenerate")
+    dc = S.Gf4DeviceCode(g)
+    assert dc.css_layout
+    shots = 3000
+    syn = _sample_paulis(g, 0.02, shots, seed=77)
+    L0 = np.full(shots, I4.prior(0.02), dtype=np.float32)
+    p, mo = MODES[mode]
+    p = S.Params(**{**p.__dict__, "max_iter": 30})
+    for kernel in ("css", "generic"):
+        gr, o = _run(g, dc, syn, L0, _with_kernel(p, kernel), mo)
+        same = _same(gr, o)
+        fails_o = int((o["conv"] == 0).sum())
+        assert int((~same).sum()) <= 2 * fails_o + int(0.002 * shots), f"{kernel}: {int((~same).sum())} mismatches"
+        _check_mismatches(g, dc, syn, L0, _with_kernel(p, kernel), mo, gr, o)
+        print(f"gf4 degenerate CSS rows {mode} {kernel} kernel: {same.mean() * 100:.2f}% identical to the oracle")
