@@ -604,7 +604,7 @@ def main():
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
             "frac": achieved / peak, "traffic": traffic,
             "kernel": ("sagms::layered_kernel<10,64>" if args.layered else
-                       "sagms::decode_kernel<10,5,BP>" if args.mode == "bp" else "sagms::qc_kernel<10,5,4>"),
+                       "sagms::qc_kernel<10,5,2,512,2048,BP>" if args.mode == "bp" else "sagms::qc_kernel<10,5,4>"),
             "note": (f"ops = sum over shots of iters x {ops_it} per iteration (Eq. 15 / Table I CN cost + VN sum, "
                      f"decision, residual XOR, popcount); peak = {props.multi_processor_count} SMs x 128 lanes x "
                      f"{sm_max:.0f} MHz (derived from unit counts and clock); HBM bound "

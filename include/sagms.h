@@ -132,9 +132,12 @@ int sagms_code_info(const sagms_code* code, int32_t* m, int32_t* n, int32_t* dc_
 
 /* Kernels that can decode a loaded code, in the numbering of a launch plan (sagms_autotune):
  * bit k of *mask set when kernel k has a layout for the code (bit 1, one shot per CTA,
- * always; 2 two-slot; 3 two-group; 4 two-group with column-indexed messages).  Parameters
- * can still rule a kernel out: per-qubit priors, no two-group kernel; BP, the one-shot-per-CTA
- * kernel or, with per-shot priors, the column-indexed one.  Host only.  Errors: ERR_ARG. */
+ * always; 2 two-slot; 3 two-group; 4 two-group with column-indexed messages).  Bit 5 (not a
+ * plan number): BP has a column-indexed shape of its own for the code (two checks per thread,
+ * 129 to 512 or 1025 to 2048 qubits), which BP with per-shot priors takes by default and under plan 4.
+ * Parameters can still rule a kernel out: per-qubit priors, no two-group kernel; BP, the
+ * one-shot-per-CTA kernel or, with per-shot priors, the column-indexed one.  Host only.
+ * Errors: ERR_ARG. */
 int sagms_code_kernels(const sagms_code* code, uint32_t* mask);
 
 /*

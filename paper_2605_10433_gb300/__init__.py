@@ -63,7 +63,7 @@ class DeviceCode:
     def kernels(self):
         """Names of the kernels with a layout for this code (decode_plan's names)."""
         mask = self._native.sagms_code_kernels(self.handle)
-        return [KERNEL_NAMES[k] for k in range(1, 5) if mask >> k & 1]
+        return [KERNEL_NAMES[k] for k in range(1, 6) if mask >> k & 1]
 
     def set_logicals(self, logicals):
         """Attach logical operators (uint32 [k][ceil(n/32)]) for the Monte Carlo check."""
@@ -271,7 +271,8 @@ def decode_host(code: DeviceCode, syn, L0, params: Params | None = None, out=Non
     return err, conv, iters
 
 
-KERNEL_NAMES = {0: "auto", 1: "one-shot-per-CTA", 2: "two-slot", 3: "two-group", 4: "two-group-qc"}
+KERNEL_NAMES = {0: "auto", 1: "one-shot-per-CTA", 2: "two-slot", 3: "two-group", 4: "two-group-qc",
+                5: "two-group-qc-bp"}
 
 
 def decode_plan(plan: int) -> dict:

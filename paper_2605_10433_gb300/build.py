@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libsagms.so")
 SOURCES = [os.path.join(HERE, "csrc", f)
-           for f in ("kernels_qc_large.cu", "kernels_qc_small.cu", "kernels_slots.cu", "kernels_generic.cu",
+           for f in ("kernels_qc_large.cu", "kernels_qc_small.cu", "kernels_qc_bp.cu", "kernels_slots.cu", "kernels_generic.cu",
                      "kernels_layered.cu", "sagms.cu",
                      "server.cu", "mc.cu", "gf4.cu")]
 DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in os.listdir(os.path.join(HERE, "csrc"))] + \

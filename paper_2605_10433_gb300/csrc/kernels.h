@@ -53,6 +53,12 @@ inline int num_qc_variants() { return kNumQcSmall + kNumQcLarge; }
 inline const QcVariant& qc_variant(int v) {
     return v < kNumQcSmall ? kQcVariantsSmall[v] : kQcVariantsLarge[v - kNumQcSmall];
 }
+// Column-indexed shapes for BP alone (kernels_qc_bp.cu): two checks per thread at 64
+// registers, two 512-thread CTAs per SM, for 129 to 512 and 1025 to 2048 qubits; only fn[3]
+// and smem[3] are set.  A code takes the first whose message rows equal its column-indexed shape's (the same
+// slots) and whose checks and qubits it fills at least halfway.
+extern const QcVariant kQcBpVariants[];
+extern const int kNumQcBp;
 
 // Layered schedule (decode_layered.cuh), MS family: (padded check degree, threads per CTA).
 // A code takes the first check degree that covers it, with 32 threads when no layer holds

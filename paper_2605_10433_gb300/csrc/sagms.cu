@@ -373,6 +373,8 @@ struct sagms_code {
     uint32_t* d_vneG;      // [2][kGroupDV][2048] byte offsets of C_g entries
     int qc_variant;        // -1: no column-indexed kernel for this code
     uint32_t* d_colQ;      // qc_layout
+    int qc_bp_variant;     // -1: no BP column-indexed shape (kQcBpVariants) for this code
+    uint32_t* d_colQbp;    // qc_layout for it
     uint16_t* d_qchk;      // [dv_max][n] checks of each qubit, 0xFFFF padding (Monte Carlo sampler)
     int lay_variant;       // -1: no layered-schedule kernel for this code (check degree above 24)
     int lay_L;             // layers of the first-fit partition
@@ -657,6 +659,17 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
 
     std::vector<uint32_t> colQ;
     if (qv >= 0) colQ = qc_layout(m, row_ptr, col_idx, qslot, qc_variant(qv));
+    // BP's column-indexed shape: the same message rows (so the same slots), filled at least
+    // halfway, as for the shape above.
+    int bpv = -1;
+    std::vector<uint32_t> colQbp;
+    for (int v = 0; qv >= 0 && v < kNumQcBp && bpv < 0; ++v) {
+        const QcVariant& V = kQcBpVariants[v];
+        if (V.dv != qc_variant(qv).dv || dc_max > V.dc) continue;
+        if (m > V.k * V.t || 2 * m <= V.k * V.t || n > V.np || 2 * n <= V.np) continue;
+        bpv = v;
+    }
+    if (bpv >= 0) colQbp = qc_layout(m, row_ptr, col_idx, qslot, kQcBpVariants[bpv]);
 
     // Layered schedule: first-fit layers and, in layer order, each check's record (columns,
     // padding n, then the check index and its degree).
@@ -721,6 +734,8 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
     code->k_logicals = -1;
     code->d_logicals = nullptr;
     code->d_colQ = nullptr;
+    code->qc_bp_variant = bpv;
+    code->d_colQbp = nullptr;
     code->slot_variant = sv;
     code->d_colB = nullptr;
     code->d_vneB = nullptr;
@@ -762,6 +777,11 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
         ce = cudaMalloc(&code->d_colQ, colQ.size() * sizeof(uint32_t));
         if (ce == cudaSuccess) ce = cudaMemcpy(code->d_colQ, colQ.data(), colQ.size() * 4, cudaMemcpyHostToDevice);
     }
+    if (ce == cudaSuccess && bpv >= 0) {
+        ce = cudaMalloc(&code->d_colQbp, colQbp.size() * sizeof(uint32_t));
+        if (ce == cudaSuccess)
+            ce = cudaMemcpy(code->d_colQbp, colQbp.data(), colQbp.size() * 4, cudaMemcpyHostToDevice);
+    }
     if (ce == cudaSuccess && lv >= 0) {
         ce = cudaMalloc(&code->d_lrec, lrec.size() * sizeof(uint32_t));
         if (ce == cudaSuccess) ce = cudaMalloc(&code->d_lptr, lptr.size() * sizeof(int));
@@ -783,6 +803,7 @@ int sagms_load_code(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr, c
         cudaFree(code->d_colG);
         cudaFree(code->d_vneG);
         cudaFree(code->d_colQ);
+        cudaFree(code->d_colQbp);
         cudaFree(code->d_lrec);
         cudaFree(code->d_lptr);
         cudaFree(code->d_lqe);
@@ -805,6 +826,7 @@ void sagms_free_code(sagms_code* code) {
     cudaFree(code->d_colG);
     cudaFree(code->d_vneG);
     cudaFree(code->d_colQ);
+    cudaFree(code->d_colQbp);
     cudaFree(code->d_lrec);
     cudaFree(code->d_lptr);
     cudaFree(code->d_lqe);
@@ -826,7 +848,7 @@ int sagms_code_info(const sagms_code* code, int32_t* m, int32_t* n, int32_t* dc_
 int sagms_code_kernels(const sagms_code* code, uint32_t* mask) {
     if (!code || !mask) return fail(SAGMS_ERR_ARG, "code or mask is NULL");
     *mask = (1u << 1) | (code->slot_variant >= 0 ? 1u << 2 : 0u) | (code->groups ? 1u << 3 : 0u) |
-            (code->qc_variant >= 0 ? 1u << 4 : 0u);
+            (code->qc_variant >= 0 ? 1u << 4 : 0u) | (code->qc_bp_variant >= 0 ? 1u << 5 : 0u);
     return SAGMS_OK;
 }
 
@@ -911,12 +933,17 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     const bool msfam_fast = !bp && !(p->flags & SAGMS_FLAG_GENERIC_KERNEL);
     const bool bp_fast = bp && !per_qubit && !(p->flags & SAGMS_FLAG_GENERIC_KERNEL);   // BP: per-shot priors
     const bool auto_ceiling = (p->flags & SAGMS_FLAG_AUTO_CEILING) != 0;
-    // BP on the column-indexed kernel by default only up to 128 qubits: on the larger shapes
-    // (one 512-thread CTA of 128-register threads per SM) BP's transcendental chains leave
-    // too few warps to hide them, and the 1024-thread one-shot-per-CTA kernel is faster
-    // (plan kernel 4 still selects it).
-    const bool use_qc = (msfam_fast || bp_fast) && code->qc_variant >= 0 &&
-                        (plan.kernel == 4 || (plan.kernel == 0 && (!bp || qc_variant(code->qc_variant).np <= 128)));
+    // BP on the column-indexed kernel: on its own shape (two checks per thread, two CTAs per
+    // SM) where the code has one (129 to 512 and 1025 to 2048 qubits), else on the code's
+    // shape up to 128 qubits.  On the larger shapes of four checks per thread (one 512-thread CTA of
+    // 128-register threads per SM) BP's transcendental chains leave too few warps to hide them,
+    // and the 1024-thread one-shot-per-CTA kernel is faster (plan kernel 4 still selects it).
+    const bool qc_bp = bp_fast && code->qc_bp_variant >= 0 && (plan.kernel == 0 || plan.kernel == 4);
+    const bool use_qc = qc_bp || ((msfam_fast || bp_fast) && code->qc_variant >= 0 &&
+                                  (plan.kernel == 4 || (plan.kernel == 0 && (!bp || qc_variant(code->qc_variant).np <= 128))));
+    const QcVariant* QV = qc_bp ? &kQcBpVariants[code->qc_bp_variant]
+                                : (code->qc_variant >= 0 ? &qc_variant(code->qc_variant) : nullptr);
+    const uint32_t* d_colQ = qc_bp ? code->d_colQbp : code->d_colQ;
     const int qc_form = bp ? 3 : (per_qubit ? 2 : (auto_ceiling ? 1 : 0));   // which instantiation
     const bool use_groups = !use_qc && msfam_fast && code->groups && !per_qubit &&
                             (plan.kernel == 0 || plan.kernel >= 3);
@@ -933,7 +960,7 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
     int threads;
     int shots_per_cta;   // shots one CTA decodes at a time
     if (use_qc) {
-        const QcVariant& V = qc_variant(code->qc_variant);
+        const QcVariant& V = *QV;
         fn = reinterpret_cast<const void*>(V.fn[qc_form]);
         smem = V.smem[qc_form];
         threads = kQcThreads;
@@ -1007,7 +1034,7 @@ int launch_decode(const sagms_code* code, const sagms_params* p, int64_t shots, 
         const long long g = std::min(grid, (cnt + shots_per_cta - 1) / shots_per_cta);
         c.chunk_lg = plan.chunk_lg > 0 ? plan.chunk_lg : chunk_lg_for(cnt, g);
         if (use_qc)
-            qc_variant(code->qc_variant).fn[qc_form]<<<(unsigned)g, threads, smem, stream>>>(c, code->d_colQ);
+            QV->fn[qc_form]<<<(unsigned)g, threads, smem, stream>>>(c, d_colQ);
         else if (use_groups)
             group_kernel_fn()<<<(unsigned)g, threads, smem, stream>>>(c, glay);
         else

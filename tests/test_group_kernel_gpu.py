@@ -307,11 +307,14 @@ def test_negative_zero_priors_decide_zero(dev_check):
         assert not (I.unpack_bits(G.gpu_decode(dc, syn, L0q, lay)["err"], c.n)[:, 126]).any()
 
 
-@pytest.mark.parametrize("lw", [(63, 3), (127, 4), (255, 5), (511, 5), (1023, 5), (1023, 3)])
+@pytest.mark.parametrize("lw", [(63, 3), (127, 4), (255, 5), (511, 5), (1023, 5), (1023, 3), (255, 3), (511, 4)])
 def test_column_indexed_bp_bitwise_identical_to_one_shot_per_cta(dev_check, lw):
     """BP (Eq. 3, per-shot priors in LLR units) on the column-indexed kernel: the same slot
     order, phi function and prefix / suffix sums as the one-shot-per-CTA kernel, so outputs
-    and posterior traces agree bit for bit (zero syndromes and negative priors included)."""
+    and posterior traces agree bit for bit (zero syndromes and negative priors included).
+    For 129 to 512 and 1025 to 2048 qubits BP has shapes of its own (two checks per thread,
+    groups of 64, 128 and 512 threads, every slot-degree class): they serve the default plan
+    and plan 4; at 1022 qubits it keeps the code's own column-indexed shape under plan 4."""
     c = I.gb_code(*lw)
     _, syn, L0, _ = I.workload(c, [0.005, 0.02, 0.06], 1501, seed=lw[0] + 7)
     syn = syn.copy()
@@ -321,7 +324,10 @@ def test_column_indexed_bp_bitwise_identical_to_one_shot_per_cta(dev_check, lw):
     p = S.Params(mode="bp", max_iter=40)
     dc = S.DeviceCode.from_code(c)
     assert "two-group-qc" in dc.kernels
-    assert _same(_decode_with_kernel(c, KERNEL_QC, syn, L0, p), _decode_with_kernel(c, KERNEL_GENERIC, syn, L0, p))
+    assert ("two-group-qc-bp" in dc.kernels) == (128 < c.n <= 512 or c.n > 1024)
+    ref = _decode_with_kernel(c, KERNEL_GENERIC, syn, L0, p)
+    assert _same(_decode_with_kernel(c, KERNEL_QC, syn, L0, p), ref)
+    assert _same(G.gpu_decode(dc, syn, L0, p), ref)   # the default plan
     tr = _decode_with_kernel(c, KERNEL_GENERIC, syn[:12], L0[:12], p, trace=True)["trace"]
     tq = _decode_with_kernel(c, KERNEL_QC, syn[:12], L0[:12], p, trace=True)["trace"]
     assert np.array_equal(np.nan_to_num(tr, nan=7.0), np.nan_to_num(tq, nan=7.0))
