@@ -512,12 +512,12 @@ __device__ __forceinline__ void qc_group(const DecodeArgs& a, unsigned char* sme
 // colQ: [K][DC][T] u32, byte offset 4 * col of check tg + kT in slot j (S::PAD for a padded
 // slot or a check past m).  AUTO: the gain ceiling of each shot comes from its prior
 // (SAGMS_FLAG_AUTO_CEILING), a separate instantiation so the default one carries no trace of it.
-// Two CTAs per SM (64 registers) for the small shapes and for BP with two checks per thread in
-// groups of 64 threads or more, where BP's transcendental chains need the warps more than the
-// registers (a few bytes spill at DC = 10).
+// Two CTAs per SM (64 registers) for the small shapes and for BP with two checks per thread,
+// where BP's transcendental chains need the warps more than the registers (a few bytes spill
+// at DC = 10; still 1.15-1.5x faster).  The MS family keeps four checks per thread at 128
+// registers: at 64 it measured 10-21% slower.
 template <class S, bool AUTO, bool PQ, bool BPK = false>
-__global__ void __launch_bounds__(kQcThreads,
-                                  (S::K * S::DC <= 12 || (BPK && S::K == 2 && S::T >= 64 && S::DC <= 10)) ? 2 : 1)
+__global__ void __launch_bounds__(kQcThreads, (S::K * S::DC <= 12 || (BPK && S::K == 2 && S::DC <= 10)) ? 2 : 1)
 qc_kernel(const DecodeArgs a, const uint32_t* __restrict__ colQ) {
     constexpr int DC = S::DC, K = S::K, T = S::T;
     extern __shared__ __align__(16) unsigned char smem[];

@@ -307,7 +307,7 @@ def test_negative_zero_priors_decide_zero(dev_check):
         assert not (I.unpack_bits(G.gpu_decode(dc, syn, L0q, lay)["err"], c.n)[:, 126]).any()
 
 
-@pytest.mark.parametrize("lw", [(63, 3), (127, 4), (255, 5), (511, 5), (1023, 5), (1023, 3), (255, 3), (511, 4)])
+@pytest.mark.parametrize("lw", [(63, 3), (63, 5), (127, 4), (255, 5), (511, 5), (1023, 5), (1023, 3), (255, 3), (511, 4)])
 def test_column_indexed_bp_bitwise_identical_to_one_shot_per_cta(dev_check, lw):
     """BP (Eq. 3, per-shot priors in LLR units) on the column-indexed kernel: the same slot
     order, phi function and prefix / suffix sums as the one-shot-per-CTA kernel, so outputs
